@@ -1,0 +1,471 @@
+#!/usr/bin/env python
+"""Benchmark: 3-D diffusion T_eff at 512^3 FP64, nt = 100 (Fig. 1 workload).
+
+One "step" is one pass of the hot path over one synthetic input: the stable
+dt from maximum(Ci) reduced on the GPU, then the Fig. 1 time loop (boundary
+copy and nt steps with swapped buffers).  T_eff = 3 * nx*ny*nz * 8 bytes *
+nt / time (read T and Ci, write T2 per step).  Inputs (3 x 1 GiB) are larger
+than the 129 MB L2, so no flush is needed between iterations.
+
+Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded samples of the same workload).
+Multi-GPU (torchrun): every rank runs an independent replica.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3-D diffusion T_eff GB/s (% HBM peak) FP64/FP32 at 512^3; gradient/forward time"
+PAPER_TEFF_A100 = 1262.0  # GB/s, FP64 512^3 on an A100 SXM4 (Sect. Results); another machine
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--size", type=int, default=512)
+    p.add_argument("--nt", type=int, default=100)
+    p.add_argument("--no-secondary", action="store_true", help="skip FP32 / gradient / batch lines")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ system
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_digest(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, digest: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged.
+
+    Lines: ``TRAFFIC <kernel> <n> <bytes_per_launch> <source digest>``.
+    """
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        f = ln.split()
+        if len(f) == 5 and f[0] == "TRAFFIC" and f[1] == kernel and f[4] == digest:
+            return float(f[3]) * (n ** 3) / (int(f[2]) ** 3)
+    return None
+
+
+# --------------------------------------------------------------- workloads
+def fields(n):
+    from paper_2211_15634_gb300 import inputs
+    T0 = inputs.t0_gaussian(n, n, n)
+    Ci = inputs.ci_random(n, n, n)
+    return T0, Ci, inputs.inverse_spacing(n, n, n)
+
+
+def oracle_sample(T0, Ci, inv, steps, threads):
+    """Time the FP64 oracle for `steps` steps on the whole field (host cores)."""
+    import oracle
+    n = T0.shape[0]
+    oracle.set_threads(threads)
+    dx = 1.0 / (n - 1)
+    dt = oracle.stable_dt(dx, dx, dx, 1.0, oracle.maximum(Ci))
+    t = time.perf_counter()
+    oracle.run(T0, Ci, 1.0, dt, *inv, steps)
+    el = time.perf_counter() - t
+    return el
+
+
+def cpu_baseline(T0, Ci, inv, budget_s=15.0):
+    import oracle
+    threads = max(1, oracle.max_threads())
+    n = T0.shape[0]
+    t1 = oracle_sample(T0, Ci, inv, 1, threads)
+    steps = int(max(1, min(100, budget_s / max(t1, 1e-3))))
+    el = oracle_sample(T0, Ci, inv, steps, threads)
+    gbs = 3 * n ** 3 * 8 * steps / el / 1e9
+    oracle.set_threads(1)
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps (plus the initial copy) on the full {n}^3 fields, "
+                      f"{el:.1f} s on {threads} host threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n = args.size
+    T0, Ci, inv = fields(n)
+    threads = max(1, oracle.max_threads())
+    t1 = oracle_sample(T0, Ci, inv, 1, threads)
+    total = args.steps + args.warmup
+    steps = int(max(1, min(args.nt, 150.0 / total / max(t1, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(T0, Ci, inv, steps, threads)
+    times = [oracle_sample(T0, Ci, inv, steps, threads) for _ in range(args.steps)]
+    el = sum(times)
+    gbs = 3 * n ** 3 * 8 * steps * args.steps / el / 1e9
+    line = {
+        "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"diffusion3d FP64 {n}^3 Gaussian T0, random Ci, nt={args.nt}",
+                   "nx": n, "ny": n, "nz": n, "nt": args.nt, "parallelism": "host threads"},
+        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": f"each step = {steps} oracle time steps on the full {n}^3 fields"},
+        "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- our path
+def secondary_metrics(torch, api, ag, inputs, log):
+    """FP32 512^3, gradient/forward ratio at 256^3, batched workload."""
+    out = {}
+    dev = torch.device("cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return statistics.median(ts)
+
+    # FP32 deviation storage at 512^3, plain and compensated
+    n, nt = 512, 100
+    T0, Ci, inv = fields(n)
+    T = torch.from_numpy(T0).to(dev)
+    C = torch.from_numpy(Ci).to(dev)
+    D = api.to_deviation(T, 1.7)
+    C32 = api.to_f32(C)
+    del T, C
+    D2 = D.clone()
+    comp = torch.zeros_like(D)
+    dt = api.stable_dt(C32, 1.0)
+    t = timed(lambda: api.run(D, D2, C32, 1.0, dt, inv, nt, graph=True))
+    out["fp32_512_teff_gbs"] = round(3 * n ** 3 * 4 * nt / t / 1e9, 1)
+    t = timed(lambda: api.run(D, D2, C32, 1.0, dt, inv, nt, comp=comp, graph=True))
+    out["fp32c_512_teff_gbs"] = round(5 * n ** 3 * 4 * nt / t / 1e9, 1)
+    del D, D2, comp, C32
+    api.clear_graph_cache()
+    torch.cuda.empty_cache()
+
+    # gradient / forward at 256^3, nt = 200, sqrt(nt) checkpoints
+    n, nt = 256, 200
+    T0 = inputs.t0_gaussian(n, n, n)
+    Ct = inputs.ci_smooth(n, n, n)
+    inv = inputs.inverse_spacing(n, n, n)
+    dx = 1.0 / (n - 1)
+    dt = dx * dx / 1.0 / (1.5 / inputs.C0) / 6.1
+    for name, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
+        if dtype == torch.float64:
+            Td = torch.from_numpy(T0).to(dev)
+            Ctd = torch.from_numpy(Ct).to(dev)
+            Cd = torch.full_like(Td, 1.0 / inputs.C0)
+        else:
+            Td = api.to_deviation(torch.from_numpy(T0).to(dev), 1.7)
+            Ctd = api.to_f32(torch.from_numpy(Ct).to(dev))
+            Cd = torch.full_like(Td, 1.0 / inputs.C0)
+        a, b = Td.clone(), Td.clone()
+        Tobs = api.run(a, b, Ctd, 1.0, dt, inv, nt).clone()
+        fa, fb = Td.clone(), Td.clone()
+        t_fwd = timed(lambda: api.run(fa, fb, Cd, 1.0, dt, inv, nt, graph=True))
+        t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt), reps=2)
+        out[f"grad_over_fwd_256_{name}"] = round(t_grad / t_fwd, 3)
+        out[f"fwd_256_{name}_ms"] = round(1e3 * t_fwd, 2)
+        del Td, Ctd, Cd, a, b, Tobs, fa, fb
+        api.clear_graph_cache()
+        torch.cuda.empty_cache()
+
+    # batched workload: 256 problems, n_p uniform in {32..160}, nt = 500
+    sizes = inputs.batch_sizes(256)
+    nt = 500
+    for name, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
+        probs, bytes_per_step = [], 0
+        esz = 8 if dtype == torch.float64 else 4
+        for q, nq in enumerate(sizes):
+            nq = int(nq)
+            T0q, Ciq = inputs.batch_problem(q, nq)
+            Tq = torch.from_numpy(T0q).to(dev)
+            Cq = torch.from_numpy(Ciq).to(dev)
+            if dtype == torch.float32:
+                Tq = api.to_deviation(Tq, 1.7)
+                Cq = api.to_f32(Cq)
+            dtq = api.stable_dt(Cq, 1.0)
+            probs.append(dict(T=Tq, T2=Tq.clone(), Ci=Cq, lam=1.0, dt=dtq,
+                              inv_spacing=inputs.inverse_spacing(nq, nq, nq)))
+            bytes_per_step += 3 * nq ** 3 * esz
+        b = api.Batch(probs)
+        t_b = timed(lambda: b.run(nt, graph=True), reps=2)
+        out[f"batch_{name}_teff_gbs"] = round(bytes_per_step * nt / t_b / 1e9, 1)
+
+        def per_problem():
+            for p in probs:
+                api.run(p["T"], p["T2"], p["Ci"], 1.0, p["dt"], p["inv_spacing"], nt)
+        t_p = timed(per_problem, reps=1)
+        out[f"batch_{name}_per_problem_teff_gbs"] = round(bytes_per_step * nt / t_p / 1e9, 1)
+        del probs, b
+        api.clear_graph_cache()
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_2211_15634_gb300 import api, inputs
+    from paper_2211_15634_gb300 import autograd as ag
+    from paper_2211_15634_gb300 import _lib
+
+    _lib.load()
+    n, nt, K, W = args.size, args.nt, args.steps, args.warmup
+    assert W >= 3, "need at least 3 warm-up steps"
+    T0, Ci, inv = fields(n)
+    dev = torch.device(f"cuda:{local}")
+    T = torch.from_numpy(T0).to(dev)
+    T2 = torch.empty_like(T)
+    C = torch.from_numpy(Ci).to(dev)
+    lam = 1.0
+    bytes_per_launch = 3 * n ** 3 * 8
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def one_step(kernel_events=None):
+        dt = api.stable_dt(C, lam)          # A1: maximum(Ci) on the GPU, dt on the host
+        api.copy_boundary(T2, T)            # Fig. 1: T2 = copy(T) on the boundary
+        for it in range(nt):
+            src, dst = (T, T2) if it % 2 == 0 else (T2, T)
+            if kernel_events is not None:
+                kernel_events[it][0].record()
+            api.step(dst, src, C, lam, dt, inv)
+            if kernel_events is not None:
+                kernel_events[it][1].record()
+        return dt
+
+    for _ in range(W):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local).start() if rank == 0 else None
+    kev = [[[ev(), ev()] for _ in range(nt)] for _ in range(K)]
+    torch.cuda.synchronize()
+    t_start, t_end = ev(), ev()
+    t_start.record()
+    for s in range(K):
+        one_step(kev[s])
+    t_end.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    region_s = t_start.elapsed_time(t_end) / 1e3
+    launch_ms = [a.elapsed_time(b) for step in kev for (a, b) in step]
+    if world > 1:
+        tt = torch.tensor([region_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        region_s = float(tt.item())
+    gbs = world * bytes_per_launch * nt * K / region_s / 1e9
+    gpu_launches = K * (nt + 3)  # per step: max reduction (2 kernels), boundary copy, nt steps
+
+    # the same time loop as a captured CUDA graph (library-side cache)
+    dt = api.stable_dt(C, lam)
+    api.run(T, T2, C, lam, dt, inv, nt, graph=True)
+    torch.cuda.synchronize()
+    g0, g1 = ev(), ev()
+    g0.record()
+    for _ in range(K):
+        api.run(T, T2, C, lam, dt, inv, nt, graph=True)
+    g1.record()
+    torch.cuda.synchronize()
+    graph_gbs = bytes_per_launch * nt * K / (g0.elapsed_time(g1) / 1e3) / 1e9
+    api.clear_graph_cache()
+
+    # end to end through the public API: pinned host in, host result out
+    e2e = None
+    if rank == 0 or world > 1:
+        T0h = torch.from_numpy(T0).pin_memory()
+        Cih = torch.from_numpy(Ci).pin_memory()
+        outh = torch.empty_like(T0h).pin_memory()
+        bufs = (T, T2, C)
+        api.solve(T0h, Cih, lam, None, inv, nt, out_host=outh, buffers=bufs)
+        times = []
+        for _ in range(max(1, args.e2e_steps)):
+            t0 = time.perf_counter()
+            api.solve(T0h, Cih, lam, None, inv, nt, out_host=outh, buffers=bufs)
+            times.append(time.perf_counter() - t0)
+        e2e_s = sum(times)
+        e2e = {"value": round(world * bytes_per_launch * nt * len(times) / e2e_s / 1e9, 1),
+               "unit": "GB/s", "h2d_bytes_per_step": 2 * n ** 3 * 8,
+               "d2h_bytes_per_step": n ** 3 * 8}
+        api.clear_graph_cache()
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    hbm, src = measured_peaks()
+    mean_launch_s = statistics.mean(launch_ms) / 1e3
+    achieved = bytes_per_launch / mean_launch_s / 1e9
+    kernel = api.step_kernel_name(torch.float64)
+    digest = source_digest(api.step_kernel_sources(torch.float64))
+    traffic = profiled_traffic(kernel, digest, n)
+    line = {
+        "metric": METRIC, "value": round(gbs, 1), "unit": "GB/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": round(1e3 * region_s / K, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": round(gbs / world / PAPER_TEFF_A100, 3),
+        "vs_baseline_note": "paper T_eff 1262 GB/s, FP64 512^3, A100 SXM4: another machine, context",
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"diffusion3d FP64 {n}^3 Gaussian T0, random Ci, nt={nt}",
+                   "nx": n, "ny": n, "nz": n, "nt": nt, "lam": lam, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (3 x 1 GiB fields), no flush needed",
+                   "pct_hbm_peak": round(100 * gbs / world / hbm, 1)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": kernel,
+                     "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+                     "launches_timed": len(launch_ms),
+                     "mean_launch_ms": round(1e3 * mean_launch_s, 4)},
+        "graph_value": round(graph_gbs, 1),
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline(T0, Ci, inv)
+        except Exception as exc:  # reported, not fatal
+            line["cpu_baseline"] = {"error": str(exc)}
+    del T, T2, C
+    torch.cuda.empty_cache()
+    if not args.no_secondary and world == 1:
+        try:
+            line["secondary"] = secondary_metrics(torch, api, ag, inputs, log)
+        except Exception as exc:
+            line["secondary"] = {"error": repr(exc)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * ps_diffusion3d.h - C ABI of the GB300 (sm_103a) 3-D heat diffusion stencil.
+ *
+ * The operation is the explicit time step of the 3-D variable-coefficient
+ * heat diffusion solver in Omlin & Raess, "High-performance xPU Stencil
+ * Computations in Julia" (arXiv 2211.15634), Fig. 1:
+ *
+ *   step!(T2, T, Ci, lam, dt, _dx, _dy, _dz):
+ *     @inn(T2) = @inn(T) + dt*(lam*@inn(Ci)*(@d2_xi(T)*_dx^2
+ *                                          + @d2_yi(T)*_dy^2 + @d2_zi(T)*_dz^2))
+ *
+ * with @d2_di the three-point second difference along axis d at interior
+ * nodes, iterated nt times with the two buffers swapped after every step
+ * (Fig. 1 time loop) and the stable step dt = min(dx^2,dy^2,dz^2)/lam/
+ * maximum(Ci)/6.1 (Fig. 1).  Boundary nodes are never written: they keep
+ * their initial values in both buffers (Dirichlet), which is what
+ * "T2 = copy(T)" in Fig. 1 sets up.
+ *
+ * ----------------------------------------------------------------------
+ * Conventions that hold for every entry point
+ * ----------------------------------------------------------------------
+ * Layout   A field is one contiguous array of nx*ny*nz elements; node
+ *          (i,j,k) is at offset i + nx*(j + ny*k) (x fastest, Julia's
+ *          column-major T[i,j,k]).  Base pointers must be 16-byte aligned
+ *          (any size works; rows need not be aligned).
+ * Dtypes   PS_F64: every field is double.
+ *          PS_F32: every field is float.  Temperature fields hold the
+ *          deviation D = T - T_ref from a constant reference (the solver
+ *          is exact under this shift because the second difference of a
+ *          constant is zero and the boundary is fixed); ps_to_deviation /
+ *          ps_from_deviation convert.
+ * Memory   All field pointers are DEVICE pointers allocated and owned by
+ *          the caller.  The library allocates nothing on these calls.
+ *          Entry points that need scratch take a caller-owned device
+ *          workspace of at least ps_workspace_bytes() bytes.
+ * Streams  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *          Every call only enqueues work on it and returns; none
+ *          synchronizes, except where a host result is returned
+ *          (ps_maximum, ps_diffusion3d_stable_dt), which synchronize
+ *          `stream` before returning.
+ * Errors   Every entry point returns a ps_status.  Arguments are checked
+ *          on the host before anything is launched; a failed check
+ *          launches nothing.  PS_ERR_CUDA reports a CUDA error seen at
+ *          launch.  ps_last_error() gives a message for the last non-OK
+ *          status of the calling thread.  Nothing traps on the device.
+ */
+#ifndef PS_DIFFUSION3D_H
+#define PS_DIFFUSION3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { PS_F32 = 0, PS_F64 = 1 } ps_dtype;
+
+typedef enum {
+    PS_OK = 0,
+    PS_ERR_ARG = -1,         /* null pointer, size < 3, bad dtype, nt < 0, ... */
+    PS_ERR_ALIAS = -2,       /* an output overlaps an input it must not overlap */
+    PS_ERR_ALIGN = -3,       /* a base pointer is not 16-byte aligned */
+    PS_ERR_CUDA = -4,        /* a CUDA call or launch failed */
+    PS_ERR_UNSUPPORTED = -5  /* valid request this build cannot serve */
+} ps_status;
+
+/* Flags of ps_diffusion3d_run_ex. */
+#define PS_RUN_GRAPH 1u       /* capture the nt launches into a CUDA graph once, replay it */
+#define PS_RUN_COMPENSATED 2u /* PS_F32 only: compensated (Kahan) update, needs `comp` */
+#define PS_RUN_NATIVE_F64 4u  /* PS_F64 only: force the plain FP64-instruction kernel */
+
+/* Library version (major*10000 + minor*100 + patch). */
+int ps_version(void);
+
+/* Message for the last non-OK status returned to the calling thread
+ * ("" if none).  The pointer stays valid until the thread's next call. */
+const char *ps_last_error(void);
+
+/* Bytes of device workspace the reduction entry points need. */
+size_t ps_workspace_bytes(void);
+
+/* ---------------------------------------------------------------------
+ * Time step (Fig. 1, step!).  Writes the interior nodes of T2 from T and
+ * Ci; T2's boundary is left untouched.  T2 must not overlap T or Ci.
+ * lam, dt, _dx, _dy, _dz are the paper's arguments (_d = 1/d-spacing);
+ * the kernel uses _d*_d.  nx, ny, nz >= 3.
+ * dtype PS_F64: results match the FP64 definition to within a few units
+ * in the last place per step (FMA contraction and association differ).
+ * ------------------------------------------------------------------- */
+int ps_diffusion3d_step(void *T2, const void *T, const void *Ci, double lam, double dt,
+                        double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
+                        int dtype, void *stream);
+
+/* Compensated FP32 step: as ps_diffusion3d_step with dtype PS_F32, but the
+ * update D2 = D + delta is done with a per-node Kahan compensation term
+ * `comp` (float, same layout, read and updated in place; start it at 0).
+ * Only interior nodes of comp are touched. */
+int ps_diffusion3d_step_comp_f32(float *T2, const float *T, float *comp, const float *Ci,
+                                 double lam, double dt, double _dx, double _dy, double _dz,
+                                 int64_t nx, int64_t ny, int64_t nz, void *stream);
+
+/* Copy the six boundary faces of T into T2 (so that T2 = copy(T) holds on
+ * the boundary, Fig. 1), leaving T2's interior untouched. */
+int ps_diffusion3d_copy_boundary(void *T2, const void *T, int64_t nx, int64_t ny, int64_t nz,
+                                 int dtype, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Time loop (Fig. 1): copy T's boundary into T2, then nt steps, swapping
+ * the roles of T and T2 after each.  On return *result_in_T2 (host int,
+ * may be NULL) is 1 when the final state is in T2 (nt odd) and 0 when it is
+ * in T.  T's interior is overwritten when nt >= 2.
+ * ------------------------------------------------------------------- */
+int ps_diffusion3d_run(void *T, void *T2, const void *Ci, double lam, double dt, double _dx,
+                       double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int nt,
+                       int dtype, void *stream, int *result_in_T2);
+
+/* As ps_diffusion3d_run with flags (PS_RUN_*).  `comp` is the float
+ * compensation field for PS_RUN_COMPENSATED (caller zeroes it), else NULL.
+ * With PS_RUN_GRAPH the nt launches are captured into a CUDA graph on the
+ * first call for a given argument set and replayed afterwards (the graph
+ * is cached inside the library until ps_clear_graph_cache()). */
+int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double lam, double dt,
+                          double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
+                          int nt, int dtype, unsigned flags, void *stream, int *result_in_T2);
+
+/* Destroy every cached CUDA graph. */
+int ps_clear_graph_cache(void);
+
+/* ---------------------------------------------------------------------
+ * Adjoint of one step (the transpose of step!'s Jacobian; derived from
+ * Fig. 1's step, no paper line).  With ybar = dL/dT_{t+1} and T = T_t,
+ * the state the forward step read:
+ *   w[q]      = dt*lam*Ci[q]*ybar[q] at interior q, 0 elsewhere;
+ *   Tbar[p]   = ybar[p] + sum_d (w[p-e_d] - 2 w[p] + w[p+e_d]) * _d^2
+ *               at EVERY node p (w = 0 outside the grid);
+ *   Cibar[q] += dt*lam*ybar[q]*Lap(T)[q] at interior q.
+ * Tbar is written at all nodes and must not overlap any input; Cibar is
+ * read-modify-written (accumulated) at interior nodes only.
+ * dtype PS_F64: all fields double.  PS_F32: all fields float.
+ * ------------------------------------------------------------------- */
+int ps_diffusion3d_adjoint(void *Tbar, void *Cibar, const void *ybar, const void *T,
+                           const void *Ci, double lam, double dt, double _dx, double _dy,
+                           double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                           void *stream);
+
+/* ---------------------------------------------------------------------
+ * Reductions in FP64 (deterministic: a fixed partition and a fixed
+ * summation order, independent of timing).  A, B are device arrays of n
+ * elements of `dtype`; out_dev is a device double; workspace is a device
+ * buffer of ps_workspace_bytes().
+ * ------------------------------------------------------------------- */
+/* maximum(A) (Fig. 1's maximum(Ci)); result to a device double. */
+int ps_maximum_async(double *out_dev, const void *A, int64_t n, int dtype, void *workspace,
+                     void *stream);
+/* maximum(A) returned to the host (synchronizes `stream`). */
+int ps_maximum(double *out_host, const void *A, int64_t n, int dtype, void *workspace,
+               void *stream);
+/* Fig. 1: dt = min(dx^2,dy^2,dz^2)/lam/maximum(Ci)/6.1 with dd = ld/(nd-1);
+ * the maximum is reduced on the device, dt is formed on the host in FP64 and
+ * returned in *dt_host (synchronizes `stream`). */
+int ps_diffusion3d_stable_dt(double *dt_host, const void *Ci, int64_t nx, int64_t ny, int64_t nz,
+                             double lam, double lx, double ly, double lz, int dtype,
+                             void *workspace, void *stream);
+/* sum_p A[p]*B[p], accumulated in FP64, to a device double. */
+int ps_dot(double *out_dev, const void *A, const void *B, int64_t n, int dtype, void *workspace,
+           void *stream);
+/* Loss of the inverse problem: 1/2 * sum_p (A[p]-B[p])^2 in FP64 to
+ * *out_dev, and, if R is not NULL, the residual R = A - B (the cotangent
+ * dL/dA) in `dtype`. */
+int ps_half_sq_dist(double *out_dev, void *R, const void *A, const void *B, int64_t n, int dtype,
+                    void *workspace, void *stream);
+
+/* FP32 deviation storage: D[p] = (float)(T[p] - t_ref), with the
+ * subtraction in FP64 and one rounding to float. */
+int ps_to_deviation(float *D, const double *T, double t_ref, int64_t n, void *stream);
+/* T[p] = (double)D[p] + t_ref in FP64. */
+int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Batched step: many independent problems of different sizes, one launch
+ * per step.  The host describes each problem with a ps_problem; the
+ * library lays them out in a device table (problem records followed by a
+ * static work list of (problem, x-y tile, z-chunk) items) that the caller
+ * copies to device memory once.  A step processes every work item of the
+ * table; `parity` 0 reads T and writes T2, parity 1 reads T2 and writes T
+ * (so parity = step index & 1 reproduces the swap of Fig. 1's loop).
+ * ------------------------------------------------------------------- */
+typedef struct {
+    void *T;          /* device field, nx*ny*nz of dtype */
+    void *T2;         /* device field, same size, boundary equal to T's */
+    const void *Ci;   /* device field */
+    double lam, dt, _dx, _dy, _dz;
+    int64_t nx, ny, nz;
+} ps_problem;
+
+/* Bytes of the table for these problems with the given tile shape
+ * (tile_x, tile_y: interior nodes per work item in x and y; tile_z: nodes
+ * per z-chunk; 0 picks the library default for the dtype). */
+size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
+                            int tile_z);
+/* Fill host_buf (bytes >= ps_batch_table_bytes) with the table.  Checks
+ * every problem like ps_diffusion3d_step.  *nitems_out = work items. */
+int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, int nprob,
+                        int dtype, int tile_x, int tile_y, int tile_z, int64_t *nitems_out);
+/* One step of every problem in the device table (dev_table = device copy
+ * of the filled host buffer). */
+int ps_diffusion3d_batch_step(const void *dev_table, int parity, int dtype, void *stream);
+/* nt batched steps with parity 0, 1, 0, ... (the buffers of problem p hold
+ * its final state in T2 when nt is odd, in T when even).  Flags: PS_RUN_GRAPH
+ * captures the nt launches once per (table, nt, dtype) and replays them. */
+int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned flags,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_DIFFUSION3D_H */

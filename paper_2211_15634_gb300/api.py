@@ -1,0 +1,301 @@
+"""Python API over the C ABI (torch tensors for device memory and streams).
+
+Fields are C-contiguous CUDA tensors of shape ``(nz, ny, nx)`` (x fastest),
+``torch.float64`` for the FP64 path or ``torch.float32`` for the FP32 path
+(which stores temperatures as deviations from a reference, see
+:func:`to_deviation`).  Every function enqueues on the tensor device's
+current torch stream and returns without synchronizing unless it returns a
+Python float.  ``inv_spacing`` is ``(_dx, _dy, _dz)`` as in Fig. 1's
+``step!`` arguments.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import PS_F32, PS_F64, check
+
+_WS = {}
+
+
+def _code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return PS_F64
+    if t.dtype == torch.float32:
+        return PS_F32
+    raise TypeError(f"unsupported dtype {t.dtype} (need float32 or float64)")
+
+
+def _field(t: torch.Tensor, name: str, code: Optional[int] = None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if code is not None and _code(t) != code:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {'float64' if code else 'float32'}")
+    return t.data_ptr()
+
+
+def _grid(t: torch.Tensor):
+    if t.dim() != 3:
+        raise ValueError("fields must have shape (nz, ny, nx)")
+    nz, ny, nx = t.shape
+    return nx, ny, nz
+
+
+def _stream(t: torch.Tensor) -> int:
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def workspace(device) -> torch.Tensor:
+    """Per-device scratch buffer for the reductions (allocated once, reused)."""
+    device = torch.device(device)
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    ws = _WS.get(idx)
+    if ws is None:
+        n = _lib.load().ps_workspace_bytes()
+        ws = torch.empty(n, dtype=torch.uint8, device=f"cuda:{idx}")
+        _WS[idx] = ws
+    return ws
+
+
+def _same(a: torch.Tensor, *others: torch.Tensor):
+    for o in others:
+        if o.shape != a.shape or o.device != a.device:
+            raise ValueError("fields must share shape and device")
+
+
+def step(T2, T, Ci, lam: float, dt: float, inv_spacing: Sequence[float]) -> None:
+    """One step of Fig. 1 (``step!(T2, T, Ci, lam, dt, _dx, _dy, _dz)``)."""
+    code = _code(T)
+    _same(T, T2, Ci)
+    nx, ny, nz = _grid(T)
+    check(_lib.load().ps_diffusion3d_step(_field(T2, "T2", code), _field(T, "T", code),
+                                          _field(Ci, "Ci", code), lam, dt, *inv_spacing, nx, ny,
+                                          nz, code, _stream(T)))
+
+
+def step_compensated(T2, T, comp, Ci, lam: float, dt: float, inv_spacing) -> None:
+    """FP32 step with the per-node Kahan compensation field ``comp``."""
+    _same(T, T2, comp, Ci)
+    nx, ny, nz = _grid(T)
+    check(_lib.load().ps_diffusion3d_step_comp_f32(
+        _field(T2, "T2", PS_F32), _field(T, "T", PS_F32), _field(comp, "comp", PS_F32),
+        _field(Ci, "Ci", PS_F32), lam, dt, *inv_spacing, nx, ny, nz, _stream(T)))
+
+
+def copy_boundary(T2, T) -> None:
+    """T2's six boundary faces := T's (Fig. 1's ``T2 = copy(T)`` on the boundary)."""
+    code = _code(T)
+    _same(T, T2)
+    nx, ny, nz = _grid(T)
+    check(_lib.load().ps_diffusion3d_copy_boundary(_field(T2, "T2", code), _field(T, "T", code),
+                                                   nx, ny, nz, code, _stream(T)))
+
+
+def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, graph=False,
+        native_f64=False) -> torch.Tensor:
+    """Fig. 1 time loop on the buffer pair (T, T2); returns the tensor holding T(nt)."""
+    code = _code(T)
+    _same(T, T2, Ci)
+    nx, ny, nz = _grid(T)
+    flags = 0
+    if graph:
+        flags |= _lib.PS_RUN_GRAPH
+    if comp is not None:
+        flags |= _lib.PS_RUN_COMPENSATED
+        _same(T, comp)
+    if native_f64:
+        flags |= _lib.PS_RUN_NATIVE_F64
+    odd = ctypes.c_int(0)
+    check(_lib.load().ps_diffusion3d_run_ex(
+        _field(T, "T", code), _field(T2, "T2", code),
+        _field(comp, "comp", PS_F32) if comp is not None else None, _field(Ci, "Ci", code), lam,
+        dt, *inv_spacing, nx, ny, nz, int(nt), code, flags, _stream(T), ctypes.byref(odd)))
+    return T2 if odd.value else T
+
+
+def adjoint(Tbar, Cibar, ybar, T, Ci, lam: float, dt: float, inv_spacing) -> None:
+    """Transposed step: Tbar := M^T ybar; Cibar += dt*lam*ybar*Lap(T) (interior)."""
+    code = _code(T)
+    _same(T, Tbar, Cibar, ybar, Ci)
+    nx, ny, nz = _grid(T)
+    check(_lib.load().ps_diffusion3d_adjoint(
+        _field(Tbar, "Tbar", code), _field(Cibar, "Cibar", code), _field(ybar, "ybar", code),
+        _field(T, "T", code), _field(Ci, "Ci", code), lam, dt, *inv_spacing, nx, ny, nz, code,
+        _stream(T)))
+
+
+def maximum_async(A, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """max(A) into a 0-dim float64 device tensor (no synchronization)."""
+    code = _code(A)
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=A.device)
+    check(_lib.load().ps_maximum_async(out.data_ptr(), _field(A, "A", code), A.numel(), code,
+                                       workspace(A.device).data_ptr(), _stream(A)))
+    return out
+
+
+def maximum(A) -> float:
+    """``maximum(A)`` returned to the host (synchronizes the stream)."""
+    code = _code(A)
+    v = ctypes.c_double(0.0)
+    check(_lib.load().ps_maximum(ctypes.byref(v), _field(A, "A", code), A.numel(), code,
+                                 workspace(A.device).data_ptr(), _stream(A)))
+    return v.value
+
+
+def stable_dt(Ci, lam: float = 1.0, lengths=(1.0, 1.0, 1.0)) -> float:
+    """Fig. 1: ``dt = min(dx^2,dy^2,dz^2)/lam/maximum(Ci)/6.1`` (maximum on the GPU)."""
+    code = _code(Ci)
+    nx, ny, nz = _grid(Ci)
+    v = ctypes.c_double(0.0)
+    check(_lib.load().ps_diffusion3d_stable_dt(ctypes.byref(v), _field(Ci, "Ci", code), nx, ny, nz,
+                                               lam, *lengths, code,
+                                               workspace(Ci.device).data_ptr(), _stream(Ci)))
+    return v.value
+
+
+def dot(A, B, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """sum(A*B) accumulated in FP64, as a 0-dim device tensor."""
+    code = _code(A)
+    _same(A, B)
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=A.device)
+    check(_lib.load().ps_dot(out.data_ptr(), _field(A, "A", code), _field(B, "B", code), A.numel(),
+                             code, workspace(A.device).data_ptr(), _stream(A)))
+    return out
+
+
+def half_sq_dist(A, B, residual: Optional[torch.Tensor] = None,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """L = 1/2 ||A - B||^2 in FP64 (0-dim device tensor); optionally residual := A - B."""
+    code = _code(A)
+    _same(A, B)
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=A.device)
+    rptr = None
+    if residual is not None:
+        _same(A, residual)
+        rptr = _field(residual, "residual", code)
+    check(_lib.load().ps_half_sq_dist(out.data_ptr(), rptr, _field(A, "A", code),
+                                      _field(B, "B", code), A.numel(), code,
+                                      workspace(A.device).data_ptr(), _stream(A)))
+    return out
+
+
+def to_deviation(T: torch.Tensor, t_ref: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FP32 deviation field ``(float)(T - t_ref)`` of an FP64 field."""
+    if out is None:
+        out = torch.empty(T.shape, dtype=torch.float32, device=T.device)
+    check(_lib.load().ps_to_deviation(_field(out, "D", PS_F32), _field(T, "T", PS_F64), t_ref,
+                                      T.numel(), _stream(T)))
+    return out
+
+
+def from_deviation(D: torch.Tensor, t_ref: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FP64 field ``(double)D + t_ref`` from an FP32 deviation field."""
+    if out is None:
+        out = torch.empty(D.shape, dtype=torch.float64, device=D.device)
+    check(_lib.load().ps_from_deviation(_field(out, "T", PS_F64), _field(D, "D", PS_F32), t_ref,
+                                        D.numel(), _stream(D)))
+    return out
+
+
+def to_f32(A: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FP32 copy of an FP64 coefficient field (one rounding per element)."""
+    return to_deviation(A, 0.0, out)
+
+
+class Batch:
+    """Many independent problems stepped together by one persistent launch.
+
+    ``problems`` is a list of dicts with keys ``T, T2, Ci`` (CUDA tensors of
+    one dtype, any cubic or non-cubic shape), ``lam``, ``dt`` and
+    ``inv_spacing``.  T2's boundary must equal T's (e.g. ``T2 = T.clone()``).
+    """
+
+    def __init__(self, problems, tile=(0, 0, 0)):
+        if not problems:
+            raise ValueError("empty batch")
+        lib = _lib.load()
+        self.code = _code(problems[0]["T"])
+        self.device = problems[0]["T"].device
+        self.problems = problems
+        arr = (_lib.PsProblem * len(problems))()
+        for q, p in enumerate(problems):
+            _same(p["T"], p["T2"], p["Ci"])
+            nx, ny, nz = _grid(p["T"])
+            arr[q] = _lib.PsProblem(_field(p["T"], "T", self.code), _field(p["T2"], "T2", self.code),
+                                    _field(p["Ci"], "Ci", self.code), p["lam"], p["dt"],
+                                    *p["inv_spacing"], nx, ny, nz)
+        nbytes = lib.ps_batch_table_bytes(arr, len(problems), self.code, *tile)
+        if nbytes == 0:
+            raise ValueError("invalid batch description")
+        host = (ctypes.c_char * nbytes)()
+        nitems = ctypes.c_int64(0)
+        check(lib.ps_batch_table_fill(host, nbytes, arr, len(problems), self.code, *tile,
+                                      ctypes.byref(nitems)))
+        self.nitems = nitems.value
+        self.tile = tile
+        cpu = torch.frombuffer(bytearray(host.raw), dtype=torch.uint8)
+        self.table = cpu.to(self.device)
+        torch.cuda.current_stream(self.device).synchronize()
+
+    def step(self, parity: int) -> None:
+        check(_lib.load().ps_diffusion3d_batch_step(self.table.data_ptr(), int(parity), self.code,
+                                                    torch.cuda.current_stream(self.device).cuda_stream))
+
+    def run(self, nt: int, graph: bool = True) -> None:
+        """nt steps; problem p's state ends in T2 when nt is odd, in T when even."""
+        flags = _lib.PS_RUN_GRAPH if graph else 0
+        check(_lib.load().ps_diffusion3d_batch_run(self.table.data_ptr(), int(nt), self.code, flags,
+                                                   torch.cuda.current_stream(self.device).cuda_stream))
+
+    def result(self, q: int, nt: int) -> torch.Tensor:
+        p = self.problems[q]
+        return p["T2"] if nt & 1 else p["T"]
+
+
+def clear_graph_cache() -> None:
+    check(_lib.load().ps_clear_graph_cache())
+
+
+def step_kernel_name(dtype) -> str:
+    """Name of the kernel that ``step`` launches for this dtype (for profiles)."""
+    return "k_step_basic" if dtype == torch.float64 else "k_step_basic"
+
+
+def step_kernel_sources(dtype):
+    """Source files of that kernel, relative to the repository root."""
+    return ["paper_2211_15634_gb300/csrc/stencil_basic.cuh"]
+
+
+def solve(T0_host: torch.Tensor, Ci_host: torch.Tensor, lam: float, dt: Optional[float],
+          inv_spacing, nt: int, *, device="cuda", graph: bool = True,
+          out_host: Optional[torch.Tensor] = None, buffers=None,
+          lengths=(1.0, 1.0, 1.0)) -> torch.Tensor:
+    """End to end: host fields in (pinned CPU tensors), T(nt) back on the host.
+
+    ``dt=None`` takes Fig. 1's stable step from maximum(Ci) (reduced on the
+    GPU).  ``buffers`` may hold preallocated device tensors ``(T, T2, Ci)``.
+    """
+    if buffers is None:
+        T = torch.empty(T0_host.shape, dtype=T0_host.dtype, device=device)
+        T2 = torch.empty_like(T)
+        Ci = torch.empty(Ci_host.shape, dtype=Ci_host.dtype, device=device)
+    else:
+        T, T2, Ci = buffers
+    T.copy_(T0_host, non_blocking=True)
+    Ci.copy_(Ci_host, non_blocking=True)
+    if dt is None:
+        dt = stable_dt(Ci, lam, lengths)
+    res = run(T, T2, Ci, lam, dt, inv_spacing, nt, graph=graph)
+    if out_host is None:
+        out_host = torch.empty(T0_host.shape, dtype=T0_host.dtype, pin_memory=True)
+    out_host.copy_(res, non_blocking=True)
+    torch.cuda.current_stream(T.device).synchronize()
+    return out_host

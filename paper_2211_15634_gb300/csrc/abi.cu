@@ -1,0 +1,551 @@
+// C ABI of the library: host-side argument checks, dispatch to the kernels,
+// the CUDA-graph cache of ps_diffusion3d_run_ex and the batch-table builder.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace psd {
+
+static thread_local std::string g_err;
+
+static int fail(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return status;
+}
+
+static int cuda_fail(cudaError_t e, const char *where) {
+    return fail(PS_ERR_CUDA, "%s: CUDA error %d (%s)", where, (int)e, cudaGetErrorString(e));
+}
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+int sm_count() {
+    static int cache[64] = {0};
+    const int d = current_device();
+    if (d < 0 || d >= 64) return 148;
+    if (cache[d] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0)
+            v = 148;
+        cache[d] = v;
+    }
+    return cache[d];
+}
+
+static int elem_bytes(int dtype) { return dtype == PS_F64 ? 8 : 4; }
+
+static int check_dtype(int dtype) {
+    if (dtype != PS_F32 && dtype != PS_F64) return fail(PS_ERR_ARG, "dtype %d is not PS_F32/PS_F64", dtype);
+    return PS_OK;
+}
+
+static int check_grid(int64_t nx, int64_t ny, int64_t nz) {
+    if (nx < 3 || ny < 3 || nz < 3)
+        return fail(PS_ERR_ARG, "grid %lld x %lld x %lld: every size must be >= 3", (long long)nx,
+                    (long long)ny, (long long)nz);
+    if (nx > (1LL << 31) || ny > (1LL << 31) || nz > (1LL << 31) ||
+        (double)nx * (double)ny * (double)nz > 9.0e15)
+        return fail(PS_ERR_ARG, "grid %lld x %lld x %lld is too large", (long long)nx, (long long)ny,
+                    (long long)nz);
+    return PS_OK;
+}
+
+static int check_ptr(const void *p, const char *name) {
+    if (!p) return fail(PS_ERR_ARG, "%s is NULL", name);
+    if (((uintptr_t)p) & 15u) return fail(PS_ERR_ALIGN, "%s = %p is not 16-byte aligned", name, p);
+    return PS_OK;
+}
+
+static bool overlap(const void *a, const void *b, size_t bytes) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+static int check_finite(double v, const char *name) {
+    if (!std::isfinite(v)) return fail(PS_ERR_ARG, "%s is not finite", name);
+    return PS_OK;
+}
+
+#define PS_TRY(x)                    \
+    do {                             \
+        int _st = (x);               \
+        if (_st != PS_OK) return _st; \
+    } while (0)
+
+static int check_step_args(const void *T2, const void *T, const void *Ci, double lam, double dt,
+                           double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
+                           int dtype) {
+    PS_TRY(check_dtype(dtype));
+    PS_TRY(check_grid(nx, ny, nz));
+    PS_TRY(check_ptr(T2, "T2"));
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_ptr(Ci, "Ci"));
+    PS_TRY(check_finite(lam, "lam"));
+    PS_TRY(check_finite(dt, "dt"));
+    PS_TRY(check_finite(_dx, "_dx"));
+    PS_TRY(check_finite(_dy, "_dy"));
+    PS_TRY(check_finite(_dz, "_dz"));
+    const size_t bytes = (size_t)(nx * ny * nz) * elem_bytes(dtype);
+    if (overlap(T2, T, bytes)) return fail(PS_ERR_ALIAS, "T2 overlaps T");
+    if (overlap(T2, Ci, bytes)) return fail(PS_ERR_ALIAS, "T2 overlaps Ci");
+    return PS_OK;
+}
+
+static cudaError_t enqueue_step(void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
+                                Grid3 g, int dtype, unsigned flags, cudaStream_t s) {
+    if (dtype == PS_F64) {
+        if (flags & PS_RUN_NATIVE_F64)
+            return launch_step_f64_native((double *)T2, (const double *)T, (const double *)Ci, c, g, s);
+        return launch_step_f64_fast((double *)T2, (const double *)T, (const double *)Ci, c, g, s);
+    }
+    if (flags & PS_RUN_COMPENSATED)
+        return launch_step_f32_comp((float *)T2, (const float *)T, (float *)comp, (const float *)Ci,
+                                    c, g, s);
+    return launch_step_f32((float *)T2, (const float *)T, (const float *)Ci, c, g, s);
+}
+
+// Boundary copy followed by nt steps with alternating buffers.
+static cudaError_t enqueue_run(void *T, void *T2, void *comp, const void *Ci, StepCoef c, Grid3 g,
+                               int nt, int dtype, unsigned flags, cudaStream_t s) {
+    cudaError_t e = launch_copy_boundary(T2, T, g, elem_bytes(dtype), s);
+    for (int it = 0; it < nt && e == cudaSuccess; ++it) {
+        void *src = (it & 1) ? T2 : T;
+        void *dst = (it & 1) ? T : T2;
+        e = enqueue_step(dst, src, comp, Ci, c, g, dtype, flags, s);
+    }
+    return e;
+}
+
+// ---------------------------------------------------------------- graphs
+using GraphKey = std::tuple<int, const void *, const void *, const void *, const void *, double,
+                            double, double, double, double, int64_t, int64_t, int64_t, int, int,
+                            unsigned>;
+static std::mutex g_graph_mu;
+static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+static cudaStream_t g_capture_stream[64] = {nullptr};
+
+static cudaError_t capture_stream(cudaStream_t *out) {
+    const int d = current_device();
+    if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    if (!g_capture_stream[d]) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g_capture_stream[d], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    *out = g_capture_stream[d];
+    return cudaSuccess;
+}
+
+static int run_graph(void *T, void *T2, void *comp, const void *Ci, double lam, double dt,
+                     double _dx, double _dy, double _dz, Grid3 g, int nt, int dtype,
+                     unsigned flags, cudaStream_t s) {
+    const GraphKey key{current_device(), T, T2, comp, Ci, lam, dt, _dx, _dy, _dz, g.nx, g.ny, g.nz,
+                       nt, dtype, flags & ~PS_RUN_GRAPH};
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) {
+        cudaStream_t cs;
+        cudaError_t e = capture_stream(&cs);
+        if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        cudaError_t le = enqueue_run(T, T2, comp, Ci, make_coef(lam, dt, _dx, _dy, _dz), g, nt, dtype,
+                                     flags, cs);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(le, "capturing the time loop");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        it = g_graphs.emplace(key, exec).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return PS_OK;
+}
+
+}  // namespace psd
+
+using namespace psd;
+
+extern "C" {
+
+int ps_version(void) { return 100; }
+
+const char *ps_last_error(void) { return g_err.c_str(); }
+
+size_t ps_workspace_bytes(void) { return kWorkspaceBytes; }
+
+int ps_diffusion3d_step(void *T2, const void *T, const void *Ci, double lam, double dt, double _dx,
+                        double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                        void *stream) {
+    PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, dtype));
+    cudaError_t e = enqueue_step(T2, T, nullptr, Ci, make_coef(lam, dt, _dx, _dy, _dz),
+                                 Grid3{nx, ny, nz}, dtype, 0u, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_step");
+    return PS_OK;
+}
+
+int ps_diffusion3d_step_comp_f32(float *T2, const float *T, float *comp, const float *Ci,
+                                 double lam, double dt, double _dx, double _dy, double _dz,
+                                 int64_t nx, int64_t ny, int64_t nz, void *stream) {
+    PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, PS_F32));
+    PS_TRY(check_ptr(comp, "comp"));
+    const size_t bytes = (size_t)(nx * ny * nz) * 4;
+    if (overlap(comp, T, bytes) || overlap(comp, T2, bytes) || overlap(comp, Ci, bytes))
+        return fail(PS_ERR_ALIAS, "comp overlaps T, T2 or Ci");
+    cudaError_t e = launch_step_f32_comp(T2, T, comp, Ci, make_coef(lam, dt, _dx, _dy, _dz),
+                                         Grid3{nx, ny, nz}, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_step_comp_f32");
+    return PS_OK;
+}
+
+int ps_diffusion3d_copy_boundary(void *T2, const void *T, int64_t nx, int64_t ny, int64_t nz,
+                                 int dtype, void *stream) {
+    PS_TRY(check_dtype(dtype));
+    PS_TRY(check_grid(nx, ny, nz));
+    PS_TRY(check_ptr(T2, "T2"));
+    PS_TRY(check_ptr(T, "T"));
+    if (overlap(T2, T, (size_t)(nx * ny * nz) * elem_bytes(dtype))) return fail(PS_ERR_ALIAS, "T2 overlaps T");
+    cudaError_t e = launch_copy_boundary(T2, T, Grid3{nx, ny, nz}, elem_bytes(dtype), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_copy_boundary");
+    return PS_OK;
+}
+
+int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double lam, double dt,
+                          double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
+                          int nt, int dtype, unsigned flags, void *stream, int *result_in_T2) {
+    PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, dtype));
+    if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
+    if (flags & ~(PS_RUN_GRAPH | PS_RUN_COMPENSATED | PS_RUN_NATIVE_F64))
+        return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
+    if (flags & PS_RUN_COMPENSATED) {
+        if (dtype != PS_F32) return fail(PS_ERR_UNSUPPORTED, "PS_RUN_COMPENSATED needs PS_F32");
+        PS_TRY(check_ptr(comp, "comp"));
+        const size_t bytes = (size_t)(nx * ny * nz) * 4;
+        if (overlap(comp, T, bytes) || overlap(comp, T2, bytes) || overlap(comp, Ci, bytes))
+            return fail(PS_ERR_ALIAS, "comp overlaps T, T2 or Ci");
+    } else {
+        comp = nullptr;
+    }
+    if ((flags & PS_RUN_NATIVE_F64) && dtype != PS_F64)
+        return fail(PS_ERR_UNSUPPORTED, "PS_RUN_NATIVE_F64 needs PS_F64");
+    const Grid3 g{nx, ny, nz};
+    if (result_in_T2) *result_in_T2 = nt & 1;
+    if (flags & PS_RUN_GRAPH)
+        return run_graph(T, T2, comp, Ci, lam, dt, _dx, _dy, _dz, g, nt, dtype, flags,
+                         (cudaStream_t)stream);
+    cudaError_t e = enqueue_run(T, T2, comp, Ci, make_coef(lam, dt, _dx, _dy, _dz), g, nt, dtype,
+                                flags, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_run");
+    return PS_OK;
+}
+
+int ps_diffusion3d_run(void *T, void *T2, const void *Ci, double lam, double dt, double _dx,
+                       double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int nt, int dtype,
+                       void *stream, int *result_in_T2) {
+    return ps_diffusion3d_run_ex(T, T2, nullptr, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, nt, dtype,
+                                 0u, stream, result_in_T2);
+}
+
+int ps_clear_graph_cache(void) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto &kv : g_graphs) cudaGraphExecDestroy(kv.second);
+    g_graphs.clear();
+    return PS_OK;
+}
+
+int ps_diffusion3d_adjoint(void *Tbar, void *Cibar, const void *ybar, const void *T,
+                           const void *Ci, double lam, double dt, double _dx, double _dy,
+                           double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                           void *stream) {
+    PS_TRY(check_dtype(dtype));
+    PS_TRY(check_grid(nx, ny, nz));
+    PS_TRY(check_ptr(Tbar, "Tbar"));
+    PS_TRY(check_ptr(Cibar, "Cibar"));
+    PS_TRY(check_ptr(ybar, "ybar"));
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_ptr(Ci, "Ci"));
+    PS_TRY(check_finite(lam, "lam"));
+    PS_TRY(check_finite(dt, "dt"));
+    PS_TRY(check_finite(_dx, "_dx"));
+    PS_TRY(check_finite(_dy, "_dy"));
+    PS_TRY(check_finite(_dz, "_dz"));
+    const size_t bytes = (size_t)(nx * ny * nz) * elem_bytes(dtype);
+    if (overlap(Tbar, ybar, bytes) || overlap(Tbar, T, bytes) || overlap(Tbar, Ci, bytes) ||
+        overlap(Tbar, Cibar, bytes))
+        return fail(PS_ERR_ALIAS, "Tbar overlaps an input");
+    if (overlap(Cibar, ybar, bytes) || overlap(Cibar, T, bytes) || overlap(Cibar, Ci, bytes))
+        return fail(PS_ERR_ALIAS, "Cibar overlaps an input");
+    const StepCoef c = make_coef(lam, dt, _dx, _dy, _dz);
+    const Grid3 g{nx, ny, nz};
+    cudaError_t e;
+    if (dtype == PS_F64)
+        e = launch_adjoint_f64((double *)Tbar, (double *)Cibar, (const double *)ybar,
+                               (const double *)T, (const double *)Ci, c, g, (cudaStream_t)stream);
+    else
+        e = launch_adjoint_f32((float *)Tbar, (float *)Cibar, (const float *)ybar, (const float *)T,
+                               (const float *)Ci, c, g, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_adjoint");
+    return PS_OK;
+}
+
+static int check_reduce(const void *A, int64_t n, int dtype, const void *ws) {
+    PS_TRY(check_dtype(dtype));
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(A, "A"));
+    PS_TRY(check_ptr(ws, "workspace"));
+    return PS_OK;
+}
+
+int ps_maximum_async(double *out_dev, const void *A, int64_t n, int dtype, void *workspace,
+                     void *stream) {
+    PS_TRY(check_reduce(A, n, dtype, workspace));
+    if (!out_dev) return fail(PS_ERR_ARG, "out_dev is NULL");
+    cudaError_t e = launch_maximum(out_dev, A, n, dtype, workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_maximum");
+    return PS_OK;
+}
+
+int ps_maximum(double *out_host, const void *A, int64_t n, int dtype, void *workspace,
+               void *stream) {
+    if (!out_host) return fail(PS_ERR_ARG, "out_host is NULL");
+    PS_TRY(check_reduce(A, n, dtype, workspace));
+    double *slot = (double *)((char *)workspace + 8);  // scratch slot inside the workspace
+    cudaError_t e = launch_maximum(slot, A, n, dtype, workspace, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, slot, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_maximum");
+    return PS_OK;
+}
+
+int ps_diffusion3d_stable_dt(double *dt_host, const void *Ci, int64_t nx, int64_t ny, int64_t nz,
+                             double lam, double lx, double ly, double lz, int dtype,
+                             void *workspace, void *stream) {
+    if (!dt_host) return fail(PS_ERR_ARG, "dt_host is NULL");
+    PS_TRY(check_grid(nx, ny, nz));
+    PS_TRY(check_finite(lam, "lam"));
+    double mx = 0.0;
+    PS_TRY(ps_maximum(&mx, Ci, nx * ny * nz, dtype, workspace, stream));
+    const double dx = lx / (double)(nx - 1), dy = ly / (double)(ny - 1), dz = lz / (double)(nz - 1);
+    double m = dx * dx;
+    if (dy * dy < m) m = dy * dy;
+    if (dz * dz < m) m = dz * dz;
+    *dt_host = m / lam / mx / 6.1;
+    return PS_OK;
+}
+
+int ps_dot(double *out_dev, const void *A, const void *B, int64_t n, int dtype, void *workspace,
+           void *stream) {
+    PS_TRY(check_reduce(A, n, dtype, workspace));
+    PS_TRY(check_ptr(B, "B"));
+    if (!out_dev) return fail(PS_ERR_ARG, "out_dev is NULL");
+    cudaError_t e = launch_dot(out_dev, A, B, n, dtype, workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_dot");
+    return PS_OK;
+}
+
+int ps_half_sq_dist(double *out_dev, void *R, const void *A, const void *B, int64_t n, int dtype,
+                    void *workspace, void *stream) {
+    PS_TRY(check_reduce(A, n, dtype, workspace));
+    PS_TRY(check_ptr(B, "B"));
+    if (!out_dev) return fail(PS_ERR_ARG, "out_dev is NULL");
+    if (R) {
+        PS_TRY(check_ptr(R, "R"));
+        const size_t bytes = (size_t)n * elem_bytes(dtype);
+        if (overlap(R, A, bytes) || overlap(R, B, bytes)) return fail(PS_ERR_ALIAS, "R overlaps A or B");
+    }
+    cudaError_t e = launch_half_sq_dist(out_dev, R, A, B, n, dtype, workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_half_sq_dist");
+    return PS_OK;
+}
+
+int ps_to_deviation(float *D, const double *T, double t_ref, int64_t n, void *stream) {
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(D, "D"));
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_finite(t_ref, "t_ref"));
+    if (overlap(D, T, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "D overlaps T");
+    cudaError_t e = launch_to_deviation(D, T, t_ref, n, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_to_deviation");
+    return PS_OK;
+}
+
+int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *stream) {
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(D, "D"));
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_finite(t_ref, "t_ref"));
+    if (overlap(D, T, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "T overlaps D");
+    cudaError_t e = launch_from_deviation(T, D, t_ref, n, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_from_deviation");
+    return PS_OK;
+}
+
+// ------------------------------------------------------------------ batch
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static int resolve_tiles(int dtype, int *tx, int *ty, int *tz) {
+    int dx, dy, dz;
+    batch_default_tile(dtype, &dx, &dy, &dz);
+    if (*tx == 0) *tx = dx;
+    if (*ty == 0) *ty = dy;
+    if (*tz == 0) *tz = dz;
+    if (*tx < 1 || *ty < 1 || *tz < 1 || (int64_t)*tx * *ty > (1 << 16))
+        return fail(PS_ERR_ARG, "tile %d x %d x %d is invalid", *tx, *ty, *tz);
+    return PS_OK;
+}
+
+static int64_t items_of(const ps_problem &p, int tx, int ty, int tz) {
+    return ((p.nx - 2 + tx - 1) / tx) * ((p.ny - 2 + ty - 1) / ty) * ((p.nz - 2 + tz - 1) / tz);
+}
+
+static size_t table_bytes(int nprob, int64_t nitems) {
+    return align_up(sizeof(BatchHeader), 64) + align_up(sizeof(BatchProblem) * (size_t)nprob, 64) +
+           sizeof(BatchItem) * (size_t)nitems;
+}
+
+size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
+                            int tile_z) {
+    if (!probs || nprob < 1 || check_dtype(dtype) != PS_OK) return 0;
+    if (resolve_tiles(dtype, &tile_x, &tile_y, &tile_z) != PS_OK) return 0;
+    int64_t nitems = 0;
+    for (int q = 0; q < nprob; ++q) {
+        if (probs[q].nx < 3 || probs[q].ny < 3 || probs[q].nz < 3) return 0;
+        nitems += items_of(probs[q], tile_x, tile_y, tile_z);
+    }
+    return table_bytes(nprob, nitems);
+}
+
+int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, int nprob, int dtype,
+                        int tile_x, int tile_y, int tile_z, int64_t *nitems_out) {
+    if (!host_buf || !probs) return fail(PS_ERR_ARG, "host_buf or probs is NULL");
+    if (nprob < 1) return fail(PS_ERR_ARG, "nprob = %d < 1", nprob);
+    PS_TRY(check_dtype(dtype));
+    PS_TRY(resolve_tiles(dtype, &tile_x, &tile_y, &tile_z));
+    int64_t nitems = 0;
+    for (int q = 0; q < nprob; ++q) {
+        const ps_problem &p = probs[q];
+        int st = check_step_args(p.T2, p.T, p.Ci, p.lam, p.dt, p._dx, p._dy, p._dz, p.nx, p.ny, p.nz, dtype);
+        if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
+        if (p.nx - 2 + tile_x > (1LL << 31) || p.ny - 2 + tile_y > (1LL << 31) || p.nz - 2 + tile_z > (1LL << 31))
+            return fail(PS_ERR_ARG, "problem %d is too large for the batch table", q);
+        nitems += items_of(p, tile_x, tile_y, tile_z);
+    }
+    const size_t need = table_bytes(nprob, nitems);
+    if (bytes < need) return fail(PS_ERR_ARG, "table buffer has %zu bytes, needs %zu", bytes, need);
+    std::memset(host_buf, 0, need);
+    char *base = (char *)host_buf;
+    BatchHeader *h = (BatchHeader *)base;
+    h->nprob = nprob;
+    h->nitems = nitems;
+    h->dtype = dtype;
+    h->tile_x = tile_x;
+    h->tile_y = tile_y;
+    h->tile_z = tile_z;
+    h->problems_offset = (int64_t)align_up(sizeof(BatchHeader), 64);
+    h->items_offset = h->problems_offset + (int64_t)align_up(sizeof(BatchProblem) * (size_t)nprob, 64);
+    BatchProblem *bp = (BatchProblem *)(base + h->problems_offset);
+    std::vector<std::pair<int64_t, BatchItem>> work;
+    work.reserve((size_t)nitems);
+    for (int q = 0; q < nprob; ++q) {
+        const ps_problem &p = probs[q];
+        const StepCoef c = make_coef(p.lam, p.dt, p._dx, p._dy, p._dz);
+        bp[q] = BatchProblem{p.T, p.T2, p.Ci, c.dtlam, c.ax, c.ay, c.az, p.nx, p.ny, p.nz};
+        for (int64_t k0 = 1; k0 < p.nz - 1; k0 += tile_z)
+            for (int64_t j0 = 1; j0 < p.ny - 1; j0 += tile_y)
+                for (int64_t i0 = 1; i0 < p.nx - 1; i0 += tile_x) {
+                    const int64_t w = std::min<int64_t>(tile_x, p.nx - 1 - i0) *
+                                      std::min<int64_t>(tile_y, p.ny - 1 - j0) *
+                                      std::min<int64_t>(tile_z, p.nz - 1 - k0);
+                    work.push_back({w, BatchItem{q, (int32_t)i0, (int32_t)j0, (int32_t)k0}});
+                }
+    }
+    // largest items first: the round-robin hand-out then stays balanced
+    std::stable_sort(work.begin(), work.end(),
+                     [](const std::pair<int64_t, BatchItem> &a, const std::pair<int64_t, BatchItem> &b) {
+                         return a.first > b.first;
+                     });
+    BatchItem *items = (BatchItem *)(base + h->items_offset);
+    for (size_t t = 0; t < work.size(); ++t) items[t] = work[t].second;
+    if (nitems_out) *nitems_out = nitems;
+    return PS_OK;
+}
+
+int ps_diffusion3d_batch_step(const void *dev_table, int parity, int dtype, void *stream) {
+    if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
+    PS_TRY(check_dtype(dtype));
+    if (parity != 0 && parity != 1) return fail(PS_ERR_ARG, "parity %d is not 0 or 1", parity);
+    cudaError_t e = launch_batch_step(dev_table, parity, dtype, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_batch_step");
+    return PS_OK;
+}
+
+int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned flags,
+                             void *stream) {
+    if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
+    PS_TRY(check_dtype(dtype));
+    if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
+    if (flags & ~PS_RUN_GRAPH) return fail(PS_ERR_ARG, "unsupported flags 0x%x", flags);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!(flags & PS_RUN_GRAPH)) {
+        for (int it = 0; it < nt; ++it) {
+            cudaError_t e = launch_batch_step(dev_table, it & 1, dtype, s);
+            if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_batch_run");
+        }
+        return PS_OK;
+    }
+    const GraphKey key{current_device(), dev_table, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0,
+                       0.0, -1, -1, -1, nt, dtype, 0x80000000u};
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) {
+        cudaStream_t cs;
+        cudaError_t e = capture_stream(&cs);
+        if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        cudaError_t le = cudaSuccess;
+        for (int t = 0; t < nt && le == cudaSuccess; ++t) le = launch_batch_step(dev_table, t & 1, dtype, cs);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(le, "capturing the batch loop");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        it = g_graphs.emplace(key, exec).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return PS_OK;
+}
+
+}  // extern "C"

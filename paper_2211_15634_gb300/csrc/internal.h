@@ -1,0 +1,83 @@
+// Internal declarations shared by the library's translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "ps_diffusion3d.h"
+
+namespace psd {
+
+// Coefficients of one step, precomputed on the host in FP64 from the
+// paper's arguments: dtlam = dt*lam and a_d = _d*_d (Fig. 1's _dx^2 ...).
+struct StepCoef {
+    double dtlam, ax, ay, az;
+};
+
+inline StepCoef make_coef(double lam, double dt, double _dx, double _dy, double _dz) {
+    return StepCoef{dt * lam, _dx * _dx, _dy * _dy, _dz * _dz};
+}
+
+struct Grid3 {
+    int64_t nx, ny, nz;
+    int64_t n() const { return nx * ny * nz; }
+};
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+int current_device();
+
+// ---- forward step kernels (step_f64.cu, step_f32.cu) ----
+cudaError_t launch_step_f64_native(double *T2, const double *T, const double *Ci, StepCoef c,
+                                   Grid3 g, cudaStream_t s);
+cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, StepCoef c,
+                                 Grid3 g, cudaStream_t s);
+cudaError_t launch_step_f32(float *T2, const float *T, const float *Ci, StepCoef c, Grid3 g,
+                            cudaStream_t s);
+cudaError_t launch_step_f32_comp(float *T2, const float *T, float *comp, const float *Ci,
+                                 StepCoef c, Grid3 g, cudaStream_t s);
+
+// ---- helpers (misc.cu) ----
+cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);
+cudaError_t launch_to_deviation(float *D, const double *T, double t_ref, int64_t n, cudaStream_t s);
+cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64_t n,
+                                  cudaStream_t s);
+
+// ---- adjoint (adjoint.cu) ----
+cudaError_t launch_adjoint_f64(double *Tbar, double *Cibar, const double *ybar, const double *T,
+                               const double *Ci, StepCoef c, Grid3 g, cudaStream_t s);
+cudaError_t launch_adjoint_f32(float *Tbar, float *Cibar, const float *ybar, const float *T,
+                               const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
+
+// ---- reductions (reduce.cu) ----
+constexpr int kReduceBlocks = 1024;           // fixed partition => deterministic sums
+constexpr size_t kWorkspaceBytes = 16384;     // >= kReduceBlocks doubles + one key
+cudaError_t launch_maximum(double *out_dev, const void *A, int64_t n, int dtype, void *ws,
+                           cudaStream_t s);
+cudaError_t launch_dot(double *out_dev, const void *A, const void *B, int64_t n, int dtype,
+                       void *ws, cudaStream_t s);
+cudaError_t launch_half_sq_dist(double *out_dev, void *R, const void *A, const void *B, int64_t n,
+                                int dtype, void *ws, cudaStream_t s);
+
+// ---- batch (batch.cu) ----
+struct BatchHeader {
+    int64_t nprob, nitems;
+    int32_t dtype, tile_x, tile_y, tile_z;
+    int64_t problems_offset, items_offset;  // byte offsets from the table start
+};
+struct BatchProblem {
+    void *T;
+    void *T2;
+    const void *Ci;
+    double dtlam, ax, ay, az;
+    int64_t nx, ny, nz;
+};
+struct BatchItem {
+    int32_t prob;
+    int32_t i0, j0, k0;  // first interior node of the work item (1-based interior coordinates)
+};
+cudaError_t launch_batch_step(const void *dev_table, int parity, int dtype, cudaStream_t s);
+int batch_default_tile(int dtype, int *tx, int *ty, int *tz);
+
+}  // namespace psd

@@ -1,0 +1,82 @@
+// Boundary copy (Fig. 1's T2 = copy(T), restricted to the boundary faces)
+// and the FP32 deviation conversions.
+#include "internal.h"
+
+namespace psd {
+
+// blockIdx.y selects the face: 0/1 z = 0 / nz-1, 2/3 y = 0 / ny-1, 4/5 x = 0 / nx-1.
+// Edges and corners belong to several faces and are written with the same
+// value more than once.
+template <typename E>
+__global__ void k_copy_boundary(E *__restrict__ dst, const E *__restrict__ src, int64_t nx,
+                                int64_t ny, int64_t nz) {
+    const int face = blockIdx.y;
+    const int64_t count = face < 2 ? nx * ny : (face < 4 ? nx * nz : ny * nz);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+        int64_t p;
+        if (face < 2) {
+            const int64_t k = face == 0 ? 0 : nz - 1;
+            p = t + nx * ny * k;
+        } else if (face < 4) {
+            const int64_t j = face == 2 ? 0 : ny - 1;
+            const int64_t i = t % nx, k = t / nx;
+            p = i + nx * (j + ny * k);
+        } else {
+            const int64_t i = face == 4 ? 0 : nx - 1;
+            const int64_t j = t % ny, k = t / ny;
+            p = i + nx * (j + ny * k);
+        }
+        dst[p] = src[p];
+    }
+}
+
+cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes,
+                                 cudaStream_t s) {
+    const int64_t maxface = g.nx * g.ny > g.nx * g.nz ? g.nx * g.ny : g.nx * g.nz;
+    const int64_t mf = maxface > g.ny * g.nz ? maxface : g.ny * g.nz;
+    int64_t blocks = (mf + 255) / 256;
+    if (blocks > 4LL * sm_count()) blocks = 4LL * sm_count();
+    const dim3 grid((unsigned)blocks, 6, 1);
+    if (elem_bytes == 8)
+        k_copy_boundary<unsigned long long><<<grid, 256, 0, s>>>(
+            (unsigned long long *)T2, (const unsigned long long *)T, g.nx, g.ny, g.nz);
+    else
+        k_copy_boundary<unsigned><<<grid, 256, 0, s>>>((unsigned *)T2, (const unsigned *)T, g.nx,
+                                                      g.ny, g.nz);
+    return cudaGetLastError();
+}
+
+__global__ void k_to_deviation(float *__restrict__ D, const double *__restrict__ T, double t_ref,
+                               int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        D[p] = __double2float_rn(T[p] - t_ref);
+}
+
+__global__ void k_from_deviation(double *__restrict__ T, const float *__restrict__ D, double t_ref,
+                                 int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        T[p] = (double)D[p] + t_ref;
+}
+
+static unsigned ew_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = 8LL * sm_count();
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+cudaError_t launch_to_deviation(float *D, const double *T, double t_ref, int64_t n,
+                                cudaStream_t s) {
+    k_to_deviation<<<ew_blocks(n), 256, 0, s>>>(D, T, t_ref, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64_t n,
+                                  cudaStream_t s) {
+    k_from_deviation<<<ew_blocks(n), 256, 0, s>>>(T, D, t_ref, n);
+    return cudaGetLastError();
+}
+
+}  // namespace psd

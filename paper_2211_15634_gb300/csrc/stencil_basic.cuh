@@ -1,0 +1,70 @@
+// Plain 7-point step kernels: one thread per interior (i, j) column,
+// marching along z with a three-value register queue.  x/y neighbours are
+// read through the L1/L2 caches.  These are the straightforward kernels
+// (FP64 instructions for FP64 data); the tiled kernels replace them on the
+// hot path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace psd {
+
+template <typename F>
+struct CoefT {
+    F dtlam, ax, ay, az;
+};
+
+// Fig. 1 step!: T2 = T + dt*lam*Ci*((d2x*_dx^2 + d2y*_dy^2) + d2z*_dz^2) at
+// interior nodes; the z-range of this block is [k0, k1).
+template <typename F, bool kComp>
+__global__ void __launch_bounds__(256)
+k_step_basic(F *__restrict__ T2, const F *__restrict__ T, F *__restrict__ comp,
+             const F *__restrict__ Ci, CoefT<F> c, int64_t nx, int64_t ny, int64_t nz, int kchunk) {
+    const int64_t i = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = 1 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > nx - 2 || j > ny - 2) return;
+    const int64_t k0 = 1 + (int64_t)blockIdx.z * kchunk;
+    const int64_t k1 = k0 + kchunk < nz - 1 ? k0 + kchunk : nz - 1;
+    if (k0 >= k1) return;
+    const int64_t sy = nx, sz = nx * ny;
+    int64_t p = i + sy * (j + ny * k0);
+    F tm = T[p - sz], tc = T[p];
+    for (int64_t k = k0; k < k1; ++k, p += sz) {
+        const F tp = T[p + sz];
+        const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
+        const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
+        const F d2z = (tp - tc) - (tc - tm);
+        const F lap = (d2x * c.ax + d2y * c.ay) + d2z * c.az;
+        if (kComp) {
+            // compensated update: y = delta - c; t = D + y; c = (t - D) - y; D = t
+            const F delta = c.dtlam * (Ci[p] * lap);
+            const F y = delta - comp[p];
+            const F t = tc + y;
+            comp[p] = (t - tc) - y;
+            T2[p] = t;
+        } else {
+            T2[p] = tc + c.dtlam * (Ci[p] * lap);
+        }
+        tm = tc;
+        tc = tp;
+    }
+}
+
+template <typename F, bool kComp>
+cudaError_t launch_step_basic(F *T2, const F *T, F *comp, const F *Ci, CoefT<F> c, int64_t nx,
+                              int64_t ny, int64_t nz, int nsm, cudaStream_t s) {
+    const dim3 block(32, 8, 1);
+    const int64_t gx = (nx - 2 + block.x - 1) / block.x, gy = (ny - 2 + block.y - 1) / block.y;
+    // enough z-chunks for about 8 blocks per SM, each chunk at least 16 planes
+    int64_t want = (8LL * nsm + gx * gy - 1) / (gx * gy);
+    int64_t kchunk = (nz - 2 + want - 1) / want;
+    if (kchunk < 16) kchunk = 16;
+    const int64_t gz = (nz - 2 + kchunk - 1) / kchunk;
+    if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return cudaErrorInvalidConfiguration;
+    k_step_basic<F, kComp><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), block, 0, s>>>(
+        T2, T, comp, Ci, c, nx, ny, nz, (int)kchunk);
+    return cudaGetLastError();
+}
+
+}  // namespace psd

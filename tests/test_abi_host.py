@@ -1,0 +1,167 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+declared in include/*.h, and rejects bad arguments on the host before any
+launch (fake device addresses are never dereferenced)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2211_15634_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(ps_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("ps_diffusion3d_step", "ps_diffusion3d_run", "ps_diffusion3d_adjoint",
+                 "ps_diffusion3d_batch_step", "ps_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    assert set(_lib.SIGNATURES) >= set(declared_functions())
+
+
+def test_version_and_workspace(lib):
+    assert lib.ps_version() >= 100
+    assert lib.ps_workspace_bytes() >= 8 * 1024 + 64
+
+
+A = 0x10000       # fake, 16-byte aligned device addresses (never dereferenced)
+B = 0x90000000
+C = 0x190000000
+
+
+def step(lib, T2=B, T=A, Ci=C, n=(8, 8, 8), dtype=_lib.PS_F64, dt=1e-3):
+    return lib.ps_diffusion3d_step(T2, T, Ci, 1.0, dt, 7.0, 7.0, 7.0, *n, dtype, None)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(T2=None), _lib.PS_ERR_ARG),
+    (dict(T=None), _lib.PS_ERR_ARG),
+    (dict(Ci=None), _lib.PS_ERR_ARG),
+    (dict(n=(2, 8, 8)), _lib.PS_ERR_ARG),
+    (dict(n=(8, 8, 0)), _lib.PS_ERR_ARG),
+    (dict(dtype=7), _lib.PS_ERR_ARG),
+    (dict(dt=float("nan")), _lib.PS_ERR_ARG),
+    (dict(T2=A), _lib.PS_ERR_ALIAS),
+    (dict(T2=A + 16), _lib.PS_ERR_ALIAS),
+    (dict(T2=C), _lib.PS_ERR_ALIAS),
+    (dict(T=A + 8), _lib.PS_ERR_ALIGN),
+])
+def test_step_rejects_bad_arguments(lib, kw, status):
+    assert step(lib, **kw) == status
+    assert len(lib.ps_last_error()) > 0
+
+
+def test_last_error_names_the_argument(lib):
+    assert step(lib, Ci=None) == _lib.PS_ERR_ARG
+    assert b"Ci" in lib.ps_last_error()
+    assert step(lib, n=(8, 1, 8)) == _lib.PS_ERR_ARG
+    assert b">= 3" in lib.ps_last_error()
+
+
+def test_run_and_adjoint_reject_bad_arguments(lib):
+    odd = ctypes.c_int(-1)
+    assert lib.ps_diffusion3d_run(A, B, C, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8, -1, _lib.PS_F64, None,
+                                  ctypes.byref(odd)) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_run_ex(A, B, None, C, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8, 3, _lib.PS_F64,
+                                     _lib.PS_RUN_COMPENSATED, None, ctypes.byref(odd)) == _lib.PS_ERR_UNSUPPORTED
+    assert lib.ps_diffusion3d_run_ex(A, B, None, C, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8, 3, _lib.PS_F32,
+                                     _lib.PS_RUN_COMPENSATED, None, ctypes.byref(odd)) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_run_ex(A, B, None, C, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8, 3, _lib.PS_F64,
+                                     0x100, None, ctypes.byref(odd)) == _lib.PS_ERR_ARG
+    D, E = 0x290000000, 0x390000000
+    # Tbar overlapping ybar, Cibar overlapping T
+    assert lib.ps_diffusion3d_adjoint(A, B, A, C, D, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8,
+                                      _lib.PS_F64, None) == _lib.PS_ERR_ALIAS
+    assert lib.ps_diffusion3d_adjoint(E, C, A, C, D, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8,
+                                      _lib.PS_F64, None) == _lib.PS_ERR_ALIAS
+    assert lib.ps_diffusion3d_adjoint(E, B, A, C, None, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8,
+                                      _lib.PS_F64, None) == _lib.PS_ERR_ARG
+
+
+def test_reductions_reject_bad_arguments(lib):
+    v = ctypes.c_double(0)
+    assert lib.ps_maximum(ctypes.byref(v), A, 0, _lib.PS_F64, B, None) == _lib.PS_ERR_ARG
+    assert lib.ps_maximum(ctypes.byref(v), A, 10, _lib.PS_F64, None, None) == _lib.PS_ERR_ARG
+    assert lib.ps_maximum(None, A, 10, _lib.PS_F64, B, None) == _lib.PS_ERR_ARG
+    assert lib.ps_dot(None, A, B, 10, _lib.PS_F64, C, None) == _lib.PS_ERR_ARG
+    assert lib.ps_half_sq_dist(C, A, A, B, 10, _lib.PS_F64, C + 4096, None) == _lib.PS_ERR_ALIAS
+    assert lib.ps_diffusion3d_batch_step(None, 0, _lib.PS_F64, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_batch_step(A, 2, _lib.PS_F64, None) == _lib.PS_ERR_ARG
+
+
+def make_problems(sizes, base=0x100000000):
+    arr = (_lib.PsProblem * len(sizes))()
+    addr = base
+    for q, n in enumerate(sizes):
+        nbytes = (n ** 3 * 8 + 4095) // 4096 * 4096
+        T, T2, Ci = addr, addr + nbytes, addr + 2 * nbytes
+        addr += 3 * nbytes
+        arr[q] = _lib.PsProblem(T, T2, Ci, 1.0, 1e-4, n - 1.0, n - 1.0, n - 1.0, n, n, n)
+    return arr
+
+
+def test_batch_table_layout(lib):
+    """The table lists every interior node exactly once, largest items first."""
+    import numpy as np
+    sizes = [5, 33, 17, 40]
+    arr = make_problems(sizes)
+    tx, ty, tz = 8, 4, 6
+    nbytes = lib.ps_batch_table_bytes(arr, len(sizes), _lib.PS_F64, tx, ty, tz)
+    assert nbytes > 0
+    buf = (ctypes.c_char * nbytes)()
+    nitems = ctypes.c_int64(0)
+    assert lib.ps_batch_table_fill(buf, nbytes, arr, len(sizes), _lib.PS_F64, tx, ty, tz,
+                                   ctypes.byref(nitems)) == _lib.PS_OK
+    raw = bytes(buf)
+    nprob, nit = np.frombuffer(raw[:16], dtype=np.int64)
+    dtype, ttx, tty, ttz = np.frombuffer(raw[16:32], dtype=np.int32)
+    poff, ioff = np.frombuffer(raw[32:48], dtype=np.int64)
+    assert (nprob, nit, dtype, ttx, tty, ttz) == (4, nitems.value, _lib.PS_F64, tx, ty, tz)
+    items = np.frombuffer(raw[ioff:ioff + 16 * nit], dtype=np.int32).reshape(-1, 4)
+    covered = {q: np.zeros((n, n, n), dtype=np.int32) for q, n in enumerate(sizes)}
+    works = []
+    for q, i0, j0, k0 in items:
+        n = sizes[q]
+        i1, j1, k1 = min(i0 + tx, n - 1), min(j0 + ty, n - 1), min(k0 + tz, n - 1)
+        covered[q][k0:k1, j0:j1, i0:i1] += 1
+        works.append((i1 - i0) * (j1 - j0) * (k1 - k0))
+    for q, n in enumerate(sizes):
+        inner = covered[q][1:-1, 1:-1, 1:-1]
+        assert inner.min() == 1 and inner.max() == 1
+        assert covered[q].sum() == (n - 2) ** 3
+    assert works == sorted(works, reverse=True)
+    # problem records carry the pointers and step coefficients
+    rec = np.frombuffer(raw[poff:poff + 80], dtype=np.uint64)
+    assert int(rec[0]) == arr[0].T and int(rec[1]) == arr[0].T2 and int(rec[2]) == arr[0].Ci
+
+
+def test_batch_table_rejects_bad_problem(lib):
+    arr = make_problems([8, 9])
+    arr[1].T2 = arr[1].T  # aliasing inside one problem
+    nbytes = lib.ps_batch_table_bytes(arr, 2, _lib.PS_F64, 0, 0, 0)
+    buf = (ctypes.c_char * nbytes)()
+    assert lib.ps_batch_table_fill(buf, nbytes, arr, 2, _lib.PS_F64, 0, 0, 0, None) == _lib.PS_ERR_ALIAS
+    assert b"problem 1" in lib.ps_last_error()
+    arr = make_problems([8])
+    assert lib.ps_batch_table_fill(buf, 16, arr, 1, _lib.PS_F64, 0, 0, 0, None) == _lib.PS_ERR_ARG

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+* FP64: relative L-inf <= 1e-12 after nt steps (measured against max|T_ref|).
+* FP32 (deviation storage): |D_gpu - D_ref| <= nt * 13 * 2^-24 * max|D0|, the
+  worst-case bound of one FP32 rounding of D + delta plus about six roundings
+  inside delta (|delta| <= 2 max|D| for a stable dt) per step, with errors
+  carried forward without growth by the contractive step.  The reference is
+  the FP64 oracle run on the FP32-rounded Ci and D0, so the bound covers the
+  arithmetic only; storage rounding is reported separately by the benchmark.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import light_cone_reference, problem, rel_linf, to_dev, to_host
+from paper_2211_15634_gb300 import api, inputs
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+U32 = 2.0 ** -24
+FP64_TOL = 1e-12
+
+
+def f32_tol(nt, D0):
+    return nt * 13 * U32 * float(np.max(np.abs(D0)))
+
+
+def gpu_run(T0, Ci, lam, dt, inv, nt, dtype=torch.float64, **kw):
+    T = to_dev(T0, dtype)
+    T2 = torch.empty_like(T)
+    C = to_dev(Ci, dtype)
+    res = api.run(T, T2, C, lam, dt, inv, nt, **kw)
+    return to_host(res)
+
+
+SHAPES = [(3, 3, 3), (4, 3, 5), (5, 6, 7), (37, 29, 23), (66, 19, 20), (130, 67, 33), (257, 9, 12)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("nt", [1, 2, 9])
+def test_fp64_run_matches_oracle(shape, nt):
+    nx, ny, nz = shape
+    T0, Ci, lam, dt, inv = problem(nx, ny, nz, gaussian=False)
+    ref = oracle.run(T0, Ci, lam, dt, *inv, nt)
+    got = gpu_run(T0, Ci, lam, dt, inv, nt)
+    assert rel_linf(got, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("shape", [(37, 29, 23), (130, 67, 33)])
+def test_fp64_native_kernel_matches_oracle(shape):
+    nx, ny, nz = shape
+    T0, Ci, lam, dt, inv = problem(nx, ny, nz)
+    ref = oracle.run(T0, Ci, lam, dt, *inv, 20)
+    got = gpu_run(T0, Ci, lam, dt, inv, 20, native_f64=True)
+    assert rel_linf(got, ref) <= FP64_TOL
+
+
+def test_fp64_step_leaves_boundary_untouched():
+    nx, ny, nz = 21, 18, 13
+    T0, Ci, lam, dt, inv = problem(nx, ny, nz)
+    T = to_dev(T0)
+    T2 = torch.full_like(T, float("nan"))
+    api.step(T2, T, to_dev(Ci), lam, dt, inv)
+    out = to_host(T2)
+    inner = np.zeros(T0.shape, dtype=bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    assert np.all(np.isnan(out[~inner])) and np.all(np.isfinite(out[inner]))
+    ref = T0.copy()
+    oracle.step(ref, T0, Ci, lam, dt, *inv)
+    assert rel_linf(out[inner], ref[inner]) <= 1e-15
+
+
+def test_constant_field_stays_bitwise_fp64_and_fp32():
+    nx, ny, nz = 67, 35, 19
+    _, Ci, lam, dt, inv = problem(nx, ny, nz)
+    T0 = np.full((nz, ny, nx), 1.7)
+    assert np.all(gpu_run(T0, Ci, lam, dt, inv, 7) == 1.7)
+    D0 = np.zeros((nz, ny, nx))  # deviation of the constant field
+    assert np.all(gpu_run(D0, Ci, lam, dt, inv, 7, dtype=torch.float32) == 0.0)
+
+
+@pytest.mark.parametrize("shape,k", [((33, 20, 17), (1, 2, 1)), ((64, 64, 64), (2, 1, 3))])
+def test_eigenmode_decay_on_gpu(shape, k):
+    nx, ny, nz = shape
+    lam, Ci0, nt = 1.0, 0.5, 40
+    dx, dy, dz = inputs.spacing(nx, ny, nz)
+    s = [np.sin(kd * np.pi * np.arange(n) * d) for kd, n, d in zip(k, (nx, ny, nz), (dx, dy, dz))]
+    mode = s[2][:, None, None] * s[1][None, :, None] * s[0][None, None, :]
+    mode[[0, -1], :, :] = 0.0
+    mode[:, [0, -1], :] = 0.0
+    mode[:, :, [0, -1]] = 0.0
+    T0 = 1.7 + mode
+    Ci = np.full(T0.shape, Ci0)
+    dt = min(dx * dx, dy * dy, dz * dz) / lam / Ci0 / 6.1
+    g = 1.0 - dt * lam * Ci0 * sum(4.0 / d ** 2 * np.sin(kd * np.pi * d / 2) ** 2
+                                    for kd, d in zip(k, (dx, dy, dz)))
+    got = gpu_run(T0, Ci, lam, dt, (1 / dx, 1 / dy, 1 / dz), nt)
+    assert np.max(np.abs(got - (1.7 + g ** nt * mode))) <= 1e-13 * 2.7
+
+
+def test_run_graph_equals_plain_run_bitwise():
+    nx, ny, nz = 70, 41, 29
+    T0, Ci, lam, dt, inv = problem(nx, ny, nz)
+    a = gpu_run(T0, Ci, lam, dt, inv, 11)
+    b = gpu_run(T0, Ci, lam, dt, inv, 11, graph=True)
+    c = gpu_run(T0, Ci, lam, dt, inv, 11, graph=True)  # cached graph replay
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    api.clear_graph_cache()
+
+
+def test_run_nt0_returns_input():
+    T0, Ci, lam, dt, inv = problem(9, 8, 7)
+    assert np.array_equal(gpu_run(T0, Ci, lam, dt, inv, 0), T0)
+
+
+# --------------------------------------------------------------------- FP32
+@pytest.mark.parametrize("shape", [(5, 6, 7), (37, 29, 23), (130, 67, 33)])
+@pytest.mark.parametrize("comp", [False, True])
+def test_fp32_run_matches_oracle(shape, comp):
+    nx, ny, nz = shape
+    nt = 20
+    T0, Ci, lam, dt, inv = problem(nx, ny, nz)
+    D0 = (T0 - 1.7).astype(np.float32).astype(np.float64)
+    Ci32 = Ci.astype(np.float32).astype(np.float64)
+    ref = oracle.run(D0, Ci32, lam, dt, *inv, nt)
+    D = to_dev(D0, torch.float32)
+    D2 = torch.empty_like(D)
+    C = to_dev(Ci32, torch.float32)
+    cbuf = torch.zeros_like(D) if comp else None
+    got = to_host(api.run(D, D2, C, lam, dt, inv, nt, comp=cbuf))
+    assert np.max(np.abs(got - ref)) <= f32_tol(nt, D0)
+
+
+def test_deviation_roundtrip():
+    T0, *_ = problem(31, 17, 9)
+    T = to_dev(T0)
+    D = api.to_deviation(T, 1.7)
+    assert np.array_equal(to_host(D), (T0 - 1.7).astype(np.float32).astype(np.float64))
+    back = to_host(api.from_deviation(D, 1.7))
+    assert np.array_equal(back, (T0 - 1.7).astype(np.float32).astype(np.float64) + 1.7)
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 7, 6), (37, 29, 23), (66, 19, 20)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_adjoint_step_matches_oracle(shape, dtype):
+    nx, ny, nz = shape
+    T, Ci, lam, dt, inv = problem(nx, ny, nz, gaussian=False)
+    ybar = inputs.random_field(T.shape, 5)
+    cib0 = inputs.random_field(T.shape, 6)
+    if dtype == torch.float32:
+        T, Ci, ybar, cib0 = (a.astype(np.float32).astype(np.float64) for a in (T, Ci, ybar, cib0))
+    cib_ref = cib0.copy()
+    tbar_ref = oracle.adjoint_step(ybar, T, Ci, cib_ref, lam, dt, *inv)
+    Tbar = torch.empty(T.shape, dtype=dtype, device="cuda")
+    Cib = to_dev(cib0, dtype)
+    api.adjoint(Tbar, Cib, to_dev(ybar, dtype), to_dev(T, dtype), to_dev(Ci, dtype), lam, dt, inv)
+    tol = 1e-14 if dtype == torch.float64 else 2e-6
+    assert rel_linf(to_host(Tbar), tbar_ref) <= tol
+    assert np.max(np.abs(to_host(Cib) - cib_ref)) <= tol * np.max(np.abs(cib_ref))
+
+
+def test_gpu_adjoint_dot_product():
+    nx, ny, nz = 45, 33, 27
+    _, Ci, lam, dt, inv = problem(nx, ny, nz)
+    x = inputs.random_field((nz, ny, nx), 11)
+    y = inputs.random_field((nz, ny, nx), 12)
+    xd, yd, Cd = to_dev(x), to_dev(y), to_dev(Ci)
+    Mx = xd.clone()
+    api.step(Mx, xd, Cd, lam, dt, inv)
+    MTy = torch.empty_like(yd)
+    api.adjoint(MTy, torch.zeros_like(yd), yd, xd, Cd, lam, dt, inv)
+    lhs = float(api.dot(Mx, yd))
+    rhs = float(api.dot(xd, MTy))
+    assert abs(lhs - rhs) <= 1e-14 * float(torch.linalg.norm(Mx) * torch.linalg.norm(yd))
+
+
+# --------------------------------------------------------------- reductions
+@pytest.mark.parametrize("n", [1, 7, 1000, 1234567])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_reductions(n, dtype):
+    a = inputs.random_field((n,), 3, -2.0, 1.0)
+    b = inputs.random_field((n,), 4, -1.0, 3.0)
+    if dtype == torch.float32:
+        a, b = a.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+    A, B = to_dev(a, dtype), to_dev(b, dtype)
+    assert api.maximum(A) == a.max()
+    assert float(api.maximum_async(A)) == a.max()
+    assert abs(float(api.dot(A, B)) - float(np.dot(a, b))) <= 1e-13 * float(np.dot(np.abs(a), np.abs(b)))
+    R = torch.empty_like(A)
+    L = float(api.half_sq_dist(A, B, residual=R))
+    assert abs(L - 0.5 * float(np.sum((a - b) ** 2))) <= 1e-13 * L
+    exp_r = (a - b) if dtype == torch.float64 else (a - b).astype(np.float32).astype(np.float64)
+    assert np.array_equal(to_host(R), exp_r)
+    # a fixed partition and order: repeated sums are bitwise equal
+    assert float(api.dot(A, B)) == float(api.dot(A, B))
+
+
+def test_stable_dt_matches_oracle():
+    nx, ny, nz = 40, 33, 21
+    Ci = inputs.ci_random(nx, ny, nz)
+    dt = api.stable_dt(to_dev(Ci), 1.0)
+    dx, dy, dz = inputs.spacing(nx, ny, nz)
+    assert dt == oracle.stable_dt(dx, dy, dz, 1.0, oracle.maximum(Ci))
+
+
+def test_copy_boundary():
+    T0, *_ = problem(19, 14, 11, gaussian=False)
+    T = to_dev(T0)
+    T2 = torch.full_like(T, -5.0)
+    api.copy_boundary(T2, T)
+    out = to_host(T2)
+    inner = np.zeros(T0.shape, dtype=bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    assert np.array_equal(out[~inner], T0[~inner]) and np.all(out[inner] == -5.0)
+
+
+# -------------------------------------------------------------------- batch
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batch_matches_single_runs(dtype):
+    sizes = [3, 5, 17, 32, 40, 33, 64]
+    nt = 7
+    probs, refs = [], []
+    for q, n in enumerate(sizes):
+        T0, Ci, lam, dt, inv = problem(n, n, n, seed=1000 + q)
+        if dtype == torch.float32:
+            T0 = (T0 - 1.7).astype(np.float32).astype(np.float64)
+            Ci = Ci.astype(np.float32).astype(np.float64)
+        refs.append((oracle.run(T0, Ci, lam, dt, *inv, nt), T0))
+        T = to_dev(T0, dtype)
+        probs.append(dict(T=T, T2=T.clone(), Ci=to_dev(Ci, dtype), lam=lam, dt=dt, inv_spacing=inv))
+    b = api.Batch(probs)
+    b.run(nt, graph=True)
+    for q, (ref, T0) in enumerate(refs):
+        got = to_host(b.result(q, nt))
+        if dtype == torch.float64:
+            assert rel_linf(got, ref) <= FP64_TOL
+        else:
+            assert np.max(np.abs(got - ref)) <= f32_tol(nt, T0) + 1e-30
+    api.clear_graph_cache()
+
+
+# -------------------------------------------------------- full-size checks
+@pytest.mark.slow
+def test_fp64_512_light_cone_samples():
+    """The benchmark's workload (512^3, Gaussian T0, random Ci, nt=100) in the
+    launch configuration it times, checked at sampled nodes against the oracle
+    on each node's dependency cone."""
+    n, nt = 512, 100
+    T0, Ci, lam, dt, inv = problem(n, n, n)
+    got = gpu_run(T0, Ci, lam, dt, inv, nt, graph=True)
+    pts = [(256, 256, 256), (1, 1, 1), (510, 300, 7), (255, 3, 509), (120, 400, 256), (0, 17, 30)]
+    oracle.set_threads(max(1, oracle.max_threads()))
+    ref = light_cone_reference(oracle, T0, Ci, lam, dt, inv, nt, pts)
+    oracle.set_threads(1)
+    vals = np.array([got[k, j, i] for (i, j, k) in pts])
+    assert np.max(np.abs(vals - ref)) <= FP64_TOL * np.max(np.abs(T0))
+    # the step is a convex combination: the field stays within the initial range
+    assert got.min() >= T0.min() - 1e-12 and got.max() <= T0.max() + 1e-12
+    api.clear_graph_cache()
+
+
+@pytest.mark.slow
+def test_fp64_512_one_step_samples():
+    """One step at 512^3: sampled nodes against the oracle's step on each
+    node's 3x3x3 neighbourhood."""
+    n = 512
+    T0, Ci, lam, dt, inv = problem(n, n, n)
+    T = to_dev(T0)
+    T2 = T.clone()
+    api.step(T2, T, to_dev(Ci), lam, dt, inv)
+    got = to_host(T2)
+    rng = np.random.default_rng(0)
+    pts = [tuple(int(v) for v in rng.integers(1, n - 1, 3)) for _ in range(2000)]
+    ref = light_cone_reference(oracle, T0, Ci, lam, dt, inv, 1, pts)
+    vals = np.array([got[k, j, i] for (i, j, k) in pts])
+    assert np.max(np.abs(vals - ref)) <= 1e-15 * np.max(np.abs(T0))
