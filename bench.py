@@ -419,8 +419,8 @@ def run_ours(args):
     hbm, src = measured_peaks()
     mean_launch_s = statistics.mean(launch_ms) / 1e3
     achieved = bytes_per_launch / mean_launch_s / 1e9
-    kernel = api.step_kernel_name(torch.float64)
-    digest = source_digest(api.step_kernel_sources(torch.float64))
+    kernel = api.step_kernel_name(T2, T, C, lam, dt, inv)
+    digest = source_digest(api.step_kernel_sources(kernel))
     traffic = profiled_traffic(kernel, digest, n)
     line = {
         "metric": METRIC, "value": round(gbs, 1), "unit": "GB/s", "n_gpus": world, "steps": K,

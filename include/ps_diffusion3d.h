@@ -80,6 +80,18 @@ const char *ps_last_error(void);
 /* Bytes of device workspace the reduction entry points need. */
 size_t ps_workspace_bytes(void);
 
+/* Device-side error flags of the current device, to *out_host (host
+ * unsigned): bit 0 = a pipelined kernel gave up waiting for a shared-memory
+ * stage (bounded wait) and left without writing its remaining output.  With
+ * clear != 0 the flags are reset.  Synchronizes the device. */
+int ps_device_error(unsigned *out_host, int clear);
+
+/* Name of the kernel ps_diffusion3d_step would launch for these arguments
+ * (for profiles and reports; no validation, launches nothing). */
+const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void *Ci, double lam,
+                                       double dt, double _dx, double _dy, double _dz, int64_t nx,
+                                       int64_t ny, int64_t nz, int dtype);
+
 /* ---------------------------------------------------------------------
  * Time step (Fig. 1, step!).  Writes the interior nodes of T2 from T and
  * Ci; T2's boundary is left untouched.  T2 must not overlap T or Ci.

@@ -48,6 +48,8 @@ SIGNATURES = {
     "ps_version": (_I, []),
     "ps_last_error": (ctypes.c_char_p, []),
     "ps_workspace_bytes": (_SZ, []),
+    "ps_device_error": (_I, [ctypes.POINTER(_U), _I]),
+    "ps_diffusion3d_step_kernel": (ctypes.c_char_p, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I]),
     "ps_diffusion3d_step": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_step_comp_f32": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _P]),
     "ps_diffusion3d_copy_boundary": (_I, [_P, _P, _I64, _I64, _I64, _I, _P]),

@@ -264,14 +264,34 @@ def clear_graph_cache() -> None:
     check(_lib.load().ps_clear_graph_cache())
 
 
-def step_kernel_name(dtype) -> str:
-    """Name of the kernel that ``step`` launches for this dtype (for profiles)."""
-    return "k_step_basic" if dtype == torch.float64 else "k_step_basic"
+def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing) -> str:
+    """Name of the kernel that :func:`step` launches for these arguments."""
+    code = _code(T)
+    nx, ny, nz = _grid(T)
+    name = _lib.load().ps_diffusion3d_step_kernel(T2.data_ptr(), T.data_ptr(), Ci.data_ptr(), lam,
+                                                  dt, *inv_spacing, nx, ny, nz, code)
+    return name.decode()
 
 
-def step_kernel_sources(dtype):
-    """Source files of that kernel, relative to the repository root."""
-    return ["paper_2211_15634_gb300/csrc/stencil_basic.cuh"]
+KERNEL_SOURCES = {
+    "k_zmarch": ["paper_2211_15634_gb300/csrc/zmarch.cu", "paper_2211_15634_gb300/csrc/emu64.cuh",
+                 "paper_2211_15634_gb300/csrc/tma.cuh"],
+    "k_step_basic_emu": ["paper_2211_15634_gb300/csrc/stencil_basic.cuh",
+                         "paper_2211_15634_gb300/csrc/emu64.cuh"],
+    "k_step_basic": ["paper_2211_15634_gb300/csrc/stencil_basic.cuh"],
+}
+
+
+def step_kernel_sources(name: str):
+    """Source files of a step kernel, relative to the repository root."""
+    return KERNEL_SOURCES[name.split("<")[0]]
+
+
+def device_error(clear: bool = False) -> int:
+    """Device-side error flags (bit 0: a bounded pipeline wait timed out)."""
+    v = ctypes.c_uint(0)
+    check(_lib.load().ps_device_error(ctypes.byref(v), int(clear)))
+    return v.value
 
 
 def solve(T0_host: torch.Tensor, Ci_host: torch.Tensor, lam: float, dt: Optional[float],

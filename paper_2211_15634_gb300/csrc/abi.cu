@@ -74,10 +74,12 @@ static int check_ptr(const void *p, const char *name) {
     return PS_OK;
 }
 
-static bool overlap(const void *a, const void *b, size_t bytes) {
+static bool overlap2(const void *a, size_t abytes, const void *b, size_t bbytes) {
     const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
-    return x < y + bytes && y < x + bytes;
+    return x < y + bbytes && y < x + abytes;
 }
+
+static bool overlap(const void *a, const void *b, size_t bytes) { return overlap2(a, bytes, b, bytes); }
 
 static int check_finite(double v, const char *name) {
     if (!std::isfinite(v)) return fail(PS_ERR_ARG, "%s is not finite", name);
@@ -195,6 +197,22 @@ extern "C" {
 int ps_version(void) { return 100; }
 
 const char *ps_last_error(void) { return g_err.c_str(); }
+
+int ps_device_error(unsigned *out_host, int clear) {
+    if (!out_host) return fail(PS_ERR_ARG, "out_host is NULL");
+    *out_host = zmarch_device_error(clear != 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ps_device_error");
+    return PS_OK;
+}
+
+const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void *Ci, double lam,
+                                       double dt, double _dx, double _dy, double _dz, int64_t nx,
+                                       int64_t ny, int64_t nz, int dtype) {
+    const Grid3 g{nx, ny, nz};
+    if (dtype == PS_F64) return step_f64_kernel_name(g, T2, T, Ci, make_coef(lam, dt, _dx, _dy, _dz));
+    return step_f32_kernel_name(g, T2, T, Ci);
+}
 
 size_t ps_workspace_bytes(void) { return kWorkspaceBytes; }
 
@@ -388,7 +406,7 @@ int ps_to_deviation(float *D, const double *T, double t_ref, int64_t n, void *st
     PS_TRY(check_ptr(D, "D"));
     PS_TRY(check_ptr(T, "T"));
     PS_TRY(check_finite(t_ref, "t_ref"));
-    if (overlap(D, T, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "D overlaps T");
+    if (overlap2(D, (size_t)n * 4, T, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "D overlaps T");
     cudaError_t e = launch_to_deviation(D, T, t_ref, n, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_to_deviation");
     return PS_OK;
@@ -399,7 +417,7 @@ int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *
     PS_TRY(check_ptr(D, "D"));
     PS_TRY(check_ptr(T, "T"));
     PS_TRY(check_finite(t_ref, "t_ref"));
-    if (overlap(D, T, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "T overlaps D");
+    if (overlap2(D, (size_t)n * 4, T, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "T overlaps D");
     cudaError_t e = launch_from_deviation(T, D, t_ref, n, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_from_deviation");
     return PS_OK;

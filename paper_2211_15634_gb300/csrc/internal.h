@@ -37,6 +37,9 @@ cudaError_t launch_step_f32(float *T2, const float *T, const float *Ci, StepCoef
                             cudaStream_t s);
 cudaError_t launch_step_f32_comp(float *T2, const float *T, float *comp, const float *Ci,
                                  StepCoef c, Grid3 g, cudaStream_t s);
+const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c);
+const char *step_f32_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci);
+unsigned zmarch_device_error(bool clear);
 
 // ---- helpers (misc.cu) ----
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);

@@ -8,12 +8,57 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "emu64.cuh"
+
 namespace psd {
 
 template <typename F>
 struct CoefT {
     F dtlam, ax, ay, az;
 };
+
+// Same column march for FP64 data with the one-DFMA emulated arithmetic of
+// emu64.cuh (used when the TMA kernel cannot serve the grid, e.g. odd nx).
+template <bool kIso>
+__global__ void __launch_bounds__(256)
+k_step_basic_emu(double *__restrict__ T2, const double *__restrict__ T,
+                 const double *__restrict__ Ci, EmuCoef c, int64_t nx, int64_t ny, int64_t nz,
+                 int kchunk) {
+    const int64_t i = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = 1 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > nx - 2 || j > ny - 2) return;
+    const int64_t k0 = 1 + (int64_t)blockIdx.z * kchunk;
+    const int64_t k1 = k0 + kchunk < nz - 1 ? k0 + kchunk : nz - 1;
+    if (k0 >= k1) return;
+    const int64_t sy = nx, sz = nx * ny;
+    const unsigned long long *__restrict__ Tb = (const unsigned long long *)T;
+    int64_t p = i + sy * (j + ny * k0);
+    unsigned long long tm = Tb[p - sz], tc = Tb[p];
+    for (int64_t k = k0; k < k1; ++k, p += sz) {
+        const unsigned long long tp = Tb[p + sz];
+        T2[p] = emu_step_node<kIso>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy], Tb[p + sy], tm, tp, Ci[p], c);
+        tm = tc;
+        tc = tp;
+    }
+}
+
+inline cudaError_t launch_step_basic_emu(double *T2, const double *T, const double *Ci,
+                                         const EmuCoef &c, bool iso, int64_t nx, int64_t ny,
+                                         int64_t nz, int nsm, cudaStream_t s) {
+    const dim3 block(32, 8, 1);
+    const int64_t gx = (nx - 2 + block.x - 1) / block.x, gy = (ny - 2 + block.y - 1) / block.y;
+    int64_t want = (8LL * nsm + gx * gy - 1) / (gx * gy);
+    int64_t kchunk = (nz - 2 + want - 1) / want;
+    if (kchunk < 16) kchunk = 16;
+    const int64_t gz = (nz - 2 + kchunk - 1) / kchunk;
+    if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)gz);
+    if (iso)
+        k_step_basic_emu<true><<<grid, block, 0, s>>>(T2, T, Ci, c, nx, ny, nz, (int)kchunk);
+    else
+        k_step_basic_emu<false><<<grid, block, 0, s>>>(T2, T, Ci, c, nx, ny, nz, (int)kchunk);
+    return cudaGetLastError();
+}
 
 // Fig. 1 step!: T2 = T + dt*lam*Ci*((d2x*_dx^2 + d2y*_dy^2) + d2z*_dz^2) at
 // interior nodes; the z-range of this block is [k0, k1).

@@ -1,6 +1,10 @@
-// FP64 forward step kernels.
+// FP64 forward step dispatch.
+//   fast:   TMA z-march with one-DFMA emulated arithmetic (even nx), else the
+//           plain column march with the same arithmetic;
+//   native: plain column march with ordinary FP64 instructions.
 #include "internal.h"
 #include "stencil_basic.cuh"
+#include "zmarch.h"
 
 namespace psd {
 
@@ -12,9 +16,29 @@ cudaError_t launch_step_f64_native(double *T2, const double *T, const double *Ci
                                             sm_count(), s);
 }
 
+static bool emu_ok(StepCoef c) {
+    const double k[3] = {c.dtlam * c.ax, c.dtlam * c.ay, c.dtlam * c.az};
+    for (double v : k)
+        if (!(v > 2.2250738585072014e-308 && v < 1e300)) return false;  // positive normal
+    return true;
+}
+
 cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, StepCoef c,
                                  Grid3 g, cudaStream_t s) {
-    return launch_step_f64_native(T2, T, Ci, c, g, s);
+    if (!emu_ok(c)) return launch_step_f64_native(T2, T, Ci, c, g, s);
+    const bool iso = c.ax == c.ay && c.ay == c.az;
+    if (zmarch_supported(g, 8, T2, T, Ci))
+        return launch_zmarch(iso ? Z_F64_EMU_ISO : Z_F64_EMU_ANISO, T2, T, nullptr, Ci, c, g, s);
+    const EmuCoef ek{emu_const(c.dtlam * c.ax), emu_const(c.dtlam * c.ay), emu_const(c.dtlam * c.az),
+                     c.dtlam, c.ax, c.ay, c.az};
+    return launch_step_basic_emu(T2, T, Ci, ek, iso, g.nx, g.ny, g.nz, sm_count(), s);
+}
+
+const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c) {
+    if (!emu_ok(c)) return "k_step_basic<double>";
+    const bool iso = c.ax == c.ay && c.ay == c.az;
+    if (zmarch_supported(g, 8, T2, T, Ci)) return iso ? "k_zmarch<F64_EMU_ISO>" : "k_zmarch<F64_EMU_ANISO>";
+    return "k_step_basic_emu";
 }
 
 }  // namespace psd

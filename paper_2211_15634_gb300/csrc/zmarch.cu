@@ -1,0 +1,366 @@
+// Tiled z-march step kernels fed by TMA.
+//
+// A CTA owns one x-y tile of BX x BY nodes (BX = 32 threads * PX nodes per
+// thread, one warp per tile row) and a chunk of z-planes.  For every plane a
+// single thread issues one TMA box load of the tile plus a one-node halo in
+// y and a 16-byte halo in x (so every box starts on a 16-byte boundary) into
+// a ring of NST shared-memory stages, and one box of Ci into a ring of NSC
+// stages; completion is tracked with mbarrier transaction counts.  Each
+// thread keeps its PX centre values of planes k-1, k, k+1 in registers (the
+// z-neighbours) and reads x/y neighbours of plane k from shared memory, so
+// every T value is read from HBM once (plus halos that mostly hit in L2).
+// T2 is written with 16-byte stores.  Boundary nodes are never written.
+//
+// Preconditions (checked by the host launcher, else the plain kernel runs):
+// nx*sizeof(elem) is a multiple of 16 (TMA row pitch) and all base pointers
+// are 16-byte aligned.
+#include <cudaTypedefs.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "emu64.cuh"
+#include "internal.h"
+#include "tma.cuh"
+#include "zmarch.h"
+
+namespace psd {
+
+__device__ unsigned g_zmarch_error;  // set when an mbarrier wait times out
+
+template <int MODE>
+struct ZTraits;
+template <>
+struct ZTraits<Z_F64_EMU_ISO> {
+    using E = double;
+    using V = double2;
+    static constexpr int PX = 2;
+};
+template <>
+struct ZTraits<Z_F64_EMU_ANISO> : ZTraits<Z_F64_EMU_ISO> {};
+template <>
+struct ZTraits<Z_F64_NATIVE> : ZTraits<Z_F64_EMU_ISO> {};
+template <>
+struct ZTraits<Z_F32> {
+    using E = float;
+    using V = float4;
+    static constexpr int PX = 4;
+};
+template <>
+struct ZTraits<Z_F32_COMP> : ZTraits<Z_F32> {};
+
+template <typename V, typename E>
+__device__ __forceinline__ E vget(const V &v, int i) {
+    return reinterpret_cast<const E *>(&v)[i];
+}
+
+template <int MODE>
+__device__ __forceinline__ constexpr unsigned zstage_bytes(int BY) {
+    using E = typename ZTraits<MODE>::E;
+    constexpr int PX = ZTraits<MODE>::PX;
+    return ((32 * PX + 2 * PX) * (BY + 2) * sizeof(E) + 127) / 128 * 128;
+}
+
+template <int MODE, int BY, int NST, int NSC>
+__global__ void __launch_bounds__(32 * BY, 1)
+k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmC,
+         void *__restrict__ T2v, void *__restrict__ compv, const ZParams p) {
+    using Tr = ZTraits<MODE>;
+    using E = typename Tr::E;
+    using V = typename Tr::V;
+    constexpr int PX = Tr::PX, HX = PX, BX = 32 * PX, W = BX + 2 * HX, H = BY + 2;
+    constexpr unsigned TB = W * H * sizeof(E), CB = BX * BY * sizeof(E);
+    constexpr unsigned TBA = (TB + 127) / 128 * 128, CBA = (CB + 127) / 128 * 128;
+    extern __shared__ __align__(128) unsigned char smem[];
+    E *sT = (E *)smem;
+    E *sC = (E *)(smem + NST * TBA);
+    uint64_t *bar = (uint64_t *)(smem + NST * TBA + NSC * CBA);
+    __shared__ int s_abort;
+
+    const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int X0 = (int)(blockIdx.x % p.ntx) * BX, Y0 = (int)(blockIdx.x / p.ntx) * BY;
+    const int k0 = 1 + (int)blockIdx.y * p.kchunk;
+    const int k1 = (int)min((int64_t)k0 + p.kchunk, p.nz - 1);  // output planes [k0, k1)
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < NST + NSC; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // T planes k0-1 .. k1 live in stage (q - (k0-1)) % NST; Ci planes k0 .. k1-1 in (q - k0) % NSC
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            const int q = k0 - 1 + s;
+            if (q <= k1) {
+                mbar_expect_tx(&bar[s], TB);
+                tma_load_3d(sT + s * (TBA / sizeof(E)), &tmT, &bar[s], X0 - HX, Y0 - 1, q);
+            }
+        }
+        for (int s = 0; s < NSC; ++s) {
+            const int q = k0 + s;
+            if (q < k1) {
+                mbar_expect_tx(&bar[NST + s], CB);
+                tma_load_3d(sC + s * (CBA / sizeof(E)), &tmC, &bar[NST + s], X0, Y0, q);
+            }
+        }
+    }
+    auto tst = [&](int q) -> const E * { return sT + ((q - (k0 - 1)) % NST) * (TBA / sizeof(E)); };
+    auto twait = [&](int q) -> bool {
+        return mbar_wait(&bar[(q - (k0 - 1)) % NST], ((q - (k0 - 1)) / NST) & 1);
+    };
+    auto cst = [&](int q) -> const E * { return sC + ((q - k0) % NSC) * (CBA / sizeof(E)); };
+    auto cwait = [&](int q) -> bool {
+        return mbar_wait(&bar[NST + (q - k0) % NSC], ((q - k0) / NSC) & 1);
+    };
+
+    const int row = ty + 1, col = HX + lane * PX;
+    bool ok = twait(k0 - 1);
+    V qm = *(const V *)(tst(k0 - 1) + row * W + col);
+    ok = twait(k0) && ok;
+    V qc = *(const V *)(tst(k0) + row * W + col);
+    if (!ok) {
+        s_abort = 1;
+        atomicOr(&g_zmarch_error, 1u);
+    }
+    __syncthreads();
+    if (s_abort) return;
+    if (threadIdx.x == 0) {
+        const int q = k0 - 1 + NST;
+        if (q <= k1) {
+            const int s = 0;  // stage of plane k0-1
+            mbar_expect_tx(&bar[s], TB);
+            tma_load_3d(sT + s * (TBA / sizeof(E)), &tmT, &bar[s], X0 - HX, Y0 - 1, q);
+        }
+    }
+
+    const int gy = Y0 + ty;
+    const int gx0 = X0 + lane * PX;
+    const bool row_ok = gy >= 1 && gy <= p.ny - 2;
+    bool all_x = gx0 >= 1 && gx0 + PX - 1 <= p.nx - 2;
+    E *__restrict__ T2 = (E *)T2v;
+    E *__restrict__ comp = (E *)compv;
+
+    for (int k = k0; k < k1; ++k) {
+        ok = twait(k + 1);
+        const E *Tk = tst(k);
+        const V qn = *(const V *)(tst(k + 1) + row * W + col);
+        const E left = Tk[row * W + col - 1], right = Tk[row * W + col + PX];
+        const V up = *(const V *)(Tk + (row - 1) * W + col);
+        const V dn = *(const V *)(Tk + (row + 1) * W + col);
+        ok = cwait(k) && ok;
+        const V civ = *(const V *)(cst(k) + ty * BX + lane * PX);
+
+        if (row_ok) {
+            const int64_t base = (int64_t)gx0 + p.nx * ((int64_t)gy + p.ny * (int64_t)k);
+            V cv{};
+            if constexpr (MODE == Z_F32_COMP) {
+                if (all_x) cv = *(const V *)(comp + base);
+                else
+#pragma unroll
+                    for (int i = 0; i < PX; ++i) {
+                        const int gx = gx0 + i;
+                        reinterpret_cast<E *>(&cv)[i] = (gx >= 1 && gx <= p.nx - 2) ? comp[base + i] : E(0);
+                    }
+            }
+            V out;
+#pragma unroll
+            for (int i = 0; i < PX; ++i) {
+                const E c = vget<V, E>(qc, i);
+                const E xm = i == 0 ? left : vget<V, E>(qc, i - 1);
+                const E xp = i == PX - 1 ? right : vget<V, E>(qc, i + 1);
+                const E ym = vget<V, E>(up, i), yp = vget<V, E>(dn, i);
+                const E zm = vget<V, E>(qm, i), zp = vget<V, E>(qn, i);
+                const E ci = vget<V, E>(civ, i);
+                E r;
+                if constexpr (MODE == Z_F64_EMU_ISO || MODE == Z_F64_EMU_ANISO) {
+                    r = emu_step_node<MODE == Z_F64_EMU_ISO>(
+                        dbits((double)c), dbits((double)xm), dbits((double)xp), dbits((double)ym),
+                        dbits((double)yp), dbits((double)zm), dbits((double)zp), (double)ci, p.ek);
+                } else if constexpr (MODE == Z_F64_NATIVE) {
+                    const double d2x = (xp - c) - (c - xm), d2y = (yp - c) - (c - ym);
+                    const double d2z = (zp - c) - (c - zm);
+                    r = c + p.ek.dtlam * (ci * ((d2x * p.ek.ax + d2y * p.ek.ay) + d2z * p.ek.az));
+                } else {
+                    const float d2x = (xp - c) - (c - xm), d2y = (yp - c) - (c - ym);
+                    const float d2z = (zp - c) - (c - zm);
+                    const float lap = (d2x * p.fax + d2y * p.fay) + d2z * p.faz;
+                    if constexpr (MODE == Z_F32) {
+                        r = c + p.fdtlam * (ci * lap);
+                    } else {
+                        const float delta = p.fdtlam * (ci * lap);
+                        const float yv = delta - vget<V, E>(cv, i);
+                        const float t = c + yv;
+                        reinterpret_cast<E *>(&cv)[i] = (t - c) - yv;
+                        r = t;
+                    }
+                }
+                reinterpret_cast<E *>(&out)[i] = r;
+            }
+            if (all_x) {
+                *(V *)(T2 + base) = out;
+                if constexpr (MODE == Z_F32_COMP) *(V *)(comp + base) = cv;
+            } else {
+#pragma unroll
+                for (int i = 0; i < PX; ++i) {
+                    const int gx = gx0 + i;
+                    if (gx >= 1 && gx <= p.nx - 2) {
+                        T2[base + i] = vget<V, E>(out, i);
+                        if constexpr (MODE == Z_F32_COMP) comp[base + i] = vget<V, E>(cv, i);
+                    }
+                }
+            }
+        }
+        if (!ok) {
+            s_abort = 1;
+            atomicOr(&g_zmarch_error, 1u);
+        }
+        __syncthreads();  // every thread is done with plane k's T stage and Ci stage
+        if (s_abort) return;
+        if (threadIdx.x == 0) {
+            const int q = k + NST;
+            if (q <= k1) {
+                const int s = (k - (k0 - 1)) % NST;
+                mbar_expect_tx(&bar[s], TB);
+                tma_load_3d(sT + s * (TBA / sizeof(E)), &tmT, &bar[s], X0 - HX, Y0 - 1, q);
+            }
+            const int qc2 = k + NSC;
+            if (qc2 < k1) {
+                const int s = (k - k0) % NSC;
+                mbar_expect_tx(&bar[NST + s], CB);
+                tma_load_3d(sC + s * (CBA / sizeof(E)), &tmC, &bar[NST + s], X0, Y0, qc2);
+            }
+        }
+        qm = qc;
+        qc = qn;
+    }
+}
+
+// ------------------------------------------------------------------ host
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    });
+    return fn;
+}
+
+static bool make_map(CUtensorMap *m, const void *ptr, int esz, Grid3 g, unsigned bx, unsigned by) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)(g.nx * esz), (cuuint64_t)(g.nx * g.ny * esz)};
+    const cuuint32_t box[3] = {bx, by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(m, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          3, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool zmarch_supported(Grid3 g, int esz, const void *a, const void *b, const void *c) {
+    if ((g.nx * esz) % 16 != 0) return false;
+    if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15u) return false;
+    if (g.nx > (1LL << 31) - 256 || g.ny > (1LL << 31) - 64 || g.nz > (1LL << 31) - 2) return false;
+    return encode_fn() != nullptr;
+}
+
+template <int MODE, int BY, int NST, int NSC>
+static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const void *Ci, Grid3 g,
+                                   ZParams p, int kchunk, cudaStream_t s) {
+    using E = typename ZTraits<MODE>::E;
+    constexpr int PX = ZTraits<MODE>::PX, BX = 32 * PX, W = BX + 2 * PX, H = BY + 2;
+    constexpr unsigned TBA = (W * H * sizeof(E) + 127) / 128 * 128;
+    constexpr unsigned CBA = (BX * BY * sizeof(E) + 127) / 128 * 128;
+    constexpr size_t smem = NST * TBA + NSC * CBA + (NST + NSC) * 8;
+    static bool attr_done[64] = {false};
+    const int dev = current_device();
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_zmarch<MODE, BY, NST, NSC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    CUtensorMap mT, mC;
+    if (!make_map(&mT, T, sizeof(E), g, W, H) || !make_map(&mC, Ci, sizeof(E), g, BX, BY))
+        return cudaErrorInvalidValue;
+    const int64_t ntx = (g.nx + BX - 1) / BX, nty = (g.ny + BY - 1) / BY;
+    const int64_t tiles = ntx * nty;
+    if (kchunk <= 0) {
+        // Short chunks keep many CTAs in flight (no wave tail) while consecutive
+        // CTAs - neighbouring tiles of one chunk - share their halo planes in L2.
+        // 16 planes measured best at 512^3; small grids go down to 4 planes so
+        // that they still fill the GPU (about 64 CTAs per SM).
+        const int64_t target = 64LL * sm_count();
+        int64_t kc = (g.nz - 2) * tiles / target;
+        kchunk = (int)(kc < 4 ? 4 : (kc > 16 ? 16 : kc));
+    }
+    const int64_t gz = (g.nz - 2 + kchunk - 1) / kchunk;
+    if (tiles > 0x7fffffffLL || gz > 65535) return cudaErrorInvalidConfiguration;
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.nz = g.nz;
+    p.ntx = (int)ntx;
+    p.kchunk = kchunk;
+    k_zmarch<MODE, BY, NST, NSC><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
+        mT, mC, T2, comp, p);
+    return cudaGetLastError();
+}
+
+static ZParams make_params(StepCoef c) {
+    ZParams p{};
+    p.ek = EmuCoef{emu_const(c.dtlam * c.ax), emu_const(c.dtlam * c.ay), emu_const(c.dtlam * c.az),
+                   c.dtlam, c.ax, c.ay, c.az};
+    p.fdtlam = (float)c.dtlam;
+    p.fax = (float)c.ax;
+    p.fay = (float)c.ay;
+    p.faz = (float)c.az;
+    return p;
+}
+
+static int env_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+
+cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
+                          Grid3 g, cudaStream_t s) {
+    const ZParams p = make_params(c);
+    const int kchunk = env_int("PS_KCHUNK", 0);
+    const bool positive = c.dtlam * c.ax > 0 && c.dtlam * c.ay > 0 && c.dtlam * c.az > 0;
+    switch (mode) {
+        case Z_F64_EMU_ISO:
+        case Z_F64_EMU_ANISO:
+            if (!positive) return launch_zmarch_t<Z_F64_NATIVE, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            if (mode == Z_F64_EMU_ISO)
+                return launch_zmarch_t<Z_F64_EMU_ISO, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+        case Z_F64_NATIVE:
+            return launch_zmarch_t<Z_F64_NATIVE, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+        case Z_F32:
+            return launch_zmarch_t<Z_F32, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+        case Z_F32_COMP:
+            return launch_zmarch_t<Z_F32_COMP, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+unsigned zmarch_device_error(bool clear) {
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_zmarch_error, sizeof(v));
+    if (clear) {
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(g_zmarch_error, &z, sizeof(z));
+    }
+    return v;
+}
+
+}  // namespace psd

@@ -1,0 +1,24 @@
+// Declarations of the TMA-fed z-march step kernels (zmarch.cu).
+#pragma once
+
+#include "emu64.cuh"
+#include "internal.h"
+
+namespace psd {
+
+enum ZMode { Z_F64_EMU_ISO = 0, Z_F64_EMU_ANISO = 1, Z_F64_NATIVE = 2, Z_F32 = 3, Z_F32_COMP = 4 };
+
+struct ZParams {
+    int64_t nx, ny, nz;
+    int kchunk, ntx;
+    EmuCoef ek;
+    float fdtlam, fax, fay, faz;
+};
+
+// True when the TMA path can serve this grid and these pointers.
+bool zmarch_supported(Grid3 g, int esz, const void *a, const void *b, const void *c);
+cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
+                          Grid3 g, cudaStream_t s);
+unsigned zmarch_device_error(bool clear);
+
+}  // namespace psd

@@ -36,7 +36,11 @@ def gpu_run(T0, Ci, lam, dt, inv, nt, dtype=torch.float64, **kw):
     return to_host(res)
 
 
-SHAPES = [(3, 3, 3), (4, 3, 5), (5, 6, 7), (37, 29, 23), (66, 19, 20), (130, 67, 33), (257, 9, 12)]
+# odd nx -> plain column kernel; nx*8 % 16 == 0 -> TMA z-march (64 x 8 tiles in FP64,
+# 128 x 8 in FP32): several tiles in x and y with ragged tails, and short z ranges
+SHAPES = [(3, 3, 3), (4, 3, 5), (5, 6, 7), (37, 29, 23), (66, 19, 20), (130, 67, 33), (257, 9, 12),
+          (132, 21, 17), (256, 35, 19), (68, 70, 40), (200, 3, 4)]
+F32_SHAPES = [(5, 6, 7), (37, 29, 23), (130, 67, 33), (132, 21, 17), (256, 35, 19), (4, 9, 5)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -117,7 +121,39 @@ def test_run_nt0_returns_input():
 
 
 # --------------------------------------------------------------------- FP32
-@pytest.mark.parametrize("shape", [(5, 6, 7), (37, 29, 23), (130, 67, 33)])
+@pytest.mark.parametrize("kchunk", ["1", "3", "7"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_short_z_chunks(monkeypatch, kchunk, dtype):
+    """Many z-chunks per column (pipeline prologue/epilogue at every chunk edge)."""
+    monkeypatch.setenv("PS_KCHUNK", kchunk)
+    nx, ny, nz, nt = 136, 27, 22, 5
+    T0, Ci, lam, dt, inv = problem(nx, ny, nz)
+    if dtype == torch.float64:
+        ref = oracle.run(T0, Ci, lam, dt, *inv, nt)
+        assert rel_linf(gpu_run(T0, Ci, lam, dt, inv, nt), ref) <= FP64_TOL
+    else:
+        D0 = (T0 - 1.7).astype(np.float32).astype(np.float64)
+        C32 = Ci.astype(np.float32).astype(np.float64)
+        ref = oracle.run(D0, C32, lam, dt, *inv, nt)
+        got = gpu_run(D0, C32, lam, dt, inv, nt, dtype=torch.float32)
+        assert np.max(np.abs(got - ref)) <= f32_tol(nt, D0)
+    assert api.device_error() == 0
+
+
+def test_emulated_fp64_general_path():
+    """Fields that cross zero and binades at every node (signs, zeros, tiny
+    values) exercise the fixed-point path of the one-DFMA arithmetic."""
+    nx, ny, nz, nt = 66, 31, 17, 6
+    _, Ci, lam, dt, inv = problem(nx, ny, nz)
+    T0 = inputs.random_field((nz, ny, nx), 77, -1.0, 1.0)
+    T0[::3, :, ::5] = 0.0
+    T0[1::4, ::2, :] *= 1e-9
+    ref = oracle.run(T0, Ci, lam, dt, *inv, nt)
+    for flags in ({}, {"native_f64": True}):
+        assert rel_linf(gpu_run(T0, Ci, lam, dt, inv, nt, **flags), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("shape", F32_SHAPES)
 @pytest.mark.parametrize("comp", [False, True])
 def test_fp32_run_matches_oracle(shape, comp):
     nx, ny, nz = shape
