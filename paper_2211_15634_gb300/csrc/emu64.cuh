@@ -1,10 +1,10 @@
-// FP64 step arithmetic with one FP64 instruction per node.
+// FP64 step arithmetic with one (or two) FP64 instructions per node.
 //
 // The GB300 runs FP64 instructions (DFMA, DADD and every FP64<->FP32/INT
 // conversion) at about 1/58 of the FP32 rate, so a plain FP64 evaluation of
 // Fig. 1's step (about nine FP64 instructions per node) is bound by the FP64
 // pipe at roughly a quarter of the HBM rate.  These routines compute the
-// same update with integer and FP32-pipe instructions plus a single DFMA:
+// same update with integer instructions plus a single DFMA:
 //
 //   T2 = fma(Ci, L, T),   L = K * S * 2^sc,
 //
@@ -12,12 +12,18 @@
 // such sum per axis), formed EXACTLY in 64-bit integer arithmetic, K =
 // dt*lam*_d^2 is a host constant, and the product K*S is formed with a 64x64
 // bit high multiply and packed into an FP64 bit pattern with integer ops.
+// The kDmul variant instead packs S exactly and spends a second FP64
+// instruction on Ci*K:  T2 = fma(Ci*K, S*2^sc, T).
 //
 //  * Fast path: when all seven values share sign and exponent, the
 //    difference of two FP64 bit patterns is the difference of the values in
-//    units of the common ulp, so S needs no conversion at all.
-//  * General path (other nodes): every value is converted to fixed point at
-//    the largest exponent among the seven (57-bit magnitudes), then summed.
+//    units of the common ulp, so S needs no conversion at all (for negative
+//    values the bit difference is minus the value difference; the sign of
+//    the packed result is flipped instead).
+//  * General path (other nodes, rare for smooth fields): every value is
+//    converted to fixed point at the largest exponent among the seven
+//    (57-bit magnitudes), then summed.  It is a separate, non-inlined
+//    function reached by a branch, so nodes on the fast path never execute it.
 //  * Inf/NaN inputs fall back to the plain FP64 expression.
 //
 // Error: S is exact (the general path truncates values more than 57 binades
@@ -46,42 +52,74 @@ __host__ __device__ inline EmuK emu_const(double K) {
     return EmuK{man << 10, k - 62};
 }
 
+struct EmuCoef {
+    EmuK kx, ky, kz;  // dt*lam*_d^2 per axis as integer mantissa and exponent
+    double dtlam, ax, ay, az;
+    double Kx;        // dt*lam*_dx^2 (the kDmul variant, iso grids)
+};
+
 __device__ __forceinline__ unsigned long long dbits(double d) {
     return (unsigned long long)__double_as_longlong(d);
 }
 __device__ __forceinline__ double bitsd(unsigned long long b) {
     return __longlong_as_double((long long)b);
 }
-
-// FP64 nearest to K * S * 2^sc for an exact signed integer S.
-__device__ __forceinline__ double emu_scaled(long long S, int sc, EmuK K) {
-    const unsigned long long neg = (unsigned long long)(S >> 63);
-    unsigned long long a = ((unsigned long long)S ^ neg) - neg;  // |S|
-    const int lz = __clzll((long long)a);                        // 64 when S == 0
-    a <<= (lz & 63);
-    unsigned long long P = __umul64hi(a, K.m);                   // [2^61, 2^63) unless S == 0
-    const int top = (int)(P >> 62);
-    P = top ? P : (P << 1);
-    const int be = 125 + top + K.e + sc - lz + 1022;             // biased exponent - 1
-    const unsigned long long M = (P + 0x200ull) >> 10;           // [2^52, 2^53], rounded
-    unsigned long long bits = ((unsigned long long)(long long)be << 52) + M;
-    bits |= neg & 0x8000000000000000ull;
-    bits = (a == 0ull || be < 0) ? 0ull : bits;                   // zero, or underflow -> 0
-    return bitsd(bits);
-}
-
-// Signed fixed-point value of FP64 bits v at scale 2^(Emax' - 1079), where
-// Emax' = max(Emax, 1) is the largest biased exponent of the group (57-bit
-// magnitudes; values 64+ binades below Emax' become 0).
-__device__ __forceinline__ long long emu_fixed(unsigned long long v, int emax1) {
-    const int e = (int)((v >> 52) & 0x7ff);
-    const unsigned long long man = (v & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-    const int r = emax1 - (e ? e : 1);
-    const unsigned long long x = r < 64 ? ((man << 4) >> r) : 0ull;
-    return (v >> 63) ? -(long long)x : (long long)x;
-}
-
 __device__ __forceinline__ int emu_exp(unsigned long long v) { return (int)((v >> 52) & 0x7ff); }
+
+// FP64 bit pattern nearest to K * |S| * 2^sc, S an exact signed integer
+// (sign bit not set; the caller applies the sign).  Zero for S == 0 and on
+// underflow.
+__device__ __forceinline__ unsigned long long emu_scaled_mag(unsigned long long a, int sc, EmuK K) {
+    const int lz = __clzll((long long)a);  // 64 when a == 0
+    a <<= (lz & 63);
+    const unsigned long long P = __umul64hi(a, K.m);  // [2^61, 2^63) unless a == 0
+    const int top = (int)(P >> 62);
+    // top: P in [2^62, 2^63) -> 53-bit mantissa P >> 10; else (2P) >> 10 = P >> 9
+    const int sh = 9 + top;
+    const unsigned long long M = (P + (1ull << (sh - 1))) >> sh;  // [2^52, 2^53], rounded
+    const int be = 125 + top + K.e + sc - lz + 1022;            // biased exponent - 1
+    const unsigned long long bits = ((unsigned long long)(long long)be << 52) + M;
+    return (a == 0ull || be < 0) ? 0ull : bits;
+}
+
+// Exact FP64 bit pattern of |S| * 2^sc (rounded to nearest when |S| >= 2^53).
+__device__ __forceinline__ unsigned long long emu_pack_mag(unsigned long long a, int sc) {
+    const int lz = __clzll((long long)a);
+    a <<= (lz & 63);                                          // leading one at bit 63
+    const unsigned long long M = (a + 0x400ull) >> 11;        // [2^52, 2^53]
+    const int be = 63 - lz + sc + 1022;
+    const unsigned long long bits = ((unsigned long long)(long long)be << 52) + M;
+    return (a == 0ull || be < 0) ? 0ull : bits;
+}
+
+__device__ __forceinline__ unsigned long long emu_abs(long long S, unsigned long long *sign) {
+    const unsigned long long neg = (unsigned long long)(S >> 63);
+    *sign = neg & 0x8000000000000000ull;
+    return ((unsigned long long)S ^ neg) - neg;
+}
+
+// d | (a ^ c) and (a ^ c) | (b ^ c) as single 3-input logic instructions.
+__device__ __forceinline__ unsigned lop_or_xor(unsigned d, unsigned a, unsigned c) {
+    unsigned r;
+    asm("lop3.b32 %0, %1, %2, %3, 0xF6;" : "=r"(r) : "r"(d), "r"(a), "r"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned lop_xor_or(unsigned a, unsigned b, unsigned c) {
+    unsigned r;
+    asm("lop3.b32 %0, %1, %2, %3, 0x7E;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
+// True when every high word in h shares the sign and exponent field (top 12
+// bits) with hc and hc is not Inf/NaN: then the FP64 values they belong to
+// lie in one binade and their bit patterns differ by whole ulps.
+template <int N>
+__device__ __forceinline__ bool emu_same_binade_hi(const unsigned (&h)[N], unsigned hc) {
+    unsigned d = lop_xor_or(h[0], h[1], hc);
+#pragma unroll
+    for (int i = 2; i < N; ++i) d = lop_or_xor(d, h[i], hc);
+    return ((d & 0xfff00000u) | ((hc & 0x7ff00000u) == 0x7ff00000u)) == 0u;
+}
 
 // True when the six neighbours share sign and exponent with the centre and the
 // centre is finite.
@@ -96,60 +134,95 @@ __device__ __forceinline__ bool emu_same_binade(unsigned long long c, unsigned l
     return ((d & 0xfff00000u) == 0u) && ((hc & 0x7ff00000u) != 0x7ff00000u);
 }
 
-struct EmuCoef {
-    EmuK kx, ky, kz;  // dt*lam*_d^2 per axis
-    double dtlam, ax, ay, az;
-};
-
-// One node of Fig. 1's step: returns T2 for centre c, neighbours, and Ci.
-// kIso: the three axis coefficients are equal (one product instead of three).
+// L (as FP64 bits, with sign) from exact per-axis sums at scale 2^sc.
 template <bool kIso>
+__device__ __forceinline__ double emu_L(long long sx, long long sy, long long sz, int sc,
+                                        unsigned long long flip, const EmuCoef &k) {
+    unsigned long long sg;
+    if (kIso) {
+        const unsigned long long a = emu_abs(sx + sy + sz, &sg);
+        return bitsd(emu_scaled_mag(a, sc, k.kx) | (sg ^ flip));
+    } else {
+        unsigned long long s1, s2, s3;
+        const unsigned long long ax = emu_abs(sx, &s1), ay = emu_abs(sy, &s2), az = emu_abs(sz, &s3);
+        const double L = (bitsd(emu_scaled_mag(ax, sc, k.kx) | s1) +
+                          bitsd(emu_scaled_mag(ay, sc, k.ky) | s2)) +
+                         bitsd(emu_scaled_mag(az, sc, k.kz) | s3);
+        return bitsd(dbits(L) ^ flip);
+    }
+}
+
+// Fast path (caller checked emu_same_binade).
+template <bool kIso, bool kDmul>
+__device__ __forceinline__ double emu_fast_node(unsigned long long c, unsigned long long xm,
+                                                unsigned long long xp, unsigned long long ym,
+                                                unsigned long long yp, unsigned long long zm,
+                                                unsigned long long zp, double ci,
+                                                const EmuCoef &k) {
+    // bit-pattern differences = value differences in ulps of the common binade
+    const unsigned long long c2 = c + c;
+    const long long sx = (long long)(xm + xp - c2);
+    const long long sy = (long long)(ym + yp - c2);
+    const long long sz = (long long)(zm + zp - c2);
+    const int e = emu_exp(c);
+    const int sc = (e ? e : 1) - 1075;
+    const unsigned long long flip = c & 0x8000000000000000ull;  // negative values: minus
+    if (kDmul && kIso) {
+        unsigned long long sg;
+        const unsigned long long a = emu_abs(sx + sy + sz, &sg);
+        const double Sd = bitsd(emu_pack_mag(a, sc) | (sg ^ flip));
+        return fma(ci * k.Kx, Sd, bitsd(c));
+    }
+    return fma(ci, emu_L<kIso>(sx, sy, sz, sc, flip, k), bitsd(c));
+}
+
+// Signed fixed-point value of FP64 bits v at scale 2^(Emax' - 1079), where
+// Emax' = max(Emax, 1) is the largest biased exponent of the group (57-bit
+// magnitudes; values 64+ binades below Emax' become 0).
+__device__ __forceinline__ long long emu_fixed(unsigned long long v, int emax1) {
+    const int e = (int)((v >> 52) & 0x7ff);
+    const unsigned long long man = (v & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+    const int r = emax1 - (e ? e : 1);
+    const unsigned long long x = r < 64 ? ((man << 4) >> r) : 0ull;
+    return (v >> 63) ? -(long long)x : (long long)x;
+}
+
+// General path: any signs and exponents (rare for smooth fields).
+template <bool kIso>
+__device__ __noinline__ double emu_general_node(unsigned long long c, unsigned long long xm,
+                                                unsigned long long xp, unsigned long long ym,
+                                                unsigned long long yp, unsigned long long zm,
+                                                unsigned long long zp, double ci,
+                                                const EmuCoef k) {
+    int em = emu_exp(c);
+    em = max(em, max(emu_exp(xm), emu_exp(xp)));
+    em = max(em, max(emu_exp(ym), emu_exp(yp)));
+    em = max(em, max(emu_exp(zm), emu_exp(zp)));
+    if (em == 0x7ff) {  // Inf / NaN somewhere: plain FP64 propagates it
+        const double cc = bitsd(c);
+        const double d2x = (bitsd(xp) - cc) - (cc - bitsd(xm));
+        const double d2y = (bitsd(yp) - cc) - (cc - bitsd(ym));
+        const double d2z = (bitsd(zp) - cc) - (cc - bitsd(zm));
+        return cc + k.dtlam * (ci * ((d2x * k.ax + d2y * k.ay) + d2z * k.az));
+    }
+    const int em1 = em ? em : 1;
+    const long long fc2 = 2 * emu_fixed(c, em1);
+    const long long sx = emu_fixed(xm, em1) + emu_fixed(xp, em1) - fc2;
+    const long long sy = emu_fixed(ym, em1) + emu_fixed(yp, em1) - fc2;
+    const long long sz = emu_fixed(zm, em1) + emu_fixed(zp, em1) - fc2;
+    return fma(ci, emu_L<kIso>(sx, sy, sz, em1 - 1079, 0ull, k), bitsd(c));
+}
+
+// One node, either path (per-lane branch).
+template <bool kIso, bool kDmul>
 __device__ __forceinline__ double emu_step_node(unsigned long long c, unsigned long long xm,
                                                 unsigned long long xp, unsigned long long ym,
                                                 unsigned long long yp, unsigned long long zm,
                                                 unsigned long long zp, double ci,
                                                 const EmuCoef &k) {
-    long long sx, sy, sz;
-    int sc;
-    if (emu_same_binade(c, xm, xp, ym, yp, zm, zp)) {
-        // bit-pattern differences = value differences in ulps of the common binade
-        const unsigned long long c2 = c << 1;
-        sx = (long long)(xm + xp - c2);
-        sy = (long long)(ym + yp - c2);
-        sz = (long long)(zm + zp - c2);
-        if (c >> 63) {
-            sx = -sx;
-            sy = -sy;
-            sz = -sz;
-        }
-        const int e = emu_exp(c);
-        sc = (e ? e : 1) - 1075;
-    } else {
-        int em = emu_exp(c);
-        em = max(em, max(emu_exp(xm), emu_exp(xp)));
-        em = max(em, max(emu_exp(ym), emu_exp(yp)));
-        em = max(em, max(emu_exp(zm), emu_exp(zp)));
-        if (em == 0x7ff) {  // Inf / NaN somewhere: plain FP64 propagates it
-            const double cc = bitsd(c);
-            const double d2x = (bitsd(xp) - cc) - (cc - bitsd(xm));
-            const double d2y = (bitsd(yp) - cc) - (cc - bitsd(ym));
-            const double d2z = (bitsd(zp) - cc) - (cc - bitsd(zm));
-            return cc + k.dtlam * (ci * ((d2x * k.ax + d2y * k.ay) + d2z * k.az));
-        }
-        const int em1 = em ? em : 1;
-        const long long fc2 = 2 * emu_fixed(c, em1);
-        sx = emu_fixed(xm, em1) + emu_fixed(xp, em1) - fc2;
-        sy = emu_fixed(ym, em1) + emu_fixed(yp, em1) - fc2;
-        sz = emu_fixed(zm, em1) + emu_fixed(zp, em1) - fc2;
-        sc = em1 - 1079;
-    }
-    double L;
-    if (kIso) {
-        L = emu_scaled(sx + sy + sz, sc, k.kx);
-    } else {
-        L = (emu_scaled(sx, sc, k.kx) + emu_scaled(sy, sc, k.ky)) + emu_scaled(sz, sc, k.kz);
-    }
-    return fma(ci, L, bitsd(c));
+    if (emu_same_binade(c, xm, xp, ym, yp, zm, zp))
+        return emu_fast_node<kIso, kDmul>(c, xm, xp, ym, yp, zm, zp, ci, k);
+    return emu_general_node<kIso>(c, xm, xp, ym, yp, zm, zp, ci, k);
 }
 
 }  // namespace psd

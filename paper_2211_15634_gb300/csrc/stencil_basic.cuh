@@ -36,7 +36,8 @@ k_step_basic_emu(double *__restrict__ T2, const double *__restrict__ T,
     unsigned long long tm = Tb[p - sz], tc = Tb[p];
     for (int64_t k = k0; k < k1; ++k, p += sz) {
         const unsigned long long tp = Tb[p + sz];
-        T2[p] = emu_step_node<kIso>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy], Tb[p + sy], tm, tp, Ci[p], c);
+        T2[p] = emu_step_node<kIso, false>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy], Tb[p + sy], tm, tp,
+                                           Ci[p], c);
         tm = tc;
         tc = tp;
     }

@@ -30,7 +30,7 @@ cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, 
     if (zmarch_supported(g, 8, T2, T, Ci))
         return launch_zmarch(iso ? Z_F64_EMU_ISO : Z_F64_EMU_ANISO, T2, T, nullptr, Ci, c, g, s);
     const EmuCoef ek{emu_const(c.dtlam * c.ax), emu_const(c.dtlam * c.ay), emu_const(c.dtlam * c.az),
-                     c.dtlam, c.ax, c.ay, c.az};
+                     c.dtlam, c.ax, c.ay, c.az, c.dtlam * c.ax};
     return launch_step_basic_emu(T2, T, Ci, ek, iso, g.nx, g.ny, g.nz, sm_count(), s);
 }
 

@@ -16,6 +16,9 @@
 // are 16-byte aligned.
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
+#include <cstring>
+
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -41,6 +44,8 @@ template <>
 struct ZTraits<Z_F64_EMU_ANISO> : ZTraits<Z_F64_EMU_ISO> {};
 template <>
 struct ZTraits<Z_F64_NATIVE> : ZTraits<Z_F64_EMU_ISO> {};
+template <>
+struct ZTraits<Z_F64_EMU_ISO_DMUL> : ZTraits<Z_F64_EMU_ISO> {};
 template <>
 struct ZTraits<Z_F32> {
     using E = float;
@@ -106,20 +111,24 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
             }
         }
     }
-    auto tst = [&](int q) -> const E * { return sT + ((q - (k0 - 1)) % NST) * (TBA / sizeof(E)); };
-    auto twait = [&](int q) -> bool {
-        return mbar_wait(&bar[(q - (k0 - 1)) % NST], ((q - (k0 - 1)) / NST) & 1);
-    };
-    auto cst = [&](int q) -> const E * { return sC + ((q - k0) % NSC) * (CBA / sizeof(E)); };
-    auto cwait = [&](int q) -> bool {
-        return mbar_wait(&bar[NST + (q - k0) % NSC], ((q - k0) / NSC) & 1);
+    // Stage bookkeeping without divisions: T plane k0-1+i sits in stage i % NST
+    // and Ci plane k0+i in stage i % NSC; bit s of tpar / cpar is the parity of
+    // the next completion of stage s.
+    constexpr unsigned TSTRIDE = TBA / sizeof(E), CSTRIDE = CBA / sizeof(E);
+    unsigned tpar = 0u, cpar = 0u;
+    auto tnext = [](int s) { return s + 1 == NST ? 0 : s + 1; };
+    auto cnext = [](int s) { return s + 1 == NSC ? 0 : s + 1; };
+    auto acquire = [&](uint64_t *b, unsigned &par, int s) -> bool {
+        const unsigned ph = (par >> s) & 1u;
+        par ^= 1u << s;
+        return mbar_wait(b, ph);
     };
 
     const int row = ty + 1, col = HX + lane * PX;
-    bool ok = twait(k0 - 1);
-    V qm = *(const V *)(tst(k0 - 1) + row * W + col);
-    ok = twait(k0) && ok;
-    V qc = *(const V *)(tst(k0) + row * W + col);
+    bool ok = acquire(&bar[0], tpar, 0);
+    V qm = *(const V *)(sT + row * W + col);
+    ok = acquire(&bar[1 % NST], tpar, 1 % NST) && ok;
+    V qc = *(const V *)(sT + (1 % NST) * TSTRIDE + row * W + col);
     if (!ok) {
         s_abort = 1;
         atomicOr(&g_zmarch_error, 1u);
@@ -128,10 +137,9 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
     if (s_abort) return;
     if (threadIdx.x == 0) {
         const int q = k0 - 1 + NST;
-        if (q <= k1) {
-            const int s = 0;  // stage of plane k0-1
-            mbar_expect_tx(&bar[s], TB);
-            tma_load_3d(sT + s * (TBA / sizeof(E)), &tmT, &bar[s], X0 - HX, Y0 - 1, q);
+        if (q <= k1) {  // stage 0 held plane k0-1
+            mbar_expect_tx(&bar[0], TB);
+            tma_load_3d(sT, &tmT, &bar[0], X0 - HX, Y0 - 1, q);
         }
     }
 
@@ -141,16 +149,19 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
     bool all_x = gx0 >= 1 && gx0 + PX - 1 <= p.nx - 2;
     E *__restrict__ T2 = (E *)T2v;
     E *__restrict__ comp = (E *)compv;
+    int sk = 1 % NST;  // T stage of plane k
+    int ck = 0;        // Ci stage of plane k
 
     for (int k = k0; k < k1; ++k) {
-        ok = twait(k + 1);
-        const E *Tk = tst(k);
-        const V qn = *(const V *)(tst(k + 1) + row * W + col);
+        const int sk1 = tnext(sk);
+        ok = acquire(&bar[sk1], tpar, sk1);
+        ok = acquire(&bar[NST + ck], cpar, ck) && ok;
+        const E *Tk = sT + sk * TSTRIDE;
+        const V qn = *(const V *)(sT + sk1 * TSTRIDE + row * W + col);
         const E left = Tk[row * W + col - 1], right = Tk[row * W + col + PX];
         const V up = *(const V *)(Tk + (row - 1) * W + col);
         const V dn = *(const V *)(Tk + (row + 1) * W + col);
-        ok = cwait(k) && ok;
-        const V civ = *(const V *)(cst(k) + ty * BX + lane * PX);
+        const V civ = *(const V *)(sC + ck * CSTRIDE + ty * BX + lane * PX);
 
         if (row_ok) {
             const int64_t base = (int64_t)gx0 + p.nx * ((int64_t)gy + p.ny * (int64_t)k);
@@ -165,6 +176,76 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
                     }
             }
             V out;
+            if constexpr (MODE == Z_F64_EMU_ISO || MODE == Z_F64_EMU_ANISO ||
+                          MODE == Z_F64_EMU_ISO_DMUL) {
+                constexpr bool kIso = MODE != Z_F64_EMU_ANISO;
+                constexpr bool kDmul = MODE == Z_F64_EMU_ISO_DMUL;
+                unsigned long long c[PX], xm[PX], xp[PX], ym[PX], yp[PX], zm[PX], zp[PX];
+#pragma unroll
+                for (int i = 0; i < PX; ++i) {
+                    c[i] = dbits((double)vget<V, E>(qc, i));
+                    xm[i] = dbits((double)(i == 0 ? left : vget<V, E>(qc, i - 1)));
+                    xp[i] = dbits((double)(i == PX - 1 ? right : vget<V, E>(qc, i + 1)));
+                    ym[i] = dbits((double)vget<V, E>(up, i));
+                    yp[i] = dbits((double)vget<V, E>(dn, i));
+                    zm[i] = dbits((double)vget<V, E>(qm, i));
+                    zp[i] = dbits((double)vget<V, E>(qn, i));
+                }
+                // one check over the 5*PX + 2 distinct values of this thread's PX stencils
+                unsigned hw[5 * PX + 1];
+                hw[0] = (unsigned)(xm[0] >> 32);
+                hw[1] = (unsigned)(xp[PX - 1] >> 32);
+#pragma unroll
+                for (int i = 0; i < PX; ++i) {
+                    hw[2 + 4 * i] = (unsigned)(ym[i] >> 32);
+                    hw[3 + 4 * i] = (unsigned)(yp[i] >> 32);
+                    hw[4 + 4 * i] = (unsigned)(zm[i] >> 32);
+                    hw[5 + 4 * i] = (unsigned)(zp[i] >> 32);
+                }
+#pragma unroll
+                for (int i = 1; i < PX; ++i) hw[1 + 4 * PX + i] = (unsigned)(c[i] >> 32);
+                const unsigned hc = (unsigned)(c[0] >> 32);
+                if (!all_x) {
+                    // Lanes at the grid's x edges: a node that is not stored (x = 0,
+                    // x = nx-1, or past the grid where TMA filled zeros) must not
+                    // send the warp to the general path, so its private values are
+                    // replaced by the reference word.
+                    bool use[PX];
+#pragma unroll
+                    for (int i = 0; i < PX; ++i) use[i] = gx0 + i >= 1 && gx0 + i <= p.nx - 2;
+                    if (!use[0]) hw[0] = hc;       // left: x-neighbour of node 0 only
+                    if (!use[PX - 1]) hw[1] = hc;  // right: x-neighbour of the last node only
+#pragma unroll
+                    for (int i = 0; i < PX; ++i) {
+                        if (!use[i]) {  // y and z neighbours belong to node i alone
+                            hw[2 + 4 * i] = hc;
+                            hw[3 + 4 * i] = hc;
+                            hw[4 + 4 * i] = hc;
+                            hw[5 + 4 * i] = hc;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 1; i < PX; ++i) {  // centre i is also node i-1's and i+1's x-neighbour
+                        const bool need = use[i] || use[i - 1] || (i + 1 < PX && use[i + 1]);
+                        if (!need) hw[1 + 4 * PX + i] = hc;
+                    }
+                }
+                const bool fast = emu_same_binade_hi(hw, hc);
+                // warp-uniform branch: smooth fields take the short fast path
+                if (__all_sync(0xffffffffu, fast)) {
+#pragma unroll
+                    for (int i = 0; i < PX; ++i)
+                        reinterpret_cast<E *>(&out)[i] = emu_fast_node<kIso, kDmul>(
+                            c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i],
+                            (double)vget<V, E>(civ, i), p.ek);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < PX; ++i)
+                        reinterpret_cast<E *>(&out)[i] = emu_step_node<kIso, kDmul>(
+                            c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i],
+                            (double)vget<V, E>(civ, i), p.ek);
+                }
+            } else
 #pragma unroll
             for (int i = 0; i < PX; ++i) {
                 const E c = vget<V, E>(qc, i);
@@ -174,11 +255,7 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
                 const E zm = vget<V, E>(qm, i), zp = vget<V, E>(qn, i);
                 const E ci = vget<V, E>(civ, i);
                 E r;
-                if constexpr (MODE == Z_F64_EMU_ISO || MODE == Z_F64_EMU_ANISO) {
-                    r = emu_step_node<MODE == Z_F64_EMU_ISO>(
-                        dbits((double)c), dbits((double)xm), dbits((double)xp), dbits((double)ym),
-                        dbits((double)yp), dbits((double)zm), dbits((double)zp), (double)ci, p.ek);
-                } else if constexpr (MODE == Z_F64_NATIVE) {
+                if constexpr (MODE == Z_F64_NATIVE) {
                     const double d2x = (xp - c) - (c - xm), d2y = (yp - c) - (c - ym);
                     const double d2z = (zp - c) - (c - zm);
                     r = c + p.ek.dtlam * (ci * ((d2x * p.ek.ax + d2y * p.ek.ay) + d2z * p.ek.az));
@@ -212,6 +289,7 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
                 }
             }
         }
+        const int ck1 = cnext(ck);
         if (!ok) {
             s_abort = 1;
             atomicOr(&g_zmarch_error, 1u);
@@ -219,19 +297,17 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
         __syncthreads();  // every thread is done with plane k's T stage and Ci stage
         if (s_abort) return;
         if (threadIdx.x == 0) {
-            const int q = k + NST;
-            if (q <= k1) {
-                const int s = (k - (k0 - 1)) % NST;
-                mbar_expect_tx(&bar[s], TB);
-                tma_load_3d(sT + s * (TBA / sizeof(E)), &tmT, &bar[s], X0 - HX, Y0 - 1, q);
+            if (k + NST <= k1) {  // plane k's T stage takes plane k + NST
+                mbar_expect_tx(&bar[sk], TB);
+                tma_load_3d(sT + sk * TSTRIDE, &tmT, &bar[sk], X0 - HX, Y0 - 1, k + NST);
             }
-            const int qc2 = k + NSC;
-            if (qc2 < k1) {
-                const int s = (k - k0) % NSC;
-                mbar_expect_tx(&bar[NST + s], CB);
-                tma_load_3d(sC + s * (CBA / sizeof(E)), &tmC, &bar[NST + s], X0, Y0, qc2);
+            if (k + NSC < k1) {  // plane k's Ci stage takes Ci plane k + NSC
+                mbar_expect_tx(&bar[NST + ck], CB);
+                tma_load_3d(sC + ck * CSTRIDE, &tmC, &bar[NST + ck], X0, Y0, k + NSC);
             }
         }
+        sk = sk1;
+        ck = ck1;
         qm = qc;
         qc = qn;
     }
@@ -297,11 +373,13 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const vo
     if (kchunk <= 0) {
         // Short chunks keep many CTAs in flight (no wave tail) while consecutive
         // CTAs - neighbouring tiles of one chunk - share their halo planes in L2.
-        // 16 planes measured best at 512^3; small grids go down to 4 planes so
-        // that they still fill the GPU (about 64 CTAs per SM).
+        // At 512^3 the best chunk measured 16 planes (FP32) and 32 (FP64); small
+        // grids go down to 4 planes so that they still fill the GPU (about 64
+        // CTAs per SM).
         const int64_t target = 64LL * sm_count();
+        const int64_t kmax = sizeof(E) == 8 ? 32 : 16;
         int64_t kc = (g.nz - 2) * tiles / target;
-        kchunk = (int)(kc < 4 ? 4 : (kc > 16 ? 16 : kc));
+        kchunk = (int)(kc < 4 ? 4 : (kc > kmax ? kmax : kc));
     }
     const int64_t gz = (g.nz - 2 + kchunk - 1) / kchunk;
     if (tiles > 0x7fffffffLL || gz > 65535) return cudaErrorInvalidConfiguration;
@@ -318,7 +396,7 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const vo
 static ZParams make_params(StepCoef c) {
     ZParams p{};
     p.ek = EmuCoef{emu_const(c.dtlam * c.ax), emu_const(c.dtlam * c.ay), emu_const(c.dtlam * c.az),
-                   c.dtlam, c.ax, c.ay, c.az};
+                   c.dtlam, c.ax, c.ay, c.az, c.dtlam * c.ax};
     p.fdtlam = (float)c.dtlam;
     p.fax = (float)c.ax;
     p.fay = (float)c.ay;
@@ -336,12 +414,24 @@ cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const v
     const ZParams p = make_params(c);
     const int kchunk = env_int("PS_KCHUNK", 0);
     const bool positive = c.dtlam * c.ax > 0 && c.dtlam * c.ay > 0 && c.dtlam * c.az > 0;
+    // Isotropic FP64 grids default to fma(Ci*K, S, T) (two FP64 ops, fewest
+    // integer ops: measured fastest).  PS_F64_VARIANT selects an alternative
+    // for measurements: "umul" = one DFMA plus a 64-bit high multiply,
+    // "by16" = 64 x 16 tiles.
+    const char *var = getenv("PS_F64_VARIANT");
+    const bool dmul = !(var && (strcmp(var, "umul") == 0 || strcmp(var, "by16") == 0));
+    const bool by16 = var && strcmp(var, "by16") == 0;
     switch (mode) {
         case Z_F64_EMU_ISO:
         case Z_F64_EMU_ANISO:
             if (!positive) return launch_zmarch_t<Z_F64_NATIVE, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
-            if (mode == Z_F64_EMU_ISO)
+            if (mode == Z_F64_EMU_ISO) {
+                if (dmul)
+                    return launch_zmarch_t<Z_F64_EMU_ISO_DMUL, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+                if (by16)
+                    return launch_zmarch_t<Z_F64_EMU_ISO, 16, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
                 return launch_zmarch_t<Z_F64_EMU_ISO, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            }
             return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F64_NATIVE:
             return launch_zmarch_t<Z_F64_NATIVE, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);

@@ -6,7 +6,14 @@
 
 namespace psd {
 
-enum ZMode { Z_F64_EMU_ISO = 0, Z_F64_EMU_ANISO = 1, Z_F64_NATIVE = 2, Z_F32 = 3, Z_F32_COMP = 4 };
+enum ZMode {
+    Z_F64_EMU_ISO = 0,       // one DFMA per node, 64x64 high multiply by K
+    Z_F64_EMU_ANISO = 1,     // as above, one product per axis
+    Z_F64_NATIVE = 2,        // plain FP64 instructions
+    Z_F32 = 3,
+    Z_F32_COMP = 4,
+    Z_F64_EMU_ISO_DMUL = 5,  // two FP64 ops per node: fma(Ci*K, S, T)
+};
 
 struct ZParams {
     int64_t nx, ny, nz;
