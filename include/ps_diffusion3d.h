@@ -177,6 +177,26 @@ int ps_diffusion3d_stable_dt(double *dt_host, const void *Ci, int64_t nx, int64_
 /* sum_p A[p]*B[p], accumulated in FP64, to a device double. */
 int ps_dot(double *out_dev, const void *A, const void *B, int64_t n, int dtype, void *workspace,
            void *stream);
+/* sum_p A[p]*B[p] in FP64, like ps_dot, for callers that cannot allocate
+ * device memory (for example a plugin inside a host application that owns
+ * every device allocation, or a loop that must not allocate while it runs):
+ * it takes no workspace and allocates nothing.  The paper has no counterpart;
+ * this is a library convenience.
+ *   - Scratch: the per-block partial sums live in a 256 KiB array inside
+ *     the library image, resident on every GPU that uses the library until
+ *     the process exits.  n may be at most 134217728 (4096 elements per
+ *     partial x 32768 partials); larger n returns PS_ERR_UNSUPPORTED and
+ *     launches nothing.
+ *   - The first call on a device looks up the array's device address once;
+ *     make that first call before any stream capture on the device.
+ *   - Every call shares the one array (it keeps the last call's partials,
+ *     each call overwrites what it reads): calls that can overlap on the GPU,
+ *     e.g. on two streams, race and must be serialized by the caller.
+ *   - Rounding: a contiguous-chunk partition, so results may differ from
+ *     ps_dot's in the last bits; each call is deterministic. */
+int ps_dot_static(double *out_dev, const void *A, const void *B, int64_t n, int dtype,
+                  void *stream);
+
 /* Loss of the inverse problem: 1/2 * sum_p (A[p]-B[p])^2 in FP64 to
  * *out_dev, and, if R is not NULL, the residual R = A - B (the cotangent
  * dL/dA) in `dtype`. */

@@ -64,6 +64,7 @@ SIGNATURES = {
     "ps_diffusion3d_stable_dt": (_I, [ctypes.POINTER(_D), _P, _I64, _I64, _I64, _D, _D, _D, _D, _I,
                                       _P, _P]),
     "ps_dot": (_I, [_P, _P, _P, _I64, _I, _P, _P]),
+    "ps_dot_static": (_I, [_P, _P, _P, _I64, _I, _P]),
     "ps_half_sq_dist": (_I, [_P, _P, _P, _P, _I64, _I, _P, _P]),
     "ps_to_deviation": (_I, [_P, _P, _D, _I64, _P]),
     "ps_from_deviation": (_I, [_P, _P, _D, _I64, _P]),

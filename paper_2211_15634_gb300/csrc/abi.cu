@@ -31,6 +31,9 @@ static int cuda_fail(cudaError_t e, const char *where) {
     return fail(PS_ERR_CUDA, "%s: CUDA error %d (%s)", where, (int)e, cudaGetErrorString(e));
 }
 
+int api_fail(int status, const char *msg) { return fail(status, "%s", msg); }
+int api_cuda_fail(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+
 int current_device() {
     int d = 0;
     cudaGetDevice(&d);

@@ -28,6 +28,10 @@ struct Grid3 {
 int sm_count();
 int current_device();
 
+// Record a message for ps_last_error() and return the status (abi.cu).
+int api_fail(int status, const char *msg);
+int api_cuda_fail(cudaError_t e, const char *where);
+
 // ---- forward step kernels (step_f64.cu, step_f32.cu) ----
 cudaError_t launch_step_f64_native(double *T2, const double *T, const double *Ci, StepCoef c,
                                    Grid3 g, cudaStream_t s);
