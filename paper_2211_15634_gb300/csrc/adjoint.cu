@@ -5,8 +5,11 @@
 //   w[q]      = dt*lam*Ci[q]*ybar[q] at interior q, 0 elsewhere (and outside),
 //   Tbar[p]   = ybar[p] + sum_d (w[p-e_d] - 2 w[p] + w[p+e_d]) * _d^2  (all p),
 //   Cibar[q] += dt*lam*ybar[q]*Lap(T_t)[q]                             (interior q).
+#include <cstdlib>
+
 #include "internal.h"
 #include "stencil_basic.cuh"
+#include "zmarch.h"
 
 namespace psd {
 
@@ -74,14 +77,26 @@ static cudaError_t launch_adjoint_basic(F *Tbar, F *Cibar, const F *ybar, const 
     return cudaGetLastError();
 }
 
+static bool use_tma(Grid3 g, int esz, const void *a, const void *b, const void *c, const void *d,
+                    const void *e) {
+    const void *ptrs[5] = {c, d, e, a, b};  // the three TMA-read fields first
+    const char *v = getenv("PS_ADJ_PLAIN");
+    if (v && v[0] == '1') return false;
+    return adjoint_zmarch_supported(g, esz, ptrs, 5);
+}
+
 cudaError_t launch_adjoint_f64(double *Tbar, double *Cibar, const double *ybar, const double *T,
                                const double *Ci, StepCoef c, Grid3 g, cudaStream_t s) {
+    if (use_tma(g, 8, Tbar, Cibar, ybar, T, Ci))
+        return launch_adjoint_zmarch<double>(Tbar, Cibar, ybar, T, Ci, c, g, s);
     return launch_adjoint_basic<double>(Tbar, Cibar, ybar, T, Ci,
                                         CoefT<double>{c.dtlam, c.ax, c.ay, c.az}, g, s);
 }
 
 cudaError_t launch_adjoint_f32(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                const float *Ci, StepCoef c, Grid3 g, cudaStream_t s) {
+    if (use_tma(g, 4, Tbar, Cibar, ybar, T, Ci))
+        return launch_adjoint_zmarch<float>(Tbar, Cibar, ybar, T, Ci, c, g, s);
     return launch_adjoint_basic<float>(
         Tbar, Cibar, ybar, T, Ci,
         CoefT<float>{(float)c.dtlam, (float)c.ax, (float)c.ay, (float)c.az}, g, s);

@@ -213,6 +213,44 @@ __device__ __noinline__ double emu_general_node(unsigned long long c, unsigned l
     return fma(ci, emu_L<kIso>(sx, sy, sz, em1 - 1079, 0ull, k), bitsd(c));
 }
 
+// Exact per-axis second-difference sums of seven arbitrary finite FP64 values
+// (bit patterns) in fixed point at the largest exponent of the seven:
+// value(S_d) = S_d * 2^sc.  Returns false if any value is Inf/NaN.
+__device__ __forceinline__ bool emu_sums_general(unsigned long long c, unsigned long long xm,
+                                                 unsigned long long xp, unsigned long long ym,
+                                                 unsigned long long yp, unsigned long long zm,
+                                                 unsigned long long zp, long long &sx,
+                                                 long long &sy, long long &sz, int &sc) {
+    int em = emu_exp(c);
+    em = max(em, max(emu_exp(xm), emu_exp(xp)));
+    em = max(em, max(emu_exp(ym), emu_exp(yp)));
+    em = max(em, max(emu_exp(zm), emu_exp(zp)));
+    if (em == 0x7ff) return false;
+    const int em1 = em ? em : 1;
+    const long long fc2 = 2 * emu_fixed(c, em1);
+    sx = emu_fixed(xm, em1) + emu_fixed(xp, em1) - fc2;
+    sy = emu_fixed(ym, em1) + emu_fixed(yp, em1) - fc2;
+    sz = emu_fixed(zm, em1) + emu_fixed(zp, em1) - fc2;
+    sc = em1 - 1079;
+    return true;
+}
+
+// Exact FP64 of S * 2^sc (signed), via emu_pack_mag.
+__device__ __forceinline__ double emu_pack(long long S, int sc) {
+    unsigned long long sg;
+    const unsigned long long a = emu_abs(S, &sg);
+    return bitsd(emu_pack_mag(a, sc) | sg);
+}
+
+// base + sum_d K_d * S_d * 2^sc with one DFMA per distinct coefficient
+// (one in total when the grid is isotropic).  Kx/Ky/Kz are FP64 constants.
+template <bool kIso>
+__device__ __forceinline__ double emu_axpy3(double base, long long sx, long long sy, long long sz,
+                                            int sc, double Kx, double Ky, double Kz) {
+    if (kIso) return fma(Kx, emu_pack(sx + sy + sz, sc), base);
+    return fma(Kz, emu_pack(sz, sc), fma(Ky, emu_pack(sy, sc), fma(Kx, emu_pack(sx, sc), base)));
+}
+
 // One node, either path (per-lane branch).
 template <bool kIso, bool kDmul>
 __device__ __forceinline__ double emu_step_node(unsigned long long c, unsigned long long xm,

@@ -44,6 +44,7 @@ cudaError_t launch_step_f32_comp(float *T2, const float *T, float *comp, const f
 const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c);
 const char *step_f32_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci);
 unsigned zmarch_device_error(bool clear);
+unsigned adjoint_device_error(bool clear);
 
 // ---- helpers (misc.cu) ----
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);

@@ -328,7 +328,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static bool make_map(CUtensorMap *m, const void *ptr, int esz, Grid3 g, unsigned bx, unsigned by) {
+bool make_tensor_map_3d(CUtensorMap *m, const void *ptr, int esz, Grid3 g, unsigned bx, unsigned by) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
@@ -366,7 +366,8 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const vo
         attr_done[dev] = true;
     }
     CUtensorMap mT, mC;
-    if (!make_map(&mT, T, sizeof(E), g, W, H) || !make_map(&mC, Ci, sizeof(E), g, BX, BY))
+    if (!make_tensor_map_3d(&mT, T, sizeof(E), g, W, H) ||
+        !make_tensor_map_3d(&mC, Ci, sizeof(E), g, BX, BY))
         return cudaErrorInvalidValue;
     const int64_t ntx = (g.nx + BX - 1) / BX, nty = (g.ny + BY - 1) / BY;
     const int64_t tiles = ntx * nty;

@@ -1,6 +1,8 @@
 // Declarations of the TMA-fed z-march step kernels (zmarch.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "emu64.cuh"
 #include "internal.h"
 
@@ -24,6 +26,15 @@ struct ZParams {
 
 // True when the TMA path can serve this grid and these pointers.
 bool zmarch_supported(Grid3 g, int esz, const void *a, const void *b, const void *c);
+// 3-D tiled tensor map over a (nz, ny, nx) field with a bx x by x 1 box.
+bool make_tensor_map_3d(CUtensorMap *m, const void *ptr, int esz, Grid3 g, unsigned bx, unsigned by);
+
+// TMA-fed transposed step (adjoint_zmarch.cu).
+bool adjoint_zmarch_supported(Grid3 g, int esz, const void *const *ptrs, int nptr);
+template <typename E>
+cudaError_t launch_adjoint_zmarch(E *Tbar, E *Cibar, const E *ybar, const E *T, const E *Ci,
+                                  StepCoef c, Grid3 g, cudaStream_t s);
+unsigned adjoint_device_error(bool clear);
 cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
                           Grid3 g, cudaStream_t s);
 unsigned zmarch_device_error(bool clear);

@@ -180,7 +180,8 @@ def test_deviation_roundtrip():
 
 
 # ------------------------------------------------------------------ adjoint
-@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 7, 6), (37, 29, 23), (66, 19, 20)])
+@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 7, 6), (37, 29, 23), (66, 19, 20), (4, 5, 6),
+                                   (68, 21, 19), (132, 11, 9), (256, 9, 17), (128, 16, 3)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_adjoint_step_matches_oracle(shape, dtype):
     nx, ny, nz = shape
