@@ -49,7 +49,41 @@ def parse_args():
     p.add_argument("--no-secondary", action="store_true", help="skip FP32 / gradient / batch lines")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--kernel-loop", choices=["step", "adjoint"], default=None,
+                   help="profiling aid: launch only this kernel --reps times at --size (no JSON)")
+    p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    p.add_argument("--reps", type=int, default=4)
     return p.parse_args()
+
+
+def run_kernel_loop(args):
+    """Launch one kernel family a few times on --size^3 workload fields (for ncu)."""
+    import torch
+    from paper_2211_15634_gb300 import api, inputs
+    n = args.size
+    T0, Ci, inv = fields(n)
+    dev = torch.device("cuda")
+    T = torch.from_numpy(T0).to(dev)
+    C = torch.from_numpy(Ci).to(dev)
+    if args.dtype == "f32":
+        T, C = api.to_deviation(T, 1.7), api.to_f32(C)
+    T2 = T.clone()
+    dt = api.stable_dt(C, 1.0)
+    if args.kernel_loop == "step":
+        for i in range(args.reps):
+            src, dst = (T, T2) if i % 2 == 0 else (T2, T)
+            api.step(dst, src, C, 1.0, dt, inv)
+        name = api.step_kernel_name(T2, T, C, 1.0, dt, inv)
+    else:
+        ybar = T2 - T.mean()
+        Tbar = torch.empty_like(T)
+        Cib = torch.zeros_like(T)
+        for _ in range(args.reps):
+            api.adjoint(Tbar, Cib, ybar, T, C, 1.0, dt, inv)
+        name = "adjoint"
+    torch.cuda.synchronize()
+    log(f"kernel loop done: {name} x{args.reps} at {n}^3 {args.dtype}, device_error={api.device_error()}")
+    return 0
 
 
 # ------------------------------------------------------------------ system
@@ -303,9 +337,17 @@ def secondary_metrics(torch, api, ag, inputs, log):
             probs.append(dict(T=Tq, T2=Tq.clone(), Ci=Cq, lam=1.0, dt=dtq,
                               inv_spacing=inputs.inverse_spacing(nq, nq, nq)))
             bytes_per_step += 3 * nq ** 3 * esz
-        b = api.Batch(probs)
+        from paper_2211_15634_gb300 import tuner
+        b0 = api.Batch(probs)  # library default tile for every problem
+        t_0 = timed(lambda: b0.run(nt, graph=True), reps=1)
+        out[f"batch_{name}_default_tile_teff_gbs"] = round(bytes_per_step * nt / t_0 / 1e9, 1)
+        del b0
+        api.clear_graph_cache()
+        best = tuner.tune(probs)  # per size class, cached as JSON
+        b = tuner.tuned_batch(probs)
         t_b = timed(lambda: b.run(nt, graph=True), reps=2)
         out[f"batch_{name}_teff_gbs"] = round(bytes_per_step * nt / t_b / 1e9, 1)
+        out[f"batch_{name}_tiles"] = {f"{lo}-{hi}": list(t) for (lo, hi), t in sorted(best.items())}
 
         def per_problem():
             for p in probs:
@@ -462,6 +504,8 @@ def run_ours(args):
 
 def main():
     args = parse_args()
+    if args.kernel_loop:
+        return run_kernel_loop(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

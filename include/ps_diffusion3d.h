@@ -224,11 +224,14 @@ typedef struct {
     const void *Ci;   /* device field */
     double lam, dt, _dx, _dy, _dz;
     int64_t nx, ny, nz;
+    int32_t tile_x, tile_y, tile_z; /* this problem's work-item shape; 0 = the call's */
+    int32_t reserved;               /* set to 0 */
 } ps_problem;
 
 /* Bytes of the table for these problems with the given tile shape
- * (tile_x, tile_y: interior nodes per work item in x and y; tile_z: nodes
- * per z-chunk; 0 picks the library default for the dtype). */
+ * (tile_x, tile_y: interior nodes per work item in x and y, tile_x*tile_y
+ * <= 4096; tile_z: nodes per z-chunk; 0 picks the library default for the
+ * dtype; a problem's own nonzero tile fields override these). */
 size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
                             int tile_z);
 /* Fill host_buf (bytes >= ps_batch_table_bytes) with the table.  Checks

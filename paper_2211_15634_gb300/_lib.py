@@ -38,7 +38,8 @@ class PsProblem(ctypes.Structure):
     _fields_ = [("T", ctypes.c_void_p), ("T2", ctypes.c_void_p), ("Ci", ctypes.c_void_p),
                 ("lam", ctypes.c_double), ("dt", ctypes.c_double), ("_dx", ctypes.c_double),
                 ("_dy", ctypes.c_double), ("_dz", ctypes.c_double), ("nx", ctypes.c_int64),
-                ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+                ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("tile_x", ctypes.c_int32),
+                ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes)

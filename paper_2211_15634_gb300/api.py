@@ -215,7 +215,9 @@ class Batch:
 
     ``problems`` is a list of dicts with keys ``T, T2, Ci`` (CUDA tensors of
     one dtype, any cubic or non-cubic shape), ``lam``, ``dt`` and
-    ``inv_spacing``.  T2's boundary must equal T's (e.g. ``T2 = T.clone()``).
+    ``inv_spacing``, and optionally ``tile`` = (tile_x, tile_y, tile_z) for
+    that problem's work items (see ``tuner.tuned_batch``).  T2's boundary must
+    equal T's (e.g. ``T2 = T.clone()``).
     """
 
     def __init__(self, problems, tile=(0, 0, 0)):
@@ -229,9 +231,10 @@ class Batch:
         for q, p in enumerate(problems):
             _same(p["T"], p["T2"], p["Ci"])
             nx, ny, nz = _grid(p["T"])
+            tx, ty, tz = p.get("tile", (0, 0, 0))
             arr[q] = _lib.PsProblem(_field(p["T"], "T", self.code), _field(p["T2"], "T2", self.code),
                                     _field(p["Ci"], "Ci", self.code), p["lam"], p["dt"],
-                                    *p["inv_spacing"], nx, ny, nz)
+                                    *p["inv_spacing"], nx, ny, nz, tx, ty, tz, 0)
         nbytes = lib.ps_batch_table_bytes(arr, len(problems), self.code, *tile)
         if nbytes == 0:
             raise ValueError("invalid batch description")

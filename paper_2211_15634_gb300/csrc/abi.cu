@@ -11,6 +11,7 @@
 #include <tuple>
 #include <vector>
 
+#include "emu64.cuh"
 #include "internal.h"
 
 namespace psd {
@@ -435,9 +436,19 @@ static int resolve_tiles(int dtype, int *tx, int *ty, int *tz) {
     if (*tx == 0) *tx = dx;
     if (*ty == 0) *ty = dy;
     if (*tz == 0) *tz = dz;
-    if (*tx < 1 || *ty < 1 || *tz < 1 || (int64_t)*tx * *ty > (1 << 16))
-        return fail(PS_ERR_ARG, "tile %d x %d x %d is invalid", *tx, *ty, *tz);
+    if (*tx < 1 || *ty < 1 || *tz < 1 || (int64_t)*tx * *ty > 4096 || *tx > 4096 || *ty > 4096 ||
+        *tz > 32767)
+        return fail(PS_ERR_ARG, "tile %d x %d x %d is invalid (x*y <= 4096, z <= 32767)", *tx, *ty, *tz);
     return PS_OK;
+}
+
+// A problem's own tile fields override the call's.
+static int problem_tiles(const ps_problem &p, int dtype, int tx, int ty, int tz, int *ox, int *oy,
+                         int *oz) {
+    *ox = p.tile_x ? p.tile_x : tx;
+    *oy = p.tile_y ? p.tile_y : ty;
+    *oz = p.tile_z ? p.tile_z : tz;
+    return resolve_tiles(dtype, ox, oy, oz);
 }
 
 static int64_t items_of(const ps_problem &p, int tx, int ty, int tz) {
@@ -455,8 +466,10 @@ size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int t
     if (resolve_tiles(dtype, &tile_x, &tile_y, &tile_z) != PS_OK) return 0;
     int64_t nitems = 0;
     for (int q = 0; q < nprob; ++q) {
+        int tx, ty, tz;
         if (probs[q].nx < 3 || probs[q].ny < 3 || probs[q].nz < 3) return 0;
-        nitems += items_of(probs[q], tile_x, tile_y, tile_z);
+        if (problem_tiles(probs[q], dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz) != PS_OK) return 0;
+        nitems += items_of(probs[q], tx, ty, tz);
     }
     return table_bytes(nprob, nitems);
 }
@@ -472,9 +485,12 @@ int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, i
         const ps_problem &p = probs[q];
         int st = check_step_args(p.T2, p.T, p.Ci, p.lam, p.dt, p._dx, p._dy, p._dz, p.nx, p.ny, p.nz, dtype);
         if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
-        if (p.nx - 2 + tile_x > (1LL << 31) || p.ny - 2 + tile_y > (1LL << 31) || p.nz - 2 + tile_z > (1LL << 31))
+        int tx, ty, tz;
+        st = problem_tiles(p, dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz);
+        if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
+        if (p.nx + tx > (1LL << 31) || p.ny + ty > (1LL << 31) || p.nz + tz > (1LL << 31))
             return fail(PS_ERR_ARG, "problem %d is too large for the batch table", q);
-        nitems += items_of(p, tile_x, tile_y, tile_z);
+        nitems += items_of(p, tx, ty, tz);
     }
     const size_t need = table_bytes(nprob, nitems);
     if (bytes < need) return fail(PS_ERR_ARG, "table buffer has %zu bytes, needs %zu", bytes, need);
@@ -495,14 +511,44 @@ int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, i
     for (int q = 0; q < nprob; ++q) {
         const ps_problem &p = probs[q];
         const StepCoef c = make_coef(p.lam, p.dt, p._dx, p._dy, p._dz);
-        bp[q] = BatchProblem{p.T, p.T2, p.Ci, c.dtlam, c.ax, c.ay, c.az, p.nx, p.ny, p.nz};
-        for (int64_t k0 = 1; k0 < p.nz - 1; k0 += tile_z)
-            for (int64_t j0 = 1; j0 < p.ny - 1; j0 += tile_y)
-                for (int64_t i0 = 1; i0 < p.nx - 1; i0 += tile_x) {
-                    const int64_t w = std::min<int64_t>(tile_x, p.nx - 1 - i0) *
-                                      std::min<int64_t>(tile_y, p.ny - 1 - j0) *
-                                      std::min<int64_t>(tile_z, p.nz - 1 - k0);
-                    work.push_back({w, BatchItem{q, (int32_t)i0, (int32_t)j0, (int32_t)k0}});
+        BatchProblem r{};
+        r.T = p.T;
+        r.T2 = p.T2;
+        r.Ci = p.Ci;
+        r.dtlam = c.dtlam;
+        r.ax = c.ax;
+        r.ay = c.ay;
+        r.az = c.az;
+        r.nx = p.nx;
+        r.ny = p.ny;
+        r.nz = p.nz;
+        const double K[3] = {c.dtlam * c.ax, c.dtlam * c.ay, c.dtlam * c.az};
+        bool emu = true;
+        for (double v : K) emu = emu && v > 2.2250738585072014e-308 && v < 1e300;
+        if (emu) {
+            const EmuK kx = emu_const(K[0]), ky = emu_const(K[1]), kz = emu_const(K[2]);
+            r.kxm = kx.m;
+            r.kym = ky.m;
+            r.kzm = kz.m;
+            r.kxe = kx.e;
+            r.kye = ky.e;
+            r.kze = kz.e;
+            r.iso = (c.ax == c.ay && c.ay == c.az) ? 1 : 0;
+        } else {
+            r.iso = -1;  // the kernel takes the plain FP64 expression
+        }
+        bp[q] = r;
+        int tx, ty, tz;
+        problem_tiles(p, dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz);
+        for (int64_t k0 = 1; k0 < p.nz - 1; k0 += tz)
+            for (int64_t j0 = 1; j0 < p.ny - 1; j0 += ty)
+                for (int64_t i0 = 1; i0 < p.nx - 1; i0 += tx) {
+                    const int64_t ni = std::min<int64_t>(tx, p.nx - 1 - i0);
+                    const int64_t nj = std::min<int64_t>(ty, p.ny - 1 - j0);
+                    const int64_t nk = std::min<int64_t>(tz, p.nz - 1 - k0);
+                    BatchItem it{q, (int32_t)i0, (int32_t)j0, (int32_t)k0, (int16_t)ni, (int16_t)nj,
+                                 (int16_t)nk, 0};
+                    work.push_back({ni * nj * nk, it});
                 }
     }
     // largest items first: the round-robin hand-out then stays balanced

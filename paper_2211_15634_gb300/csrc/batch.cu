@@ -1,8 +1,15 @@
 // Batched step: many independent problems of different sizes in one
 // persistent launch.  The device table holds a header, one record per
-// problem and a static work list of (problem, x-y tile, z-chunk) items; CTA
-// b processes items b, b + gridDim.x, ... (no atomics, no counters, so a
-// captured graph replays the same schedule every time).
+// problem and a static work list of (problem, x-y tile, z-chunk) items, the
+// largest first; CTA b processes items b, b + gridDim.x, ... (no atomics and
+// no counters, so a captured graph replays the same schedule every time).
+//
+// Within an item every thread owns one interior (i, j) column of the tile and
+// marches along z with a three-value register queue; x/y neighbours are read
+// through L1/L2 (problems of 32^3..160^3 are small enough for the caches to
+// serve the reuse, and any nx works - the TMA path needs 16-byte row pitches).
+// FP64 problems use the emulated one-DFMA arithmetic of emu64.cuh.
+#include "emu64.cuh"
 #include "internal.h"
 
 namespace psd {
@@ -10,28 +17,63 @@ namespace psd {
 constexpr int kBatchThreads = 256;
 
 template <typename F>
-__device__ __forceinline__ void batch_item(const BatchItem item, const BatchProblem &P, int parity,
-                                           int tx, int ty, int tz) {
+__device__ __forceinline__ void batch_item(const BatchItem &item, const BatchProblem &P, int parity) {
     const F *__restrict__ T = (const F *)(parity ? P.T2 : P.T);
     F *__restrict__ T2 = (F *)(parity ? P.T : P.T2);
     const F *__restrict__ Ci = (const F *)P.Ci;
-    const F dtlam = (F)P.dtlam, ax = (F)P.ax, ay = (F)P.ay, az = (F)P.az;
-    const int64_t nx = P.nx, ny = P.ny, nz = P.nz, sy = nx, sz = nx * ny;
-    const int64_t k0 = item.k0, k1 = k0 + tz < nz - 1 ? k0 + tz : nz - 1;
-    for (int t = threadIdx.x; t < tx * ty; t += blockDim.x) {
-        const int64_t i = item.i0 + t % tx, j = item.j0 + t / tx;
-        if (i > nx - 2 || j > ny - 2) continue;
+    const int64_t nx = P.nx, ny = P.ny, sy = nx, sz = nx * ny;
+    const int ni = item.ni, nj = item.nj;
+    const int64_t k0 = item.k0, k1 = k0 + item.nk;
+    for (int t = threadIdx.x; t < ni * nj; t += blockDim.x) {
+        const int64_t i = item.i0 + t % ni, j = item.j0 + t / ni;
         int64_t p = i + sy * (j + ny * k0);
-        F tm = T[p - sz], tc = T[p];
-        for (int64_t k = k0; k < k1; ++k, p += sz) {
-            const F tp = T[p + sz];
-            const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
-            const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
-            const F d2z = (tp - tc) - (tc - tm);
-            const F lap = (d2x * ax + d2y * ay) + d2z * az;
-            T2[p] = tc + dtlam * (Ci[p] * lap);
-            tm = tc;
-            tc = tp;
+        if (sizeof(F) == 8 && P.iso < 0) {  // coefficients the emulation cannot take: plain FP64
+            const F dtlam = (F)P.dtlam, ax = (F)P.ax, ay = (F)P.ay, az = (F)P.az;
+            F tm = T[p - sz], tc = T[p];
+            for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+                const F tp = T[p + sz];
+                const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
+                const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
+                const F d2z = (tp - tc) - (tc - tm);
+                T2[p] = tc + dtlam * (Ci[p] * ((d2x * ax + d2y * ay) + d2z * az));
+                tm = tc;
+                tc = tp;
+            }
+        } else if constexpr (sizeof(F) == 8) {
+            const unsigned long long *__restrict__ Tb = (const unsigned long long *)T;
+            const EmuCoef k{EmuK{P.kxm, P.kxe}, EmuK{P.kym, P.kye}, EmuK{P.kzm, P.kze},
+                            P.dtlam, P.ax, P.ay, P.az, 0.0};
+            unsigned long long tm = Tb[p - sz], tc = Tb[p];
+            if (P.iso) {
+                for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+                    const unsigned long long tp = Tb[p + sz];
+                    T2[p] = emu_step_node<true, false>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy],
+                                                       Tb[p + sy], tm, tp, Ci[p], k);
+                    tm = tc;
+                    tc = tp;
+                }
+            } else {
+                for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+                    const unsigned long long tp = Tb[p + sz];
+                    T2[p] = emu_step_node<false, false>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy],
+                                                        Tb[p + sy], tm, tp, Ci[p], k);
+                    tm = tc;
+                    tc = tp;
+                }
+            }
+        } else {
+            const F dtlam = (F)P.dtlam, ax = (F)P.ax, ay = (F)P.ay, az = (F)P.az;
+            F tm = T[p - sz], tc = T[p];
+            for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+                const F tp = T[p + sz];
+                const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
+                const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
+                const F d2z = (tp - tc) - (tc - tm);
+                const F lap = (d2x * ax + d2y * ay) + d2z * az;
+                T2[p] = tc + dtlam * (Ci[p] * lap);
+                tm = tc;
+                tc = tp;
+            }
         }
     }
 }
@@ -43,10 +85,9 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_step(const char *__rest
     const BatchProblem *probs = (const BatchProblem *)(table + h->problems_offset);
     const BatchItem *items = (const BatchItem *)(table + h->items_offset);
     const int64_t nitems = h->nitems;
-    const int tx = h->tile_x, ty = h->tile_y, tz = h->tile_z;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem item = items[it];
-        batch_item<F>(item, probs[item.prob], parity, tx, ty, tz);
+        batch_item<F>(item, probs[item.prob], parity);
     }
 }
 

@@ -80,10 +80,15 @@ struct BatchProblem {
     const void *Ci;
     double dtlam, ax, ay, az;
     int64_t nx, ny, nz;
+    // one-DFMA-class emulated arithmetic constants (FP64): K_d = dtlam*a_d as
+    // integer mantissa/exponent, and whether the three axes share one K
+    unsigned long long kxm, kym, kzm;
+    int32_t kxe, kye, kze, iso;
 };
 struct BatchItem {
     int32_t prob;
-    int32_t i0, j0, k0;  // first interior node of the work item (1-based interior coordinates)
+    int32_t i0, j0, k0;      // first interior node of the work item
+    int16_t ni, nj, nk, pad;  // extents (clipped to the interior)
 };
 cudaError_t launch_batch_step(const void *dev_table, int parity, int dtype, cudaStream_t s);
 int batch_default_tile(int dtype, int *tx, int *ty, int *tz);

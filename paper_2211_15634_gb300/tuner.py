@@ -1,0 +1,127 @@
+"""Tile-shape autotuner for the batched step.
+
+Problems are grouped into size classes by their largest extent; for each class
+the batched kernel is timed (CUDA events, a few steps after warm-up) on that
+class's problems alone with every candidate work-item shape (tile_x, tile_y,
+tile_z), and the fastest shape is kept.  Results are cached as JSON keyed by
+GPU name, dtype and size class (file ``$PS_TUNER_CACHE`` or
+``~/.cache/psdiff/tuner.json``), so later runs reuse them without timing.
+``tuned_batch`` builds the final table with each problem's class shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, List, Sequence, Tuple
+
+import torch
+
+from . import api
+
+Tile = Tuple[int, int, int]
+
+# Candidate work-item shapes (tile_x, tile_y, tile_z): tile_x * tile_y columns,
+# each marched over tile_z planes.  tile_x == 0 is a row-packed rule: the item
+# spans whole interior rows (no partly idle warps at row ends) and as many rows
+# as make about tile_y columns.
+CANDIDATES: List[Tile] = [(32, 8, 16), (32, 8, 32), (32, 16, 16), (64, 4, 32),
+                          (0, 256, 8), (0, 256, 16), (0, 256, 32), (0, 512, 16), (0, 512, 32)]
+
+
+def tile_for(problem, cand: Tile) -> Tile:
+    """Concrete (tile_x, tile_y, tile_z) of a candidate for one problem."""
+    tx, ty, tz = cand
+    if tx != 0:
+        return cand
+    row = problem["T"].shape[2] - 2
+    rows = max(1, min(problem["T"].shape[1] - 2, -(-ty // row)))
+    while row * rows > 4096:
+        rows -= 1
+    return row, rows, tz
+SIZE_CLASSES: List[Tuple[int, int]] = [(3, 48), (48, 80), (80, 112), (112, 144), (144, 1 << 30)]
+
+
+def cache_path() -> str:
+    return os.environ.get("PS_TUNER_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "psdiff", "tuner.json"))
+
+
+def _load_cache() -> Dict[str, list]:
+    try:
+        with open(cache_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_cache(c: Dict[str, list]) -> None:
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as fh:
+            json.dump(c, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # a read-only home only costs re-tuning
+
+
+def size_class(p) -> Tuple[int, int]:
+    n = max(p["T"].shape)
+    for lo, hi in SIZE_CLASSES:
+        if lo <= n < hi:
+            return lo, hi
+    return SIZE_CLASSES[-1]
+
+
+def _key(device, dtype, cls) -> str:
+    name = torch.cuda.get_device_name(device)
+    return f"{name}|{'f64' if dtype == torch.float64 else 'f32'}|{cls[0]}-{cls[1]}"
+
+
+def time_batch_step(problems, cand: Tile, reps: int = 5, warmup: int = 2) -> float:
+    """Milliseconds per batched step of these problems with one candidate shape."""
+    b = api.Batch([dict(p, tile=tile_for(p, cand)) for p in problems])
+    for _ in range(warmup):
+        b.step(0)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for i in range(reps):
+        b.step(i & 1)
+    e.record()
+    e.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def tune(problems, candidates: Sequence[Tile] = CANDIDATES, reps: int = 5,
+         use_cache: bool = True) -> Dict[Tuple[int, int], Tile]:
+    """Best tile per size class present in ``problems`` (cached)."""
+    if not problems:
+        return {}
+    dev = problems[0]["T"].device
+    dtype = problems[0]["T"].dtype
+    cache = _load_cache() if use_cache else {}
+    classes: Dict[Tuple[int, int], list] = {}
+    for p in problems:
+        classes.setdefault(size_class(p), []).append(p)
+    best: Dict[Tuple[int, int], Tile] = {}
+    changed = False
+    for cls, members in classes.items():
+        key = _key(dev, dtype, cls)
+        if key in cache:
+            best[cls] = tuple(cache[key])
+            continue
+        timings = {t: time_batch_step(members, t, reps) for t in candidates}
+        best[cls] = min(timings, key=timings.get)
+        cache[key] = list(best[cls])
+        changed = True
+    if changed and use_cache:
+        _save_cache(cache)
+    return best
+
+
+def tuned_batch(problems, **kw) -> api.Batch:
+    """A Batch whose problems carry the tuned tile of their size class."""
+    best = tune(problems, **kw)
+    tagged = [dict(p, tile=tile_for(p, best[size_class(p)])) for p in problems]
+    return api.Batch(tagged)

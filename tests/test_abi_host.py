@@ -121,12 +121,20 @@ def make_problems(sizes, base=0x100000000):
     return arr
 
 
-def test_batch_table_layout(lib):
-    """The table lists every interior node exactly once, largest items first."""
+ITEM = [("prob", "<i4"), ("i0", "<i4"), ("j0", "<i4"), ("k0", "<i4"), ("ni", "<i2"), ("nj", "<i2"),
+        ("nk", "<i2"), ("pad", "<i2")]
+
+
+@pytest.mark.parametrize("own_tile", [False, True])
+def test_batch_table_layout(lib, own_tile):
+    """The table lists every interior node exactly once, largest items first;
+    a problem's own tile fields override the call's tile."""
     import numpy as np
     sizes = [5, 33, 17, 40]
     arr = make_problems(sizes)
     tx, ty, tz = 8, 4, 6
+    if own_tile:
+        arr[3].tile_x, arr[3].tile_y, arr[3].tile_z = 16, 3, 7
     nbytes = lib.ps_batch_table_bytes(arr, len(sizes), _lib.PS_F64, tx, ty, tz)
     assert nbytes > 0
     buf = (ctypes.c_char * nbytes)()
@@ -138,12 +146,15 @@ def test_batch_table_layout(lib):
     dtype, ttx, tty, ttz = np.frombuffer(raw[16:32], dtype=np.int32)
     poff, ioff = np.frombuffer(raw[32:48], dtype=np.int64)
     assert (nprob, nit, dtype, ttx, tty, ttz) == (4, nitems.value, _lib.PS_F64, tx, ty, tz)
-    items = np.frombuffer(raw[ioff:ioff + 16 * nit], dtype=np.int32).reshape(-1, 4)
+    items = np.frombuffer(raw[ioff:ioff + 24 * nit], dtype=np.dtype(ITEM))
     covered = {q: np.zeros((n, n, n), dtype=np.int32) for q, n in enumerate(sizes)}
     works = []
-    for q, i0, j0, k0 in items:
+    for it in items:
+        q, i0, j0, k0 = int(it["prob"]), int(it["i0"]), int(it["j0"]), int(it["k0"])
         n = sizes[q]
-        i1, j1, k1 = min(i0 + tx, n - 1), min(j0 + ty, n - 1), min(k0 + tz, n - 1)
+        px, py, pz = (16, 3, 7) if (own_tile and q == 3) else (tx, ty, tz)
+        i1, j1, k1 = min(i0 + px, n - 1), min(j0 + py, n - 1), min(k0 + pz, n - 1)
+        assert (it["ni"], it["nj"], it["nk"]) == (i1 - i0, j1 - j0, k1 - k0)
         covered[q][k0:k1, j0:j1, i0:i1] += 1
         works.append((i1 - i0) * (j1 - j0) * (k1 - k0))
     for q, n in enumerate(sizes):

@@ -280,6 +280,34 @@ def test_batch_matches_single_runs(dtype):
     api.clear_graph_cache()
 
 
+def test_tuned_batch_matches_oracle(tmp_path, monkeypatch):
+    """Autotuned per-size-class tiles (row-packed and fixed shapes mixed in one
+    table) give the same results as the oracle; the tuner caches its choice."""
+    import json
+    from paper_2211_15634_gb300 import tuner
+    monkeypatch.setenv("PS_TUNER_CACHE", str(tmp_path / "tuner.json"))
+    sizes = [34, 47, 50, 79, 90, 131, 150]
+    nt = 4
+    probs, refs = [], []
+    for q, n in enumerate(sizes):
+        T0, Ci, lam, dt, inv = problem(n, n, n, seed=2000 + q)
+        refs.append(oracle.run(T0, Ci, lam, dt, *inv, nt))
+        T = to_dev(T0)
+        probs.append(dict(T=T, T2=T.clone(), Ci=to_dev(Ci), lam=lam, dt=dt, inv_spacing=inv))
+    best = tuner.tune(probs, reps=2)
+    cache = json.load(open(tmp_path / "tuner.json"))
+    assert len(cache) == len(best) and all(tuple(v) in tuner.CANDIDATES for v in cache.values())
+    # reset the states (tuning stepped them) and run the tuned table
+    for p, n, q in zip(probs, sizes, range(len(sizes))):
+        T0, *_ = problem(n, n, n, seed=2000 + q)
+        p["T"].copy_(to_dev(T0))
+        p["T2"].copy_(p["T"])
+    b = tuner.tuned_batch(probs)
+    b.run(nt, graph=False)
+    for q, ref in enumerate(refs):
+        assert rel_linf(to_host(b.result(q, nt)), ref) <= FP64_TOL
+
+
 # -------------------------------------------------------- full-size checks
 @pytest.mark.slow
 def test_fp64_512_light_cone_samples():
