@@ -349,11 +349,23 @@ def secondary_metrics(torch, api, ag, inputs, log):
         out[f"batch_{name}_teff_gbs"] = round(bytes_per_step * nt / t_b / 1e9, 1)
         out[f"batch_{name}_tiles"] = {f"{lo}-{hi}": list(t) for (lo, hi), t in sorted(best.items())}
 
+        # one launch per problem, problem-major: each problem's nt steps in a row
+        # (its fields stay in the 129 MB L2 across its own steps)
         def per_problem():
             for p in probs:
                 api.run(p["T"], p["T2"], p["Ci"], 1.0, p["dt"], p["inv_spacing"], nt)
         t_p = timed(per_problem, reps=1)
         out[f"batch_{name}_per_problem_teff_gbs"] = round(bytes_per_step * nt / t_p / 1e9, 1)
+
+        # one launch per problem, step-major (what one batched launch per step
+        # replaces): 50 steps of all problems
+        def per_problem_stepwise(nsteps=50):
+            for it in range(nsteps):
+                for p in probs:
+                    src, dst = (p["T"], p["T2"]) if it % 2 == 0 else (p["T2"], p["T"])
+                    api.step(dst, src, p["Ci"], 1.0, p["dt"], p["inv_spacing"])
+        t_s = timed(per_problem_stepwise, reps=1)
+        out[f"batch_{name}_per_problem_stepwise_teff_gbs"] = round(bytes_per_step * 50 / t_s / 1e9, 1)
         del probs, b
         api.clear_graph_cache()
         torch.cuda.empty_cache()

@@ -488,8 +488,9 @@ int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, i
         int tx, ty, tz;
         st = problem_tiles(p, dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz);
         if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
-        if (p.nx + tx > (1LL << 31) || p.ny + ty > (1LL << 31) || p.nz + tz > (1LL << 31))
-            return fail(PS_ERR_ARG, "problem %d is too large for the batch table", q);
+        if (p.nx * p.ny * p.nz >= (1LL << 31) || p.nx + tx > (1LL << 31) || p.ny + ty > (1LL << 31) ||
+            p.nz + tz > (1LL << 31))
+            return fail(PS_ERR_ARG, "problem %d is too large for the batch table (2^31 nodes at most)", q);
         nitems += items_of(p, tx, ty, tz);
     }
     const size_t need = table_bytes(nprob, nitems);
@@ -578,6 +579,7 @@ int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned 
     if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
     if (flags & ~PS_RUN_GRAPH) return fail(PS_ERR_ARG, "unsupported flags 0x%x", flags);
     cudaStream_t s = (cudaStream_t)stream;
+    batch_prepare(dtype);
     if (!(flags & PS_RUN_GRAPH)) {
         for (int it = 0; it < nt; ++it) {
             cudaError_t e = launch_batch_step(dev_table, it & 1, dtype, s);

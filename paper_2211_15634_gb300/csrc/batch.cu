@@ -21,16 +21,18 @@ __device__ __forceinline__ void batch_item(const BatchItem &item, const BatchPro
     const F *__restrict__ T = (const F *)(parity ? P.T2 : P.T);
     F *__restrict__ T2 = (F *)(parity ? P.T : P.T2);
     const F *__restrict__ Ci = (const F *)P.Ci;
-    const int64_t nx = P.nx, ny = P.ny, sy = nx, sz = nx * ny;
+    // batch problems hold fewer than 2^31 nodes (checked when the table is
+    // built), so 32-bit offsets suffice and keep the register count low
+    const int nx = (int)P.nx, ny = (int)P.ny, sy = nx, sz = nx * ny;
     const int ni = item.ni, nj = item.nj;
-    const int64_t k0 = item.k0, k1 = k0 + item.nk;
+    const int k0 = item.k0, k1 = k0 + item.nk;
     for (int t = threadIdx.x; t < ni * nj; t += blockDim.x) {
-        const int64_t i = item.i0 + t % ni, j = item.j0 + t / ni;
-        int64_t p = i + sy * (j + ny * k0);
+        const int i = item.i0 + t % ni, j = item.j0 + t / ni;
+        int p = i + sy * (j + ny * k0);
         if (sizeof(F) == 8 && P.iso < 0) {  // coefficients the emulation cannot take: plain FP64
             const F dtlam = (F)P.dtlam, ax = (F)P.ax, ay = (F)P.ay, az = (F)P.az;
             F tm = T[p - sz], tc = T[p];
-            for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+            for (int kk = k0; kk < k1; ++kk, p += sz) {
                 const F tp = T[p + sz];
                 const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
                 const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
@@ -45,7 +47,7 @@ __device__ __forceinline__ void batch_item(const BatchItem &item, const BatchPro
                             P.dtlam, P.ax, P.ay, P.az, 0.0};
             unsigned long long tm = Tb[p - sz], tc = Tb[p];
             if (P.iso) {
-                for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+                for (int kk = k0; kk < k1; ++kk, p += sz) {
                     const unsigned long long tp = Tb[p + sz];
                     T2[p] = emu_step_node<true, false>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy],
                                                        Tb[p + sy], tm, tp, Ci[p], k);
@@ -53,7 +55,7 @@ __device__ __forceinline__ void batch_item(const BatchItem &item, const BatchPro
                     tc = tp;
                 }
             } else {
-                for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+                for (int kk = k0; kk < k1; ++kk, p += sz) {
                     const unsigned long long tp = Tb[p + sz];
                     T2[p] = emu_step_node<false, false>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy],
                                                         Tb[p + sy], tm, tp, Ci[p], k);
@@ -64,7 +66,7 @@ __device__ __forceinline__ void batch_item(const BatchItem &item, const BatchPro
         } else {
             const F dtlam = (F)P.dtlam, ax = (F)P.ax, ay = (F)P.ay, az = (F)P.az;
             F tm = T[p - sz], tc = T[p];
-            for (int64_t kk = k0; kk < k1; ++kk, p += sz) {
+            for (int kk = k0; kk < k1; ++kk, p += sz) {
                 const F tp = T[p + sz];
                 const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
                 const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
@@ -78,9 +80,17 @@ __device__ __forceinline__ void batch_item(const BatchItem &item, const BatchPro
     }
 }
 
+// Resident CTAs per SM the register budget is sized for: the FP32 march is
+// memory-latency bound and wants many loads in flight (6 x 256 threads); the
+// FP64 emulated arithmetic needs more registers (4 x 256).
 template <typename F>
-__global__ void __launch_bounds__(kBatchThreads) k_batch_step(const char *__restrict__ table,
-                                                               int parity) {
+struct BatchOcc {
+    static constexpr int min_blocks = sizeof(F) == 8 ? 4 : 6;
+};
+
+template <typename F>
+__global__ void __launch_bounds__(kBatchThreads, BatchOcc<F>::min_blocks)
+k_batch_step(const char *__restrict__ table, int parity) {
     const BatchHeader *h = (const BatchHeader *)table;
     const BatchProblem *probs = (const BatchProblem *)(table + h->problems_offset);
     const BatchItem *items = (const BatchItem *)(table + h->items_offset);
@@ -99,12 +109,37 @@ int batch_default_tile(int dtype, int *tx, int *ty, int *tz) {
     return 0;
 }
 
-cudaError_t launch_batch_step(const void *dev_table, int parity, int dtype, cudaStream_t s) {
-    const unsigned grid = (unsigned)(8 * sm_count());
+// Persistent grid = exactly the CTAs that can be resident at once: the static
+// round-robin hand-out only balances when no CTA waits for a second wave.
+template <typename F>
+static unsigned resident_grid() {
+    static int per_sm[64] = {0};
+    const int d = current_device();
+    int v = (d >= 0 && d < 64) ? per_sm[d] : 0;
+    if (v == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch_step<F>, kBatchThreads, 0) !=
+                cudaSuccess ||
+            v < 1)
+            v = 1;
+        if (d >= 0 && d < 64) per_sm[d] = v;
+    }
+    return (unsigned)(v * sm_count());
+}
+
+void batch_prepare(int dtype) {  // occupancy query outside any stream capture
     if (dtype == PS_F64)
-        k_batch_step<double><<<grid, kBatchThreads, 0, s>>>((const char *)dev_table, parity);
+        resident_grid<double>();
     else
-        k_batch_step<float><<<grid, kBatchThreads, 0, s>>>((const char *)dev_table, parity);
+        resident_grid<float>();
+}
+
+cudaError_t launch_batch_step(const void *dev_table, int parity, int dtype, cudaStream_t s) {
+    if (dtype == PS_F64)
+        k_batch_step<double><<<resident_grid<double>(), kBatchThreads, 0, s>>>((const char *)dev_table,
+                                                                            parity);
+    else
+        k_batch_step<float><<<resident_grid<float>(), kBatchThreads, 0, s>>>((const char *)dev_table,
+                                                                          parity);
     return cudaGetLastError();
 }
 

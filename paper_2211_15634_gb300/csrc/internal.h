@@ -91,6 +91,7 @@ struct BatchItem {
     int16_t ni, nj, nk, pad;  // extents (clipped to the interior)
 };
 cudaError_t launch_batch_step(const void *dev_table, int parity, int dtype, cudaStream_t s);
+void batch_prepare(int dtype);
 int batch_default_tile(int dtype, int *tx, int *ty, int *tz);
 
 }  // namespace psd
