@@ -94,6 +94,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(seconds: float, device=None) -> float:
+    """Slowest rank's time (all ranks get it); the local value without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds
+    t = torch.tensor([seconds], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, slowest_seconds: float, world: int) -> float:
+    """Units processed by all ranks (replicas: each does units_per_rank) per second."""
+    return world * units_per_rank / slowest_seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -190,6 +207,26 @@ def fields(n):
     T0 = inputs.t0_gaussian(n, n, n)
     Ci = inputs.ci_random(n, n, n)
     return T0, Ci, inputs.inverse_spacing(n, n, n)
+
+
+def big_fields(n, dtype, dev):
+    """Workload fields of an n^3 grid built plane by plane on the host (bounded
+    host memory), uploaded as `dtype`; FP32 temperatures as deviations from 1.7."""
+    import torch
+    from paper_2211_15634_gb300 import inputs
+    T = torch.empty((n, n, n), dtype=dtype, device=dev)
+    C = torch.empty((n, n, n), dtype=dtype, device=dev)
+    x = (inputs.node_coords(n) - 0.5) ** 2
+    plane = n * n
+    for k in range(n):
+        t = np.exp(-((x[None, :] + x[:, None]) + x[k]) / 0.01)
+        if dtype == torch.float64:
+            t = t + 1.7
+        idx = np.arange(k * plane, (k + 1) * plane, dtype=np.uint64)
+        c = (1.0 / inputs.C0) * (1.0 + 0.5 * inputs.uniform(inputs.SEED_CI, idx)).reshape(n, n)
+        T[k].copy_(torch.from_numpy(t))
+        C[k].copy_(torch.from_numpy(c))
+    return T, C
 
 
 def oracle_sample(T0, Ci, inv, steps, threads):
@@ -290,6 +327,45 @@ def secondary_metrics(torch, api, ag, inputs, log):
     out["fp32c_512_teff_gbs"] = round(5 * n ** 3 * 4 * nt / t / 1e9, 1)
     del D, D2, comp, C32
     api.clear_graph_cache()
+    torch.cuda.empty_cache()
+
+    # size checks: FP64 768^3 and FP32 1024^3 (nt = 100)
+    for name, n, dtype in (("fp64_768", 768, torch.float64), ("fp32_1024", 1024, torch.float32)):
+        nt = 100
+        T, C = big_fields(n, dtype, dev)
+        T2 = T.clone()
+        dt = api.stable_dt(C, 1.0)
+        inv = inputs.inverse_spacing(n, n, n)
+        t = timed(lambda: api.run(T, T2, C, 1.0, dt, inv, nt, graph=True), reps=2)
+        esz = 8 if dtype == torch.float64 else 4
+        out[f"{name}_teff_gbs"] = round(3 * n ** 3 * esz * nt / t / 1e9, 1)
+        del T, T2, C
+        api.clear_graph_cache()
+        torch.cuda.empty_cache()
+
+    # FP32 error against the FP64 oracle at 256^3 (nt = 100 and 1000, plain and compensated)
+    import oracle
+    n = 256
+    T0, Ci, inv = fields(n)
+    dt = oracle.stable_dt(1.0 / (n - 1), 1.0 / (n - 1), 1.0 / (n - 1), 1.0, oracle.maximum(Ci))
+    oracle.set_threads(max(1, oracle.max_threads()))
+    Td = torch.from_numpy(T0).to(dev)
+    C32 = api.to_f32(torch.from_numpy(Ci).to(dev))
+    for nt in (100, 1000):
+        ref = oracle.run(T0, Ci, 1.0, dt, *inv, nt)
+        scale = float(np.max(np.abs(ref)))
+        for tag, comp in (("fp32", False), ("fp32c", True)):
+            D = api.to_deviation(Td, 1.7)
+            D2 = D.clone()
+            cbuf = torch.zeros_like(D) if comp else None
+            res = api.run(D, D2, C32, 1.0, dt, inv, nt, comp=cbuf)
+            got = api.from_deviation(res, 1.7).cpu().numpy()
+            out[f"{tag}_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref)) / scale:.3e}")
+        T64, T64b = Td.clone(), Td.clone()
+        got = api.run(T64, T64b, torch.from_numpy(Ci).to(dev), 1.0, dt, inv, nt).cpu().numpy()
+        out[f"fp64_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref)) / scale:.3e}")
+    oracle.set_threads(1)
+    del Td, C32, D, D2
     torch.cuda.empty_cache()
 
     # gradient / forward at 256^3, nt = 200, sqrt(nt) checkpoints
@@ -425,11 +501,8 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     region_s = t_start.elapsed_time(t_end) / 1e3
     launch_ms = [a.elapsed_time(b) for step in kev for (a, b) in step]
-    if world > 1:
-        tt = torch.tensor([region_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        region_s = float(tt.item())
-    gbs = world * bytes_per_launch * nt * K / region_s / 1e9
+    region_s = max_over_ranks(region_s, dev)
+    gbs = whole_job_rate(bytes_per_launch * nt * K, region_s, world) / 1e9
     gpu_launches = K * (nt + 3)  # per step: max reduction (2 kernels), boundary copy, nt steps
 
     # the same time loop as a captured CUDA graph (library-side cache)
