@@ -22,6 +22,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdlib>
+#include <type_traits>
 
 #include "emu64.cuh"
 #include "internal.h"
@@ -58,19 +59,28 @@ __device__ __forceinline__ E aget(const V &v, int i) {
 }
 
 template <typename E, bool kIso, int BY, int NST>
-__global__ void __launch_bounds__(32 * BY, 1)
+__global__ void __launch_bounds__(32 * BY, 3)
 k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmY,
                  const __grid_constant__ CUtensorMap tmC, E *__restrict__ Tbar,
                  E *__restrict__ Cibar, const AdjParams p) {
     using V = typename ATraits<E>::V;
+    // w tiles: FP64 holds w in 64-bit fixed point at a CTA-uniform scale, FP32 holds floats
+    constexpr bool kFix = sizeof(E) == 8;
+    using WT = std::conditional_t<kFix, long long, E>;
+    using WV = std::conditional_t<kFix, longlong2, V>;
     constexpr int PX = ATraits<E>::PX, HX = PX, BX = 32 * PX, W = BX + 2 * HX, H = BY + 2;
+    constexpr int NTH = 32 * BY, NV = (W * H + NTH - 1) / NTH;  // tile values per thread
     constexpr unsigned TB = W * H * sizeof(E);
     constexpr unsigned TBA = (TB + 127) / 128 * 128, SS = TBA / sizeof(E);  // box stride in elements
     extern __shared__ __align__(128) unsigned char smem[];
-    E *ring = (E *)smem;                         // NST stages x {T, ybar, Ci}
-    E *wtile = (E *)(smem + 3 * NST * TBA);      // 3 rotating w tiles
+    E *ring = (E *)smem;                          // NST stages x {T, ybar, Ci}
+    WT *wtile = (WT *)(smem + 3 * NST * TBA);     // 3 rotating w tiles
     uint64_t *bar = (uint64_t *)(smem + 3 * NST * TBA + 3 * TBA);
     __shared__ int s_abort;
+    __shared__ int s_emax[BY];
+    // FP64: biased exponent of the fixed-point scale (value = X * 2^(Esc-1079)); it only grows,
+    // and every stored value is at most 2^57 in magnitude.  0x7ff marks a non-finite w.
+    int Esc = 1;
 
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int X0 = (int)(blockIdx.x % p.ntx) * BX, Y0 = (int)(blockIdx.x / p.ntx) * BY;
@@ -107,10 +117,52 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
         const bool in = x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2 && q >= 1 && q <= nz - 2;
         return in ? Cs[r * W + c] * Ys[r * W + c] : E(0);
     };
-    auto fill_w = [&](E *wt, const E *Ys, const E *Cs, int q) {
-        for (int idx = threadIdx.x; idx < W * H; idx += 32 * BY) {
-            const int r = idx / W, c = idx - r * W;
-            wt[idx] = wval(Ys, Cs, r, c, q);
+    // this thread's share (indices threadIdx.x + v*NTH) of a plane's w tile; returns the
+    // largest biased exponent among them (FP64)
+    auto w_values = [&](E (&wv)[NV], const E *Ys, const E *Cs, int q) -> int {
+        int em = 0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int idx = threadIdx.x + v * NTH;
+            if (idx < W * H) {
+                const int r = idx / W, c = idx - r * W;
+                wv[v] = wval(Ys, Cs, r, c, q);
+                if constexpr (kFix) em = max(em, emu_exp(dbits(wv[v])));
+            }
+        }
+        return em;
+    };
+    auto w_store = [&](WT *wt, const E (&wv)[NV]) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int idx = threadIdx.x + v * NTH;
+            if (idx < W * H) {
+                if constexpr (kFix) wt[idx] = emu_fixed(dbits(wv[v]), Esc);
+                else wt[idx] = wv[v];
+            }
+        }
+    };
+    // FP64: agree on the CTA's scale (contains a __syncthreads); entries this thread
+    // stored earlier and its register queue are shifted down when the scale grows
+    auto agree = [&](int em_local, WT *older, WT (&wreg)[PX]) {
+        if constexpr (kFix) {
+            const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)em_local);
+            if (lane == 0) s_emax[ty] = (int)m;
+            __syncthreads();
+            int e = Esc;
+#pragma unroll
+            for (int w = 0; w < BY; ++w) e = max(e, s_emax[w]);
+            if (e > Esc) {
+                const int d = e - Esc;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const int idx = threadIdx.x + v * NTH;
+                    if (idx < W * H) older[idx] = d >= 64 ? 0 : (older[idx] >> d);
+                }
+#pragma unroll
+                for (int i = 0; i < PX; ++i) wreg[i] = d >= 64 ? 0 : (wreg[i] >> d);
+                Esc = e;
+            }
         }
     };
 
@@ -120,14 +172,30 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
     int s_c = nexts(s_m);   // stage of plane k
     bool ok = acquire(s_m);
     V tm = *(const V *)(ring + (3 * s_m) * SS + row * W + col);
-    E wm[PX];
+    E wm0[PX];
+    int em0 = 0;
 #pragma unroll
-    for (int i = 0; i < PX; ++i)
-        wm[i] = wval(ring + (3 * s_m + 1) * SS, ring + (3 * s_m + 2) * SS, row, col + i, k0 - 1);
+    for (int i = 0; i < PX; ++i) {
+        wm0[i] = wval(ring + (3 * s_m + 1) * SS, ring + (3 * s_m + 2) * SS, row, col + i, k0 - 1);
+        if constexpr (kFix) em0 = max(em0, emu_exp(dbits(wm0[i])));
+    }
     ok = acquire(s_c) && ok;
     V tc = *(const V *)(ring + (3 * s_c) * SS + row * W + col);
     int wcur = 0;
-    fill_w(wtile + wcur * SS, ring + (3 * s_c + 1) * SS, ring + (3 * s_c + 2) * SS, k0);
+    WT wm[PX];
+    {
+        E wv[NV];
+        em0 = max(em0, w_values(wv, ring + (3 * s_c + 1) * SS, ring + (3 * s_c + 2) * SS, k0));
+#pragma unroll
+        for (int i = 0; i < PX; ++i) wm[i] = WT(0);
+        agree(em0, wtile + wcur * SS, wm);  // nothing stored yet: only sets the scale
+        w_store(wtile + wcur * SS, wv);
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if constexpr (kFix) wm[i] = emu_fixed(dbits(wm0[i]), Esc);
+            else wm[i] = wm0[i];
+        }
+    }
     if (!ok) {
         s_abort = 1;
         atomicOr(&g_adj_error, 1u);
@@ -144,7 +212,12 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
         const int s_n = nexts(s_c);  // stage of plane k+1
         ok = acquire(s_n) && ok;
         const int wnxt = wcur == 2 ? 0 : wcur + 1;
-        fill_w(wtile + wnxt * SS, ring + (3 * s_n + 1) * SS, ring + (3 * s_n + 2) * SS, k + 1);
+        {
+            E wv[NV];
+            const int em = w_values(wv, ring + (3 * s_n + 1) * SS, ring + (3 * s_n + 2) * SS, k + 1);
+            agree(em, wtile + wcur * SS, wm);
+            w_store(wtile + wnxt * SS, wv);
+        }
         if (!ok) {
             s_abort = 1;
             atomicOr(&g_adj_error, 1u);
@@ -155,14 +228,14 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
 
         const E *Tk = ring + (3 * s_c) * SS;
         const E *Yk = ring + (3 * s_c + 1) * SS;
-        const E *wk = wtile + wcur * SS;
+        const WT *wk = wtile + wcur * SS;
         const V tp = *(const V *)(ring + (3 * s_n) * SS + row * W + col);
         const V yc = *(const V *)(Yk + row * W + col);
-        const V wc = *(const V *)(wk + row * W + col);
-        const V wu = *(const V *)(wk + (row - 1) * W + col);
-        const V wd = *(const V *)(wk + (row + 1) * W + col);
-        const V wp = *(const V *)(wtile + wnxt * SS + row * W + col);
-        const E wl = wk[row * W + col - 1], wr = wk[row * W + col + PX];
+        const WV wc = *(const WV *)(wk + row * W + col);
+        const WV wu = *(const WV *)(wk + (row - 1) * W + col);
+        const WV wd = *(const WV *)(wk + (row + 1) * W + col);
+        const WV wp = *(const WV *)(wtile + wnxt * SS + row * W + col);
+        const WT wl = wk[row * W + col - 1], wr = wk[row * W + col + PX];
         const V tu = *(const V *)(Tk + (row - 1) * W + col);
         const V td = *(const V *)(Tk + (row + 1) * W + col);
         const E tl = Tk[row * W + col - 1], tr = Tk[row * W + col + PX];
@@ -184,27 +257,20 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
                 }
             }
             if constexpr (sizeof(E) == 8) {
-                // ---- Tbar: exact w-stencil sums, one DFMA per coefficient
+                // ---- Tbar: exact fixed-point w-stencil sums, one DFMA per coefficient
 #pragma unroll
                 for (int i = 0; i < PX; ++i) {
-                    const unsigned long long c = dbits(aget<V, E>(wc, i));
-                    const unsigned long long xm = dbits(i == 0 ? wl : aget<V, E>(wc, i - 1));
-                    const unsigned long long xp = dbits(i == PX - 1 ? wr : aget<V, E>(wc, i + 1));
-                    const unsigned long long ym = dbits(aget<V, E>(wu, i)), yp = dbits(aget<V, E>(wd, i));
-                    const unsigned long long zm = dbits(wm[i]), zp = dbits(aget<V, E>(wp, i));
-                    long long sx, sy, sz;
-                    int sc;
+                    const long long c2 = 2 * aget<WV, WT>(wc, i);
+                    const long long xm = i == 0 ? wl : aget<WV, WT>(wc, i - 1);
+                    const long long xp = i == PX - 1 ? wr : aget<WV, WT>(wc, i + 1);
+                    const long long sx = xm + xp - c2;
+                    const long long sy = aget<WV, WT>(wu, i) + aget<WV, WT>(wd, i) - c2;
+                    const long long sz = wm[i] + aget<WV, WT>(wp, i) - c2;
                     const double yb = aget<V, E>(yc, i);
-                    double r;
-                    if (emu_sums_general(c, xm, xp, ym, yp, zm, zp, sx, sy, sz, sc)) {
-                        r = emu_axpy3<kIso>(yb, sx, sy, sz, sc, p.Kx, p.Ky, p.Kz);
-                    } else {
-                        const double cc = bitsd(c);
-                        r = yb + ((p.Kx * ((bitsd(xm) - cc) - (cc - bitsd(xp))) +
-                                   p.Ky * ((bitsd(ym) - cc) - (cc - bitsd(yp)))) +
-                                  p.Kz * ((bitsd(zm) - cc) - (cc - bitsd(zp))));
-                    }
-                    reinterpret_cast<E *>(&tb)[i] = r;
+                    // a non-finite w anywhere in this CTA's march: report NaN, not garbage
+                    reinterpret_cast<E *>(&tb)[i] =
+                        Esc == 0x7ff ? __longlong_as_double(0x7ff8000000000000ll)
+                                     : emu_axpy3<kIso>(yb, sx, sy, sz, Esc - 1079, p.Kx, p.Ky, p.Kz);
                 }
                 // ---- Cibar: T-Laplacian, same-binade fast path when the whole warp allows it
                 if (do_ci) {
@@ -321,7 +387,7 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
         }
         // rotate: plane k's values become the "minus" neighbours
 #pragma unroll
-        for (int i = 0; i < PX; ++i) wm[i] = aget<V, E>(wc, i);
+        for (int i = 0; i < PX; ++i) wm[i] = aget<WV, WT>(wc, i);
         tm = tc;
         tc = tp;
         s_m = s_c;

@@ -24,8 +24,9 @@ Tile = Tuple[int, int, int]
 # each marched over tile_z planes.  tile_x == 0 is a row-packed rule: the item
 # spans whole interior rows (no partly idle warps at row ends) and as many rows
 # as make about tile_y columns.
-CANDIDATES: List[Tile] = [(32, 8, 16), (32, 8, 32), (32, 16, 16), (64, 4, 32),
-                          (0, 256, 8), (0, 256, 16), (0, 256, 32), (0, 512, 16), (0, 512, 32)]
+DEFAULT: Tile = (32, 8, 32)  # the library's default work item (batch_default_tile)
+CANDIDATES: List[Tile] = [DEFAULT, (32, 8, 16), (32, 8, 64), (32, 16, 16), (64, 4, 32),
+                          (0, 256, 16), (0, 256, 32), (0, 512, 16), (0, 512, 32)]
 
 
 def tile_for(problem, cand: Tile) -> Tile:
@@ -93,31 +94,58 @@ def time_batch_step(problems, cand: Tile, reps: int = 5, warmup: int = 2) -> flo
     return s.elapsed_time(e) / reps
 
 
+def _time_assignment(problems, assign: Dict[Tuple[int, int], Tile], reps: int) -> float:
+    tagged = [dict(p, tile=tile_for(p, assign[size_class(p)])) for p in problems]
+    b = api.Batch(tagged)
+    for _ in range(2):
+        b.step(0)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for i in range(reps):
+        b.step(i & 1)
+    e.record()
+    e.synchronize()
+    return s.elapsed_time(e) / reps
+
+
 def tune(problems, candidates: Sequence[Tile] = CANDIDATES, reps: int = 5,
-         use_cache: bool = True) -> Dict[Tuple[int, int], Tile]:
-    """Best tile per size class present in ``problems`` (cached)."""
+         use_cache: bool = True, sweeps: int = 2) -> Dict[Tuple[int, int], Tile]:
+    """Best tile per size class present in ``problems`` (cached).
+
+    Coordinate descent on the whole batch: classes interact (they share the
+    persistent CTAs and the memory system), so each class's candidates are
+    timed with every other class held at its current choice, starting from the
+    library default, for ``sweeps`` passes over the classes.
+    """
     if not problems:
         return {}
     dev = problems[0]["T"].device
     dtype = problems[0]["T"].dtype
     cache = _load_cache() if use_cache else {}
-    classes: Dict[Tuple[int, int], list] = {}
-    for p in problems:
-        classes.setdefault(size_class(p), []).append(p)
-    best: Dict[Tuple[int, int], Tile] = {}
-    changed = False
-    for cls, members in classes.items():
-        key = _key(dev, dtype, cls)
-        if key in cache:
-            best[cls] = tuple(cache[key])
-            continue
-        timings = {t: time_batch_step(members, t, reps) for t in candidates}
-        best[cls] = min(timings, key=timings.get)
-        cache[key] = list(best[cls])
-        changed = True
-    if changed and use_cache:
+    classes = sorted({size_class(p) for p in problems})
+    keys = {cls: _key(dev, dtype, cls) for cls in classes}
+    if all(keys[c] in cache for c in classes):
+        return {c: tuple(cache[keys[c]]) for c in classes}
+    assign = {c: DEFAULT for c in classes}
+    best_t = _time_assignment(problems, assign, reps)
+    for _ in range(sweeps):
+        improved = False
+        for c in classes:
+            for cand in candidates:
+                if cand == assign[c]:
+                    continue
+                trial = dict(assign)
+                trial[c] = cand
+                t = _time_assignment(problems, trial, reps)
+                if t < best_t * 0.99:  # keep only clear wins
+                    assign, best_t, improved = trial, t, True
+        if not improved:
+            break
+    for c in classes:
+        cache[keys[c]] = list(assign[c])
+    if use_cache:
         _save_cache(cache)
-    return best
+    return assign
 
 
 def tuned_batch(problems, **kw) -> api.Batch:

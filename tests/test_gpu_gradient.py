@@ -103,6 +103,33 @@ def test_gradient_central_differences_16():
     assert abs(fd - ad) <= 1e-6 * abs(ad)
 
 
+@pytest.mark.parametrize("kchunk", ["0", "3", "40"])
+def test_adjoint_fixed_point_scale_growth(monkeypatch, kchunk):
+    """ybar growing by 10^4 along z (with sign changes and exact zeros) makes the
+    FP64 adjoint's per-CTA fixed-point scale grow in the middle of its z-march,
+    so tiles already stored must be rescaled; results still match the oracle."""
+    monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
+    nx, ny, nz = 68, 21, 40
+    T = 1.7 + inputs.random_field((nz, ny, nx), 3, 0.0, 1.0)
+    Ci = inputs.ci_random(nx, ny, nz)
+    lam = 1.0
+    dx, dy, dz = inputs.spacing(nx, ny, nz)
+    dt = min(dx * dx, dy * dy, dz * dz) / lam / Ci.max() / 6.1
+    inv = inputs.inverse_spacing(nx, ny, nz)
+    ybar = inputs.random_field(T.shape, 5) * (10.0 ** (np.arange(nz) / 10.0))[:, None, None]
+    ybar[:, ::4, ::3] = 0.0
+    cib = inputs.random_field(T.shape, 6)
+    ref = oracle.adjoint_step(ybar, T, Ci, cib, lam, dt, *inv)
+    Tbar = torch.empty(T.shape, dtype=torch.float64, device="cuda")
+    C = to_dev(inputs.random_field(T.shape, 6))
+    api.adjoint(Tbar, C, to_dev(ybar), to_dev(T), to_dev(Ci), lam, dt, inv)
+    # error relative to each plane's own scale (planes differ by up to 10^4)
+    got = to_host(Tbar)
+    for k in range(nz):
+        assert np.max(np.abs(got[k] - ref[k])) <= 1e-13 * np.max(np.abs(ref[k])), k
+    assert np.max(np.abs(to_host(C) - cib)) <= 1e-13 * np.max(np.abs(cib))
+
+
 @pytest.mark.parametrize("kchunk", ["1", "2", "5"])
 def test_adjoint_short_z_chunks(monkeypatch, kchunk):
     monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
