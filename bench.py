@@ -53,6 +53,8 @@ def parse_args():
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON)")
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     p.add_argument("--reps", type=int, default=4)
+    p.add_argument("--plain-ci", action="store_true",
+                   help="kernel loop: FP64 step on Ci as given instead of the pre-scaled field")
     return p.parse_args()
 
 
@@ -70,10 +72,13 @@ def run_kernel_loop(args):
     T2 = T.clone()
     dt = api.stable_dt(C, 1.0)
     if args.kernel_loop == "step":
+        # FP64: the pre-scaled coefficient of the headline step (--plain-ci: Ci as given)
+        scaled = args.dtype == "f64" and not args.plain_ci
+        Cs = api.scale_ci(C, 1.0, dt, inv) if scaled else C
         for i in range(args.reps):
             src, dst = (T, T2) if i % 2 == 0 else (T2, T)
-            api.step(dst, src, C, 1.0, dt, inv)
-        name = api.step_kernel_name(T2, T, C, 1.0, dt, inv)
+            api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
+        name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled)
     else:
         ybar = T2 - T.mean()
         Tbar = torch.empty_like(T)
@@ -315,6 +320,13 @@ def secondary_metrics(torch, api, ag, inputs, log):
     T0, Ci, inv = fields(n)
     T = torch.from_numpy(T0).to(dev)
     C = torch.from_numpy(Ci).to(dev)
+    # FP64 on Ci as given (three-term emulated step, no pre-scaled coefficient)
+    T2 = T.clone()
+    dt = api.stable_dt(C, 1.0)
+    t = timed(lambda: api.run(T, T2, C, 1.0, dt, inv, nt, graph=True))
+    out["fp64_512_plain_ci_teff_gbs"] = round(3 * n ** 3 * 8 * nt / t / 1e9, 1)
+    del T2
+    api.clear_graph_cache()
     D = api.to_deviation(T, 1.7)
     C32 = api.to_f32(C)
     del T, C
@@ -336,7 +348,10 @@ def secondary_metrics(torch, api, ag, inputs, log):
         T2 = T.clone()
         dt = api.stable_dt(C, 1.0)
         inv = inputs.inverse_spacing(n, n, n)
-        t = timed(lambda: api.run(T, T2, C, 1.0, dt, inv, nt, graph=True), reps=2)
+        scaled = dtype == torch.float64
+        if scaled:
+            api.scale_ci(C, 1.0, dt, inv, out=C)
+        t = timed(lambda: api.run(T, T2, C, 1.0, dt, inv, nt, graph=True, ci_scaled=scaled), reps=2)
         esz = 8 if dtype == torch.float64 else 4
         out[f"{name}_teff_gbs"] = round(3 * n ** 3 * esz * nt / t / 1e9, 1)
         del T, T2, C
@@ -361,9 +376,12 @@ def secondary_metrics(torch, api, ag, inputs, log):
             res = api.run(D, D2, C32, 1.0, dt, inv, nt, comp=cbuf)
             got = api.from_deviation(res, 1.7).cpu().numpy()
             out[f"{tag}_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref)) / scale:.3e}")
-        T64, T64b = Td.clone(), Td.clone()
-        got = api.run(T64, T64b, torch.from_numpy(Ci).to(dev), 1.0, dt, inv, nt).cpu().numpy()
-        out[f"fp64_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref)) / scale:.3e}")
+        C64 = torch.from_numpy(Ci).to(dev)
+        for tag, scaled in (("fp64", True), ("fp64_plain_ci", False)):
+            T64, T64b = Td.clone(), Td.clone()
+            Cx = api.scale_ci(C64, 1.0, dt, inv) if scaled else C64
+            got = api.run(T64, T64b, Cx, 1.0, dt, inv, nt, ci_scaled=scaled).cpu().numpy()
+            out[f"{tag}_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref)) / scale:.3e}")
     oracle.set_threads(1)
     del Td, C32, D, D2
     torch.cuda.empty_cache()
@@ -468,18 +486,20 @@ def run_ours(args):
     T = torch.from_numpy(T0).to(dev)
     T2 = torch.empty_like(T)
     C = torch.from_numpy(Ci).to(dev)
+    Cs = torch.empty_like(C)  # dt*lam*_dx^2*Ci, rebuilt every step from this step's dt
     lam = 1.0
     bytes_per_launch = 3 * n ** 3 * 8
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def one_step(kernel_events=None):
         dt = api.stable_dt(C, lam)          # A1: maximum(Ci) on the GPU, dt on the host
+        api.scale_ci(C, lam, dt, inv, out=Cs)  # one pass: Cs = dt*lam*_dx^2*Ci
         api.copy_boundary(T2, T)            # Fig. 1: T2 = copy(T) on the boundary
         for it in range(nt):
             src, dst = (T, T2) if it % 2 == 0 else (T2, T)
             if kernel_events is not None:
                 kernel_events[it][0].record()
-            api.step(dst, src, C, lam, dt, inv)
+            api.step(dst, src, Cs, lam, dt, inv, ci_scaled=True)
             if kernel_events is not None:
                 kernel_events[it][1].record()
         return dt
@@ -503,16 +523,18 @@ def run_ours(args):
     launch_ms = [a.elapsed_time(b) for step in kev for (a, b) in step]
     region_s = max_over_ranks(region_s, dev)
     gbs = whole_job_rate(bytes_per_launch * nt * K, region_s, world) / 1e9
-    gpu_launches = K * (nt + 3)  # per step: max reduction (2 kernels), boundary copy, nt steps
+    # per step: max reduction (2 kernels), coefficient scaling, boundary copy, nt steps
+    gpu_launches = K * (nt + 4)
 
     # the same time loop as a captured CUDA graph (library-side cache)
     dt = api.stable_dt(C, lam)
-    api.run(T, T2, C, lam, dt, inv, nt, graph=True)
+    api.scale_ci(C, lam, dt, inv, out=Cs)
+    api.run(T, T2, Cs, lam, dt, inv, nt, graph=True, ci_scaled=True)
     torch.cuda.synchronize()
     g0, g1 = ev(), ev()
     g0.record()
     for _ in range(K):
-        api.run(T, T2, C, lam, dt, inv, nt, graph=True)
+        api.run(T, T2, Cs, lam, dt, inv, nt, graph=True, ci_scaled=True)
     g1.record()
     torch.cuda.synchronize()
     graph_gbs = bytes_per_launch * nt * K / (g0.elapsed_time(g1) / 1e3) / 1e9
@@ -546,7 +568,7 @@ def run_ours(args):
     hbm, src = measured_peaks()
     mean_launch_s = statistics.mean(launch_ms) / 1e3
     achieved = bytes_per_launch / mean_launch_s / 1e9
-    kernel = api.step_kernel_name(T2, T, C, lam, dt, inv)
+    kernel = api.step_kernel_name(T2, T, Cs, lam, dt, inv, ci_scaled=True)
     digest = source_digest(api.step_kernel_sources(kernel))
     traffic = profiled_traffic(kernel, digest, n)
     line = {
@@ -574,7 +596,7 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline(T0, Ci, inv)
         except Exception as exc:  # reported, not fatal
             line["cpu_baseline"] = {"error": str(exc)}
-    del T, T2, C
+    del T, T2, C, Cs
     torch.cuda.empty_cache()
     if not args.no_secondary and world == 1:
         try:

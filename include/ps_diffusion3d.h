@@ -69,6 +69,8 @@ typedef enum {
 #define PS_RUN_GRAPH 1u       /* capture the nt launches into a CUDA graph once, replay it */
 #define PS_RUN_COMPENSATED 2u /* PS_F32 only: compensated (Kahan) update, needs `comp` */
 #define PS_RUN_NATIVE_F64 4u  /* PS_F64 only: force the plain FP64-instruction kernel */
+#define PS_RUN_CI_SCALED 8u   /* PS_F64, equal spacings: Ci holds dt*lam*_dx^2*Ci (see
+                                 ps_diffusion3d_scale_ci); lam, dt are then only checked */
 
 /* Library version (major*10000 + minor*100 + patch). */
 int ps_version(void);
@@ -86,11 +88,11 @@ size_t ps_workspace_bytes(void);
  * clear != 0 the flags are reset.  Synchronizes the device. */
 int ps_device_error(unsigned *out_host, int clear);
 
-/* Name of the kernel ps_diffusion3d_step would launch for these arguments
- * (for profiles and reports; no validation, launches nothing). */
+/* Name of the kernel ps_diffusion3d_step_ex would launch for these arguments
+ * and flags (for profiles and reports; no validation, launches nothing). */
 const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void *Ci, double lam,
                                        double dt, double _dx, double _dy, double _dz, int64_t nx,
-                                       int64_t ny, int64_t nz, int dtype);
+                                       int64_t ny, int64_t nz, int dtype, unsigned flags);
 
 /* ---------------------------------------------------------------------
  * Time step (Fig. 1, step!).  Writes the interior nodes of T2 from T and
@@ -103,6 +105,22 @@ const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void
 int ps_diffusion3d_step(void *T2, const void *T, const void *Ci, double lam, double dt,
                         double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
                         int dtype, void *stream);
+
+/* As ps_diffusion3d_step with flags: PS_RUN_CI_SCALED (Ci is the pre-scaled
+ * field of ps_diffusion3d_scale_ci; PS_F64 and equal spacings, else
+ * PS_ERR_UNSUPPORTED) or PS_RUN_NATIVE_F64. */
+int ps_diffusion3d_step_ex(void *T2, const void *T, const void *Ci, double lam, double dt,
+                           double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
+                           int dtype, unsigned flags, void *stream);
+
+/* Pre-scaled coefficient field for repeated FP64 steps on a grid with equal
+ * spacings: Cs[p] = (dt*lam*_dx^2) * Ci[p] for p < n (FP64, device arrays;
+ * Cs may be Ci itself, else must not overlap it).  With it the step is
+ * T2 = T + Cs * (sum of the six neighbours - 6 T) - Fig. 1's step! with the
+ * constant factors folded once per run - and needs one FP64 multiply-add per
+ * node. */
+int ps_diffusion3d_scale_ci(double *Cs, const double *Ci, double lam, double dt, double _dx,
+                            int64_t n, void *stream);
 
 /* Compensated FP32 step: as ps_diffusion3d_step with dtype PS_F32, but the
  * update D2 = D + delta is done with a per-node Kahan compensation term

@@ -23,6 +23,7 @@ PS_ERR_UNSUPPORTED = -5
 PS_RUN_GRAPH = 1
 PS_RUN_COMPENSATED = 2
 PS_RUN_NATIVE_F64 = 4
+PS_RUN_CI_SCALED = 8
 
 STATUS_NAMES = {0: "PS_OK", -1: "PS_ERR_ARG", -2: "PS_ERR_ALIAS", -3: "PS_ERR_ALIGN",
                 -4: "PS_ERR_CUDA", -5: "PS_ERR_UNSUPPORTED"}
@@ -50,7 +51,10 @@ SIGNATURES = {
     "ps_last_error": (ctypes.c_char_p, []),
     "ps_workspace_bytes": (_SZ, []),
     "ps_device_error": (_I, [ctypes.POINTER(_U), _I]),
-    "ps_diffusion3d_step_kernel": (ctypes.c_char_p, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I]),
+    "ps_diffusion3d_step_kernel": (ctypes.c_char_p, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
+                                                     _U]),
+    "ps_diffusion3d_step_ex": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _U, _P]),
+    "ps_diffusion3d_scale_ci": (_I, [_P, _P, _D, _D, _D, _I64, _P]),
     "ps_diffusion3d_step": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_step_comp_f32": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _P]),
     "ps_diffusion3d_copy_boundary": (_I, [_P, _P, _I64, _I64, _I64, _I, _P]),

@@ -68,14 +68,34 @@ def _same(a: torch.Tensor, *others: torch.Tensor):
             raise ValueError("fields must share shape and device")
 
 
-def step(T2, T, Ci, lam: float, dt: float, inv_spacing: Sequence[float]) -> None:
-    """One step of Fig. 1 (``step!(T2, T, Ci, lam, dt, _dx, _dy, _dz)``)."""
+def step(T2, T, Ci, lam: float, dt: float, inv_spacing: Sequence[float], *,
+         ci_scaled: bool = False) -> None:
+    """One step of Fig. 1 (``step!(T2, T, Ci, lam, dt, _dx, _dy, _dz)``).
+
+    ``ci_scaled=True``: ``Ci`` is the pre-scaled field of :func:`scale_ci`
+    (FP64, equal spacings) and the step needs one FP64 multiply-add per node.
+    """
     code = _code(T)
     _same(T, T2, Ci)
     nx, ny, nz = _grid(T)
-    check(_lib.load().ps_diffusion3d_step(_field(T2, "T2", code), _field(T, "T", code),
-                                          _field(Ci, "Ci", code), lam, dt, *inv_spacing, nx, ny,
-                                          nz, code, _stream(T)))
+    lib = _lib.load()
+    if ci_scaled:
+        check(lib.ps_diffusion3d_step_ex(_field(T2, "T2", code), _field(T, "T", code),
+                                         _field(Ci, "Ci", code), lam, dt, *inv_spacing, nx, ny, nz,
+                                         code, _lib.PS_RUN_CI_SCALED, _stream(T)))
+        return
+    check(lib.ps_diffusion3d_step(_field(T2, "T2", code), _field(T, "T", code),
+                                  _field(Ci, "Ci", code), lam, dt, *inv_spacing, nx, ny, nz, code,
+                                  _stream(T)))
+
+
+def scale_ci(Ci, lam: float, dt: float, inv_spacing, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """``Cs = dt*lam*_dx^2 * Ci`` (FP64) for ``step``/``run`` with ``ci_scaled=True``."""
+    if out is None:
+        out = torch.empty_like(Ci)
+    check(_lib.load().ps_diffusion3d_scale_ci(_field(out, "Cs", PS_F64), _field(Ci, "Ci", PS_F64),
+                                              lam, dt, inv_spacing[0], Ci.numel(), _stream(Ci)))
+    return out
 
 
 def step_compensated(T2, T, comp, Ci, lam: float, dt: float, inv_spacing) -> None:
@@ -97,7 +117,7 @@ def copy_boundary(T2, T) -> None:
 
 
 def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, graph=False,
-        native_f64=False) -> torch.Tensor:
+        native_f64=False, ci_scaled=False) -> torch.Tensor:
     """Fig. 1 time loop on the buffer pair (T, T2); returns the tensor holding T(nt)."""
     code = _code(T)
     _same(T, T2, Ci)
@@ -110,6 +130,8 @@ def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, gr
         _same(T, comp)
     if native_f64:
         flags |= _lib.PS_RUN_NATIVE_F64
+    if ci_scaled:
+        flags |= _lib.PS_RUN_CI_SCALED
     odd = ctypes.c_int(0)
     check(_lib.load().ps_diffusion3d_run_ex(
         _field(T, "T", code), _field(T2, "T2", code),
@@ -267,12 +289,13 @@ def clear_graph_cache() -> None:
     check(_lib.load().ps_clear_graph_cache())
 
 
-def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing) -> str:
+def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing, ci_scaled=False) -> str:
     """Name of the kernel that :func:`step` launches for these arguments."""
     code = _code(T)
     nx, ny, nz = _grid(T)
+    flags = _lib.PS_RUN_CI_SCALED if ci_scaled else 0
     name = _lib.load().ps_diffusion3d_step_kernel(T2.data_ptr(), T.data_ptr(), Ci.data_ptr(), lam,
-                                                  dt, *inv_spacing, nx, ny, nz, code)
+                                                  dt, *inv_spacing, nx, ny, nz, code, flags)
     return name.decode()
 
 
@@ -305,6 +328,8 @@ def solve(T0_host: torch.Tensor, Ci_host: torch.Tensor, lam: float, dt: Optional
 
     ``dt=None`` takes Fig. 1's stable step from maximum(Ci) (reduced on the
     GPU).  ``buffers`` may hold preallocated device tensors ``(T, T2, Ci)``.
+    On FP64 grids with equal spacings the device ``Ci`` ends up holding the
+    pre-scaled coefficient of :func:`scale_ci`.
     """
     if buffers is None:
         T = torch.empty(T0_host.shape, dtype=T0_host.dtype, device=device)
@@ -316,7 +341,10 @@ def solve(T0_host: torch.Tensor, Ci_host: torch.Tensor, lam: float, dt: Optional
     Ci.copy_(Ci_host, non_blocking=True)
     if dt is None:
         dt = stable_dt(Ci, lam, lengths)
-    res = run(T, T2, Ci, lam, dt, inv_spacing, nt, graph=graph)
+    scaled = (T.dtype == torch.float64 and inv_spacing[0] == inv_spacing[1] == inv_spacing[2])
+    if scaled:  # fold dt*lam*_dx^2 into the coefficient field once per solve
+        scale_ci(Ci, lam, dt, inv_spacing, out=Ci)
+    res = run(T, T2, Ci, lam, dt, inv_spacing, nt, graph=graph, ci_scaled=scaled)
     if out_host is None:
         out_host = torch.empty(T0_host.shape, dtype=T0_host.dtype, pin_memory=True)
     out_host.copy_(res, non_blocking=True)

@@ -118,6 +118,8 @@ static int check_step_args(const void *T2, const void *T, const void *Ci, double
 static cudaError_t enqueue_step(void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
                                 Grid3 g, int dtype, unsigned flags, cudaStream_t s) {
     if (dtype == PS_F64) {
+        if (flags & PS_RUN_CI_SCALED)
+            return launch_step_f64_scaled((double *)T2, (const double *)T, (const double *)Ci, g, s);
         if (flags & PS_RUN_NATIVE_F64)
             return launch_step_f64_native((double *)T2, (const double *)T, (const double *)Ci, c, g, s);
         return launch_step_f64_fast((double *)T2, (const double *)T, (const double *)Ci, c, g, s);
@@ -212,13 +214,23 @@ int ps_device_error(unsigned *out_host, int clear) {
 
 const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void *Ci, double lam,
                                        double dt, double _dx, double _dy, double _dz, int64_t nx,
-                                       int64_t ny, int64_t nz, int dtype) {
+                                       int64_t ny, int64_t nz, int dtype, unsigned flags) {
     const Grid3 g{nx, ny, nz};
-    if (dtype == PS_F64) return step_f64_kernel_name(g, T2, T, Ci, make_coef(lam, dt, _dx, _dy, _dz));
+    if (dtype == PS_F64)
+        return step_f64_kernel_name(g, T2, T, Ci, make_coef(lam, dt, _dx, _dy, _dz),
+                                    (flags & PS_RUN_CI_SCALED) != 0);
     return step_f32_kernel_name(g, T2, T, Ci);
 }
 
 size_t ps_workspace_bytes(void) { return kWorkspaceBytes; }
+
+static int check_scaled(unsigned flags, int dtype, double _dx, double _dy, double _dz) {
+    if (!(flags & PS_RUN_CI_SCALED)) return PS_OK;
+    if (dtype != PS_F64) return fail(PS_ERR_UNSUPPORTED, "a pre-scaled Ci needs PS_F64");
+    if (!(_dx == _dy && _dy == _dz))
+        return fail(PS_ERR_UNSUPPORTED, "a pre-scaled Ci needs equal spacings (_dx == _dy == _dz)");
+    return PS_OK;
+}
 
 int ps_diffusion3d_step(void *T2, const void *T, const void *Ci, double lam, double dt, double _dx,
                         double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
@@ -227,6 +239,34 @@ int ps_diffusion3d_step(void *T2, const void *T, const void *Ci, double lam, dou
     cudaError_t e = enqueue_step(T2, T, nullptr, Ci, make_coef(lam, dt, _dx, _dy, _dz),
                                  Grid3{nx, ny, nz}, dtype, 0u, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_step");
+    return PS_OK;
+}
+
+int ps_diffusion3d_step_ex(void *T2, const void *T, const void *Ci, double lam, double dt,
+                           double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
+                           int dtype, unsigned flags, void *stream) {
+    PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, dtype));
+    if (flags & ~(PS_RUN_CI_SCALED | PS_RUN_NATIVE_F64)) return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
+    PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
+    if ((flags & PS_RUN_NATIVE_F64) && dtype != PS_F64)
+        return fail(PS_ERR_UNSUPPORTED, "PS_RUN_NATIVE_F64 needs PS_F64");
+    cudaError_t e = enqueue_step(T2, T, nullptr, Ci, make_coef(lam, dt, _dx, _dy, _dz),
+                                 Grid3{nx, ny, nz}, dtype, flags, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_step_ex");
+    return PS_OK;
+}
+
+int ps_diffusion3d_scale_ci(double *Cs, const double *Ci, double lam, double dt, double _dx,
+                            int64_t n, void *stream) {
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(Cs, "Cs"));
+    PS_TRY(check_ptr(Ci, "Ci"));
+    PS_TRY(check_finite(lam, "lam"));
+    PS_TRY(check_finite(dt, "dt"));
+    PS_TRY(check_finite(_dx, "_dx"));
+    if (Cs != Ci && overlap(Cs, Ci, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "Cs partly overlaps Ci");
+    cudaError_t e = launch_scale_ci(Cs, Ci, dt * lam * (_dx * _dx), n, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_scale_ci");
     return PS_OK;
 }
 
@@ -261,8 +301,9 @@ int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double 
                           int nt, int dtype, unsigned flags, void *stream, int *result_in_T2) {
     PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, dtype));
     if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
-    if (flags & ~(PS_RUN_GRAPH | PS_RUN_COMPENSATED | PS_RUN_NATIVE_F64))
+    if (flags & ~(PS_RUN_GRAPH | PS_RUN_COMPENSATED | PS_RUN_NATIVE_F64 | PS_RUN_CI_SCALED))
         return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
+    PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
     if (flags & PS_RUN_COMPENSATED) {
         if (dtype != PS_F32) return fail(PS_ERR_UNSUPPORTED, "PS_RUN_COMPENSATED needs PS_F32");
         PS_TRY(check_ptr(comp, "comp"));

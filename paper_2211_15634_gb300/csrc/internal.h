@@ -41,7 +41,11 @@ cudaError_t launch_step_f32(float *T2, const float *T, const float *Ci, StepCoef
                             cudaStream_t s);
 cudaError_t launch_step_f32_comp(float *T2, const float *T, float *comp, const float *Ci,
                                  StepCoef c, Grid3 g, cudaStream_t s);
-const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c);
+cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
+                                   cudaStream_t s);
+cudaError_t launch_scale_ci(double *Cs, const double *Ci, double K, int64_t n, cudaStream_t s);
+const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c,
+                                 bool scaled);
 const char *step_f32_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci);
 unsigned zmarch_device_error(bool clear);
 unsigned adjoint_device_error(bool clear);

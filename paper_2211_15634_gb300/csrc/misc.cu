@@ -61,6 +61,11 @@ __global__ void k_from_deviation(double *__restrict__ T, const float *__restrict
         T[p] = (double)D[p] + t_ref;
 }
 
+__global__ void k_scale_ci(double *__restrict__ Cs, const double *__restrict__ Ci, double K, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) Cs[p] = K * Ci[p];
+}
+
 static unsigned ew_blocks(int64_t n) {
     int64_t b = (n + 255) / 256;
     const int64_t cap = 8LL * sm_count();
@@ -76,6 +81,15 @@ cudaError_t launch_to_deviation(float *D, const double *T, double t_ref, int64_t
 cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64_t n,
                                   cudaStream_t s) {
     k_from_deviation<<<ew_blocks(n), 256, 0, s>>>(T, D, t_ref, n);
+    return cudaGetLastError();
+}
+
+}  // namespace psd
+
+namespace psd {
+
+cudaError_t launch_scale_ci(double *Cs, const double *Ci, double K, int64_t n, cudaStream_t s) {
+    k_scale_ci<<<ew_blocks(n), 256, 0, s>>>(Cs, Ci, K, n);
     return cudaGetLastError();
 }
 

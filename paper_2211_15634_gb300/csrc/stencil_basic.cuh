@@ -19,7 +19,7 @@ struct CoefT {
 
 // Same column march for FP64 data with the one-DFMA emulated arithmetic of
 // emu64.cuh (used when the TMA kernel cannot serve the grid, e.g. odd nx).
-template <bool kIso>
+template <bool kIso, bool kScaled>
 __global__ void __launch_bounds__(256)
 k_step_basic_emu(double *__restrict__ T2, const double *__restrict__ T,
                  const double *__restrict__ Ci, EmuCoef c, int64_t nx, int64_t ny, int64_t nz,
@@ -36,8 +36,11 @@ k_step_basic_emu(double *__restrict__ T2, const double *__restrict__ T,
     unsigned long long tm = Tb[p - sz], tc = Tb[p];
     for (int64_t k = k0; k < k1; ++k, p += sz) {
         const unsigned long long tp = Tb[p + sz];
-        T2[p] = emu_step_node<kIso, false>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy], Tb[p + sy], tm, tp,
-                                           Ci[p], c);
+        if (kScaled)  // Ci holds dt*lam*_d^2*Ci (isotropic grid)
+            T2[p] = emu_step_node_scaled(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy], Tb[p + sy], tm, tp, Ci[p]);
+        else
+            T2[p] = emu_step_node<kIso, false>(tc, Tb[p - 1], Tb[p + 1], Tb[p - sy], Tb[p + sy], tm,
+                                               tp, Ci[p], c);
         tm = tc;
         tc = tp;
     }
@@ -45,7 +48,7 @@ k_step_basic_emu(double *__restrict__ T2, const double *__restrict__ T,
 
 inline cudaError_t launch_step_basic_emu(double *T2, const double *T, const double *Ci,
                                          const EmuCoef &c, bool iso, int64_t nx, int64_t ny,
-                                         int64_t nz, int nsm, cudaStream_t s) {
+                                         int64_t nz, int nsm, cudaStream_t s, bool scaled = false) {
     const dim3 block(32, 8, 1);
     const int64_t gx = (nx - 2 + block.x - 1) / block.x, gy = (ny - 2 + block.y - 1) / block.y;
     int64_t want = (8LL * nsm + gx * gy - 1) / (gx * gy);
@@ -54,10 +57,12 @@ inline cudaError_t launch_step_basic_emu(double *T2, const double *T, const doub
     const int64_t gz = (nz - 2 + kchunk - 1) / kchunk;
     if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)gz);
-    if (iso)
-        k_step_basic_emu<true><<<grid, block, 0, s>>>(T2, T, Ci, c, nx, ny, nz, (int)kchunk);
+    if (scaled)
+        k_step_basic_emu<true, true><<<grid, block, 0, s>>>(T2, T, Ci, c, nx, ny, nz, (int)kchunk);
+    else if (iso)
+        k_step_basic_emu<true, false><<<grid, block, 0, s>>>(T2, T, Ci, c, nx, ny, nz, (int)kchunk);
     else
-        k_step_basic_emu<false><<<grid, block, 0, s>>>(T2, T, Ci, c, nx, ny, nz, (int)kchunk);
+        k_step_basic_emu<false, false><<<grid, block, 0, s>>>(T2, T, Ci, c, nx, ny, nz, (int)kchunk);
     return cudaGetLastError();
 }
 

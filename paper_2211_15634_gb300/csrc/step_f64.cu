@@ -34,7 +34,18 @@ cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, 
     return launch_step_basic_emu(T2, T, Ci, ek, iso, g.nx, g.ny, g.nz, sm_count(), s);
 }
 
-const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c) {
+// Ci already scaled to dt*lam*_dx^2*Ci (isotropic grids): one DFMA per node.
+cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
+                                   cudaStream_t s) {
+    const StepCoef dummy{1.0, 1.0, 1.0, 1.0};
+    if (zmarch_supported(g, 8, T2, T, Cs)) return launch_zmarch(Z_F64_SCALED, T2, T, nullptr, Cs, dummy, g, s);
+    const EmuCoef ek{};
+    return launch_step_basic_emu(T2, T, Cs, ek, true, g.nx, g.ny, g.nz, sm_count(), s, true);
+}
+
+const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c,
+                                 bool scaled) {
+    if (scaled) return zmarch_supported(g, 8, T2, T, Ci) ? "k_zmarch<F64_SCALED>" : "k_step_basic_emu";
     if (!emu_ok(c)) return "k_step_basic<double>";
     const bool iso = c.ax == c.ay && c.ay == c.az;
     if (zmarch_supported(g, 8, T2, T, Ci)) return iso ? "k_zmarch<F64_EMU_ISO>" : "k_zmarch<F64_EMU_ANISO>";

@@ -47,6 +47,8 @@ struct ZTraits<Z_F64_NATIVE> : ZTraits<Z_F64_EMU_ISO> {};
 template <>
 struct ZTraits<Z_F64_EMU_ISO_DMUL> : ZTraits<Z_F64_EMU_ISO> {};
 template <>
+struct ZTraits<Z_F64_SCALED> : ZTraits<Z_F64_EMU_ISO> {};
+template <>
 struct ZTraits<Z_F32> {
     using E = float;
     using V = float4;
@@ -177,9 +179,10 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
             }
             V out;
             if constexpr (MODE == Z_F64_EMU_ISO || MODE == Z_F64_EMU_ANISO ||
-                          MODE == Z_F64_EMU_ISO_DMUL) {
+                          MODE == Z_F64_EMU_ISO_DMUL || MODE == Z_F64_SCALED) {
                 constexpr bool kIso = MODE != Z_F64_EMU_ANISO;
                 constexpr bool kDmul = MODE == Z_F64_EMU_ISO_DMUL;
+                constexpr bool kScaled = MODE == Z_F64_SCALED;
                 unsigned long long c[PX], xm[PX], xp[PX], ym[PX], yp[PX], zm[PX], zp[PX];
 #pragma unroll
                 for (int i = 0; i < PX; ++i) {
@@ -234,16 +237,26 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
                 // warp-uniform branch: smooth fields take the short fast path
                 if (__all_sync(0xffffffffu, fast)) {
 #pragma unroll
-                    for (int i = 0; i < PX; ++i)
-                        reinterpret_cast<E *>(&out)[i] = emu_fast_node<kIso, kDmul>(
-                            c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i],
-                            (double)vget<V, E>(civ, i), p.ek);
+                    for (int i = 0; i < PX; ++i) {
+                        const double ci = (double)vget<V, E>(civ, i);
+                        if constexpr (kScaled)
+                            reinterpret_cast<E *>(&out)[i] =
+                                emu_fast_node_scaled(c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci);
+                        else
+                            reinterpret_cast<E *>(&out)[i] = emu_fast_node<kIso, kDmul>(
+                                c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci, p.ek);
+                    }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < PX; ++i)
-                        reinterpret_cast<E *>(&out)[i] = emu_step_node<kIso, kDmul>(
-                            c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i],
-                            (double)vget<V, E>(civ, i), p.ek);
+                    for (int i = 0; i < PX; ++i) {
+                        const double ci = (double)vget<V, E>(civ, i);
+                        if constexpr (kScaled)
+                            reinterpret_cast<E *>(&out)[i] =
+                                emu_step_node_scaled(c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci);
+                        else
+                            reinterpret_cast<E *>(&out)[i] = emu_step_node<kIso, kDmul>(
+                                c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci, p.ek);
+                    }
                 }
             } else
 #pragma unroll
@@ -436,6 +449,8 @@ cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const v
             return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F64_NATIVE:
             return launch_zmarch_t<Z_F64_NATIVE, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+        case Z_F64_SCALED:
+            return launch_zmarch_t<Z_F64_SCALED, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F32:
             return launch_zmarch_t<Z_F32, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F32_COMP:

@@ -15,6 +15,7 @@ enum ZMode {
     Z_F32 = 3,
     Z_F32_COMP = 4,
     Z_F64_EMU_ISO_DMUL = 5,  // two FP64 ops per node: fma(Ci*K, S, T)
+    Z_F64_SCALED = 6,        // Ci already holds dt*lam*_d^2*Ci: fma(Cs, S, T)
 };
 
 struct ZParams {

@@ -176,3 +176,32 @@ def test_batch_table_rejects_bad_problem(lib):
     assert b"problem 1" in lib.ps_last_error()
     arr = make_problems([8])
     assert lib.ps_batch_table_fill(buf, 16, arr, 1, _lib.PS_F64, 0, 0, 0, None) == _lib.PS_ERR_ARG
+
+
+def test_prescaled_step_rejects_fp32_anisotropic_and_unknown_flags(lib):
+    S = _lib.PS_RUN_CI_SCALED
+
+    def step_ex(inv=(7.0, 7.0, 7.0), dtype=_lib.PS_F64, flags=S):
+        return lib.ps_diffusion3d_step_ex(B, A, C, 1.0, 1e-3, *inv, 8, 8, 8, dtype, flags, None)
+
+    assert step_ex(dtype=_lib.PS_F32) == _lib.PS_ERR_UNSUPPORTED
+    assert step_ex(inv=(7.0, 7.0, 8.0)) == _lib.PS_ERR_UNSUPPORTED
+    assert b"equal spacings" in lib.ps_last_error()
+    assert step_ex(flags=0x40) == _lib.PS_ERR_ARG
+    odd = ctypes.c_int(-1)
+    assert lib.ps_diffusion3d_run_ex(A, B, None, C, 1.0, 1e-3, 7.0, 6.0, 7.0, 8, 8, 8, 3,
+                                     _lib.PS_F64, S, None, ctypes.byref(odd)) == _lib.PS_ERR_UNSUPPORTED
+    assert lib.ps_diffusion3d_scale_ci(B, A, 1.0, 1e-3, 7.0, 0, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_scale_ci(None, A, 1.0, 1e-3, 7.0, 10, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_scale_ci(A + 16, A, 1.0, 1e-3, 7.0, 10, None) == _lib.PS_ERR_ALIAS
+    assert lib.ps_diffusion3d_scale_ci(B, A, 1.0, float("inf"), 7.0, 10, None) == _lib.PS_ERR_ARG
+
+
+def test_kernel_names_for_the_fp64_step(lib):
+    name = lambda nx, flags: lib.ps_diffusion3d_step_kernel(B, A, C, 1.0, 1e-3, 7.0, 7.0, 7.0, nx, 8,
+                                                            8, _lib.PS_F64, flags).decode()
+    # the TMA kernel needs the driver's tensor-map encoder (absent without a GPU driver)
+    tma = name(64, 0) == "k_zmarch<F64_EMU_ISO>"
+    assert name(64, 0) == ("k_zmarch<F64_EMU_ISO>" if tma else "k_step_basic_emu")
+    assert name(64, _lib.PS_RUN_CI_SCALED) == ("k_zmarch<F64_SCALED>" if tma else "k_step_basic_emu")
+    assert name(63, _lib.PS_RUN_CI_SCALED) == "k_step_basic_emu"

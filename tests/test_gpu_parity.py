@@ -120,6 +120,64 @@ def test_run_nt0_returns_input():
     assert np.array_equal(gpu_run(T0, Ci, lam, dt, inv, 0), T0)
 
 
+# ------------------------------------------------------- pre-scaled coefficient
+def iso_problem(nx, ny, nz, gaussian=False):
+    """Workload fields on a grid with one spacing d in every direction."""
+    T0, Ci, lam, _, _ = problem(nx, ny, nz, gaussian=gaussian)
+    d = 1.0 / (max(nx, ny, nz) - 1)
+    dt = d * d / lam / Ci.max() / 6.1
+    return T0, Ci, lam, dt, (1.0 / d,) * 3
+
+
+def prescaled_run(T0, Ci, lam, dt, inv, nt, **kw):
+    T = to_dev(T0)
+    Cs = api.scale_ci(to_dev(Ci), lam, dt, inv)
+    return to_host(api.run(T, torch.empty_like(T), Cs, lam, dt, inv, nt, ci_scaled=True, **kw))
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 6, 7), (37, 29, 23), (66, 19, 20), (130, 67, 33),
+                                   (256, 35, 19), (68, 70, 40)])
+@pytest.mark.parametrize("nt", [1, 9])
+def test_fp64_prescaled_ci_matches_oracle(shape, nt):
+    """Cs = dt*lam*_d^2*Ci once, then T2 = T + Cs*(sum of neighbours - 6T):
+    the same step on a grid with equal spacings."""
+    T0, Ci, lam, dt, inv = iso_problem(*shape)
+    ref = oracle.run(T0, Ci, lam, dt, *inv, nt)
+    assert rel_linf(prescaled_run(T0, Ci, lam, dt, inv, nt), ref) <= FP64_TOL
+    assert api.device_error() == 0
+
+
+def test_fp64_prescaled_general_path_and_graph():
+    """Signs, zeros and binade changes (fixed-point path) with the pre-scaled
+    coefficient, run plainly and as a CUDA graph (bitwise equal)."""
+    nx, ny, nz, nt = 64, 31, 17, 6
+    _, Ci, lam, dt, inv = iso_problem(nx, ny, nz)
+    T0 = inputs.random_field((nz, ny, nx), 78, -1.0, 1.0)
+    T0[::3, :, ::5] = 0.0
+    T0[1::4, ::2, :] *= 1e-9
+    ref = oracle.run(T0, Ci, lam, dt, *inv, nt)
+    a = prescaled_run(T0, Ci, lam, dt, inv, nt)
+    b = prescaled_run(T0, Ci, lam, dt, inv, nt, graph=True)
+    assert rel_linf(a, ref) <= FP64_TOL and np.array_equal(a, b)
+    api.clear_graph_cache()
+
+
+def test_fp64_prescaled_step_kernel_and_in_place_scale():
+    nx, ny, nz = 64, 20, 12
+    T0, Ci, lam, dt, inv = iso_problem(nx, ny, nz, gaussian=True)
+    T, C = to_dev(T0), to_dev(Ci)
+    T2 = torch.empty_like(T)
+    api.copy_boundary(T2, T)
+    assert api.step_kernel_name(T2, T, C, lam, dt, inv, ci_scaled=True) == "k_zmarch<F64_SCALED>"
+    api.scale_ci(C, lam, dt, inv, out=C)  # in place
+    api.step(T2, T, C, lam, dt, inv, ci_scaled=True)
+    ref = T0.copy()
+    oracle.step(ref, T0, Ci, lam, dt, *inv)
+    assert rel_linf(to_host(T2), ref) <= 1e-15
+    with pytest.raises(Exception, match="equal spacings"):
+        api.step(T2, T, C, lam, dt, (inv[0], inv[1], inv[2] * 2), ci_scaled=True)
+
+
 # --------------------------------------------------------------------- FP32
 @pytest.mark.parametrize("kchunk", ["1", "3", "7"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
