@@ -49,10 +49,12 @@ def parse_args():
     p.add_argument("--no-secondary", action="store_true", help="skip FP32 / gradient / batch lines")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--kernel-loop", choices=["step", "adjoint"], default=None,
+    p.add_argument("--kernel-loop", choices=["step", "adjoint", "batch"], default=None,
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON)")
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     p.add_argument("--reps", type=int, default=4)
+    p.add_argument("--batch-count", type=int, default=256,
+                   help="kernel loop batch: the first this many problems of the 256-problem workload")
     p.add_argument("--plain-ci", action="store_true",
                    help="kernel loop: FP64 step on Ci as given instead of the pre-scaled field")
     return p.parse_args()
@@ -62,6 +64,8 @@ def run_kernel_loop(args):
     """Launch one kernel family a few times on --size^3 workload fields (for ncu)."""
     import torch
     from paper_2211_15634_gb300 import api, inputs
+    if args.kernel_loop == "batch":
+        return run_batch_loop(args)
     n = args.size
     T0, Ci, inv = fields(n)
     dev = torch.device("cuda")
@@ -88,6 +92,39 @@ def run_kernel_loop(args):
         name = "adjoint"
     torch.cuda.synchronize()
     log(f"kernel loop done: {name} x{args.reps} at {n}^3 {args.dtype}, device_error={api.device_error()}")
+    return 0
+
+
+def batch_workload(torch, api, inputs, dtype, dev, count=256):
+    """The batched workload: problem q is an n_q^3 grid, n_q uniform in 32..160."""
+    probs, nbytes = [], 0
+    esz = 8 if dtype == torch.float64 else 4
+    for q, nq in enumerate(inputs.batch_sizes(256)[:count]):
+        nq = int(nq)
+        T0q, Ciq = inputs.batch_problem(q, nq)
+        Tq = torch.from_numpy(T0q).to(dev)
+        Cq = torch.from_numpy(Ciq).to(dev)
+        if dtype == torch.float32:
+            Tq = api.to_deviation(Tq, 1.7)
+            Cq = api.to_f32(Cq)
+        dtq = api.stable_dt(Cq, 1.0)
+        probs.append(dict(T=Tq, T2=Tq.clone(), Ci=Cq, lam=1.0, dt=dtq,
+                          inv_spacing=inputs.inverse_spacing(nq, nq, nq)))
+        nbytes += 3 * nq ** 3 * esz
+    return probs, nbytes
+
+
+def run_batch_loop(args):
+    import torch
+    from paper_2211_15634_gb300 import api, inputs
+    dtype = torch.float64 if args.dtype == "f64" else torch.float32
+    probs, nbytes = batch_workload(torch, api, inputs, dtype, torch.device("cuda"), args.batch_count)
+    b = api.Batch(probs)
+    for it in range(args.reps):
+        b.step(it & 1)
+    torch.cuda.synchronize()
+    log(f"kernel loop done: k_batch_step x{args.reps}, {len(probs)} problems, {nbytes / 1e9:.2f} GB "
+        f"per step, {args.dtype}, device_error={api.device_error()}")
     return 0
 
 
@@ -417,20 +454,7 @@ def secondary_metrics(torch, api, ag, inputs, log):
     sizes = inputs.batch_sizes(256)
     nt = 500
     for name, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
-        probs, bytes_per_step = [], 0
-        esz = 8 if dtype == torch.float64 else 4
-        for q, nq in enumerate(sizes):
-            nq = int(nq)
-            T0q, Ciq = inputs.batch_problem(q, nq)
-            Tq = torch.from_numpy(T0q).to(dev)
-            Cq = torch.from_numpy(Ciq).to(dev)
-            if dtype == torch.float32:
-                Tq = api.to_deviation(Tq, 1.7)
-                Cq = api.to_f32(Cq)
-            dtq = api.stable_dt(Cq, 1.0)
-            probs.append(dict(T=Tq, T2=Tq.clone(), Ci=Cq, lam=1.0, dt=dtq,
-                              inv_spacing=inputs.inverse_spacing(nq, nq, nq)))
-            bytes_per_step += 3 * nq ** 3 * esz
+        probs, bytes_per_step = batch_workload(torch, api, inputs, dtype, dev, len(sizes))
         from paper_2211_15634_gb300 import tuner
         b0 = api.Batch(probs)  # library default tile for every problem
         t_0 = timed(lambda: b0.run(nt, graph=True), reps=1)
