@@ -56,7 +56,7 @@ def parse_args():
     p.add_argument("--batch-count", type=int, default=256,
                    help="kernel loop batch: the first this many problems of the 256-problem workload")
     p.add_argument("--plain-ci", action="store_true",
-                   help="kernel loop: FP64 step on Ci as given instead of the pre-scaled field")
+                   help="kernel loop: FP64 step/adjoint on Ci as given instead of the pre-scaled field")
     return p.parse_args()
 
 
@@ -84,12 +84,15 @@ def run_kernel_loop(args):
             api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
         name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled)
     else:
+        # FP64: the transposed step on the pre-scaled coefficient (--plain-ci: on Ci)
+        scaled = args.dtype == "f64" and not args.plain_ci
+        Cs = api.scale_ci(C, 1.0, dt, inv) if scaled else C
         ybar = T2 - T.mean()
         Tbar = torch.empty_like(T)
         Cib = torch.zeros_like(T)
         for _ in range(args.reps):
-            api.adjoint(Tbar, Cib, ybar, T, C, 1.0, dt, inv)
-        name = "adjoint"
+            api.adjoint(Tbar, Cib, ybar, T, Cs, 1.0, dt, inv, ci_scaled=scaled)
+        name = "adjoint (pre-scaled)" if scaled else "adjoint"
     torch.cuda.synchronize()
     log(f"kernel loop done: {name} x{args.reps} at {n}^3 {args.dtype}, device_error={api.device_error()}")
     return 0

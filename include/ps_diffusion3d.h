@@ -174,6 +174,20 @@ int ps_diffusion3d_adjoint(void *Tbar, void *Cibar, const void *ybar, const void
                            double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
                            void *stream);
 
+/* As ps_diffusion3d_adjoint with flags.  PS_RUN_CI_SCALED (PS_F64, equal
+ * spacings, else PS_ERR_UNSUPPORTED): `Ci` holds the pre-scaled field
+ * Cs = dt*lam*_dx^2*Ci of ps_diffusion3d_scale_ci, the transpose of the step
+ * T2 = T + Cs*L(T) with L(A) = (sum of the six neighbours) - 6 A:
+ *   w[q] = Cs[q]*ybar[q] at interior q (0 elsewhere), Tbar = ybar + L(w)
+ *   at every node, Cibar[q] += ybar[q]*L(T)[q] at interior q,
+ * so Cibar accumulates dL/dCs; dL/dCi = dt*lam*_dx^2 * dL/dCs (e.g. by
+ * ps_diffusion3d_scale_ci on the accumulated field).  lam, dt and the
+ * spacings are then only checked.  No other flag is accepted. */
+int ps_diffusion3d_adjoint_ex(void *Tbar, void *Cibar, const void *ybar, const void *T,
+                              const void *Ci, double lam, double dt, double _dx, double _dy,
+                              double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                              unsigned flags, void *stream);
+
 /* ---------------------------------------------------------------------
  * Reductions in FP64 (deterministic: a fixed partition and a fixed
  * summation order, independent of timing).  A, B are device arrays of n

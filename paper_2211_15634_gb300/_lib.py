@@ -64,6 +64,8 @@ SIGNATURES = {
                                    _P, ctypes.POINTER(_I)]),
     "ps_clear_graph_cache": (_I, []),
     "ps_diffusion3d_adjoint": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
+    "ps_diffusion3d_adjoint_ex": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
+                                       _U, _P]),
     "ps_maximum_async": (_I, [_P, _P, _I64, _I, _P, _P]),
     "ps_maximum": (_I, [ctypes.POINTER(_D), _P, _I64, _I, _P, _P]),
     "ps_diffusion3d_stable_dt": (_I, [ctypes.POINTER(_D), _P, _I64, _I64, _I64, _D, _D, _D, _D, _I,

@@ -140,15 +140,20 @@ def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, gr
     return T2 if odd.value else T
 
 
-def adjoint(Tbar, Cibar, ybar, T, Ci, lam: float, dt: float, inv_spacing) -> None:
-    """Transposed step: Tbar := M^T ybar; Cibar += dt*lam*ybar*Lap(T) (interior)."""
+def adjoint(Tbar, Cibar, ybar, T, Ci, lam: float, dt: float, inv_spacing, *,
+            ci_scaled: bool = False) -> None:
+    """Transposed step: Tbar := M^T ybar; Cibar += dt*lam*ybar*Lap(T) (interior).
+
+    ``ci_scaled=True``: ``Ci`` is the pre-scaled field of :func:`scale_ci` and
+    ``Cibar`` accumulates dL/dCs = ybar * L(T) (L = neighbour sum - 6 centre).
+    """
     code = _code(T)
     _same(T, Tbar, Cibar, ybar, Ci)
     nx, ny, nz = _grid(T)
-    check(_lib.load().ps_diffusion3d_adjoint(
+    check(_lib.load().ps_diffusion3d_adjoint_ex(
         _field(Tbar, "Tbar", code), _field(Cibar, "Cibar", code), _field(ybar, "ybar", code),
         _field(T, "T", code), _field(Ci, "Ci", code), lam, dt, *inv_spacing, nx, ny, nz, code,
-        _stream(T)))
+        _lib.PS_RUN_CI_SCALED if ci_scaled else 0, _stream(T)))
 
 
 def maximum_async(A, out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -8,6 +8,10 @@ checkpoint with the forward kernel, then applies the transposed step
 (``ps_diffusion3d_adjoint``) from the segment's last step to its first,
 accumulating dL/dCi.  dt is held constant (not differentiated through
 maximum(Ci)).  Memory: about ``nt/every + every + 2`` fields.
+
+On FP64 grids with equal spacings every kernel runs on the pre-scaled
+coefficient Cs = dt*lam*_dx^2*Ci (one FP64 multiply-add per node forward);
+the sweep then accumulates dL/dCs and returns dL/dCi = dt*lam*_dx^2 * dL/dCs.
 """
 from __future__ import annotations
 
@@ -22,6 +26,14 @@ def default_every(nt: int) -> int:
     return max(1, int(math.ceil(math.sqrt(nt))))
 
 
+def coefficient(Ci, lam, dt, inv):
+    """(field the kernels read, pre-scaled?): Cs = dt*lam*_dx^2*Ci on FP64 grids
+    with equal spacings, else Ci itself."""
+    if Ci.dtype == torch.float64 and inv[0] == inv[1] == inv[2]:
+        return api.scale_ci(Ci, lam, dt, inv), True
+    return Ci, False
+
+
 class _Pool:
     """Two work buffers plus the checkpoints, all with T0's boundary."""
 
@@ -34,8 +46,11 @@ class _Pool:
         return t
 
 
-def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every):
-    """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...])."""
+def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
+    """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...]).
+
+    ``coef`` = :func:`coefficient` (computed here when None)."""
+    C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     pool = _Pool(T0)
     ckpts = [T0]
     work = [pool.fresh(), pool.fresh()]
@@ -45,7 +60,7 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every):
             dst = pool.fresh()  # the step writes straight into the next checkpoint
         else:
             dst = work[0] if cur is not work[0] else work[1]
-        api.step(dst, cur, Ci, lam, dt, inv)
+        api.step(dst, cur, C, lam, dt, inv, ci_scaled=scaled)
         cur = dst
         if (t + 1) % every == 0 and t + 1 < nt:
             ckpts.append(cur)
@@ -54,11 +69,12 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every):
     return cur, ckpts
 
 
-def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts):
+def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None):
     """Reverse sweep; returns (dL/dT0, dL/dCi)."""
+    C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     ybar = ybar_nt.contiguous().clone()
     tbar = torch.empty_like(ybar)
-    cibar = torch.zeros_like(Ci)
+    cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
     pool = _Pool(ckpts[0])
     seg_bufs = []
     nseg = len(ckpts)
@@ -70,11 +86,13 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts):
             idx = t - t0 - 1
             if idx >= len(seg_bufs):
                 seg_bufs.append(pool.fresh())
-            api.step(seg_bufs[idx], states[-1], Ci, lam, dt, inv)
+            api.step(seg_bufs[idx], states[-1], C, lam, dt, inv, ci_scaled=scaled)
             states.append(seg_bufs[idx])
         for t in range(t1 - 1, t0 - 1, -1):
-            api.adjoint(tbar, cibar, ybar, states[t - t0], Ci, lam, dt, inv)
+            api.adjoint(tbar, cibar, ybar, states[t - t0], C, lam, dt, inv, ci_scaled=scaled)
             ybar, tbar = tbar, ybar
+    if scaled:  # dL/dCi = dt*lam*_dx^2 * dL/dCs
+        api.scale_ci(cibar, lam, dt, inv, out=cibar)
     return ybar, cibar
 
 
@@ -86,9 +104,11 @@ class Diffusion3DFn(torch.autograd.Function):
         T0 = T0.detach().contiguous()
         Ci = Ci.detach().contiguous()
         every = default_every(nt) if every is None else int(every)
-        out, ckpts = forward_checkpointed(T0, Ci, lam, dt, tuple(inv_spacing), int(nt), every)
+        coef = coefficient(Ci, lam, dt, tuple(inv_spacing))
+        out, ckpts = forward_checkpointed(T0, Ci, lam, dt, tuple(inv_spacing), int(nt), every, coef)
         ctx.cfg = (lam, dt, tuple(inv_spacing), int(nt), every)
         ctx.ckpts = ckpts
+        ctx.coef = coef
         ctx.save_for_backward(Ci)
         return out
 
@@ -96,8 +116,10 @@ class Diffusion3DFn(torch.autograd.Function):
     def backward(ctx, grad_out):
         (Ci,) = ctx.saved_tensors
         lam, dt, inv, nt, every = ctx.cfg
-        dT0, dCi = backward_checkpointed(grad_out, Ci, lam, dt, inv, nt, every, ctx.ckpts)
+        dT0, dCi = backward_checkpointed(grad_out, Ci, lam, dt, inv, nt, every, ctx.ckpts,
+                                         ctx.coef)
         ctx.ckpts = None
+        ctx.coef = None
         return dT0, dCi, None, None, None, None, None
 
 
@@ -105,8 +127,9 @@ def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None):
     """L = 1/2||T(nt) - Tobs||^2 (FP64 on the GPU) and (dL/dT0, dL/dCi)."""
     every = default_every(nt) if every is None else int(every)
     inv = tuple(inv_spacing)
-    out, ckpts = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every)
+    coef = coefficient(Ci.contiguous(), lam, dt, inv)
+    out, ckpts = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef)
     resid = torch.empty_like(out)
     L = api.half_sq_dist(out, Tobs, residual=resid)
-    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts)
+    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef)
     return L, dT0, dCi

@@ -206,7 +206,8 @@ const char *ps_last_error(void) { return g_err.c_str(); }
 
 int ps_device_error(unsigned *out_host, int clear) {
     if (!out_host) return fail(PS_ERR_ARG, "out_host is NULL");
-    *out_host = zmarch_device_error(clear != 0) | adjoint_device_error(clear != 0);
+    *out_host = zmarch_device_error(clear != 0) | adjoint_device_error(clear != 0) |
+                adjoint_scaled_device_error(clear != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ps_device_error");
     return PS_OK;
@@ -344,6 +345,15 @@ int ps_diffusion3d_adjoint(void *Tbar, void *Cibar, const void *ybar, const void
                            const void *Ci, double lam, double dt, double _dx, double _dy,
                            double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
                            void *stream) {
+    return ps_diffusion3d_adjoint_ex(Tbar, Cibar, ybar, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz,
+                                     dtype, 0u, stream);
+}
+
+int ps_diffusion3d_adjoint_ex(void *Tbar, void *Cibar, const void *ybar, const void *T,
+                              const void *Ci, double lam, double dt, double _dx, double _dy,
+                              double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                              unsigned flags, void *stream) {
+    if (flags & ~PS_RUN_CI_SCALED) return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
     PS_TRY(check_dtype(dtype));
     PS_TRY(check_grid(nx, ny, nz));
     PS_TRY(check_ptr(Tbar, "Tbar"));
@@ -362,10 +372,14 @@ int ps_diffusion3d_adjoint(void *Tbar, void *Cibar, const void *ybar, const void
         return fail(PS_ERR_ALIAS, "Tbar overlaps an input");
     if (overlap(Cibar, ybar, bytes) || overlap(Cibar, T, bytes) || overlap(Cibar, Ci, bytes))
         return fail(PS_ERR_ALIAS, "Cibar overlaps an input");
+    PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
     const StepCoef c = make_coef(lam, dt, _dx, _dy, _dz);
     const Grid3 g{nx, ny, nz};
     cudaError_t e;
-    if (dtype == PS_F64)
+    if (flags & PS_RUN_CI_SCALED)
+        e = launch_adjoint_f64_scaled((double *)Tbar, (double *)Cibar, (const double *)ybar,
+                                      (const double *)T, (const double *)Ci, g, (cudaStream_t)stream);
+    else if (dtype == PS_F64)
         e = launch_adjoint_f64((double *)Tbar, (double *)Cibar, (const double *)ybar,
                                (const double *)T, (const double *)Ci, c, g, (cudaStream_t)stream);
     else

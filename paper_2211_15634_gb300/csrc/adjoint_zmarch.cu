@@ -416,8 +416,9 @@ static cudaError_t launch_adj_t(E *Tbar, E *Cibar, const E *ybar, const E *T, co
         return cudaErrorInvalidValue;
     const int64_t ntx = (g.nx + BX - 1) / BX, nty = (g.ny + BY - 1) / BY, tiles = ntx * nty;
     if (kchunk <= 0) {
-        const int64_t target = 48LL * sm_count();
-        const int64_t kc = g.nz * tiles / target;
+        // long z-chunks amortise the two prologue planes; keep at least ~3 waves of CTAs
+        const int64_t waves = 3LL * 3 * sm_count();
+        const int64_t kc = g.nz * tiles / waves;
         kchunk = (int)(kc < 4 ? 4 : (kc > 16 ? 16 : kc));
     }
     const int64_t gz = (g.nz + kchunk - 1) / kchunk;

@@ -49,6 +49,7 @@ const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const v
 const char *step_f32_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci);
 unsigned zmarch_device_error(bool clear);
 unsigned adjoint_device_error(bool clear);
+unsigned adjoint_scaled_device_error(bool clear);
 
 // ---- helpers (misc.cu) ----
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);
@@ -59,6 +60,8 @@ cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64
 // ---- adjoint (adjoint.cu) ----
 cudaError_t launch_adjoint_f64(double *Tbar, double *Cibar, const double *ybar, const double *T,
                                const double *Ci, StepCoef c, Grid3 g, cudaStream_t s);
+cudaError_t launch_adjoint_f64_scaled(double *Tbar, double *Csbar, const double *ybar,
+                                      const double *T, const double *Cs, Grid3 g, cudaStream_t s);
 cudaError_t launch_adjoint_f32(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
 

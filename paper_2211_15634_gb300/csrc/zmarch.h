@@ -36,6 +36,9 @@ template <typename E>
 cudaError_t launch_adjoint_zmarch(E *Tbar, E *Cibar, const E *ybar, const E *T, const E *Ci,
                                   StepCoef c, Grid3 g, cudaStream_t s);
 unsigned adjoint_device_error(bool clear);
+// TMA-fed transposed step on the pre-scaled coefficient (adjoint_scaled.cu).
+cudaError_t launch_adjoint_scaled(double *Tbar, double *Csbar, const double *ybar, const double *T,
+                                  const double *Cs, Grid3 g, cudaStream_t s);
 cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
                           Grid3 g, cudaStream_t s);
 unsigned zmarch_device_error(bool clear);

@@ -205,3 +205,17 @@ def test_kernel_names_for_the_fp64_step(lib):
     assert name(64, 0) == ("k_zmarch<F64_EMU_ISO>" if tma else "k_step_basic_emu")
     assert name(64, _lib.PS_RUN_CI_SCALED) == ("k_zmarch<F64_SCALED>" if tma else "k_step_basic_emu")
     assert name(63, _lib.PS_RUN_CI_SCALED) == "k_step_basic_emu"
+
+
+def test_scaled_adjoint_rejects_fp32_anisotropic_and_unknown_flags(lib):
+    D, E = 0x290000000, 0x390000000
+    S = _lib.PS_RUN_CI_SCALED
+
+    def adj(inv=(7.0, 7.0, 7.0), dtype=_lib.PS_F64, flags=S):
+        return lib.ps_diffusion3d_adjoint_ex(E, B, A, C, D, 1.0, 1e-3, *inv, 8, 8, 8, dtype, flags, None)
+
+    assert adj(dtype=_lib.PS_F32) == _lib.PS_ERR_UNSUPPORTED
+    assert adj(inv=(7.0, 6.0, 7.0)) == _lib.PS_ERR_UNSUPPORTED
+    assert adj(flags=_lib.PS_RUN_GRAPH) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_adjoint_ex(A, B, A, C, D, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8,
+                                         _lib.PS_F64, S, None) == _lib.PS_ERR_ALIAS
