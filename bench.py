@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--reps", type=int, default=4)
     p.add_argument("--batch-count", type=int, default=256,
                    help="kernel loop batch: the first this many problems of the 256-problem workload")
+    p.add_argument("--temporal2", action="store_true",
+                   help="kernel loop step: fused step pairs (each rep is two two-step passes)")
     p.add_argument("--plain-ci", action="store_true",
                    help="kernel loop: FP64 step/adjoint on Ci as given instead of the pre-scaled field")
     return p.parse_args()
@@ -81,8 +83,13 @@ def run_kernel_loop(args):
         Cs = api.scale_ci(C, 1.0, dt, inv) if scaled else C
         for i in range(args.reps):
             src, dst = (T, T2) if i % 2 == 0 else (T2, T)
-            api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
-        name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled)
+            if args.temporal2:  # two fused two-step passes (plus the boundary copy); nt = 4
+                # keeps the result in `src`, as an even step count must
+                api.run(src, dst, Cs, 1.0, dt, inv, 4, ci_scaled=scaled, temporal2=True)
+            else:
+                api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
+        name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled,
+                                    temporal2=args.temporal2)
     else:
         # FP64: the transposed step on the pre-scaled coefficient (--plain-ci: on Ci)
         scaled = args.dtype == "f64" and not args.plain_ci

@@ -71,6 +71,11 @@ typedef enum {
 #define PS_RUN_NATIVE_F64 4u  /* PS_F64 only: force the plain FP64-instruction kernel */
 #define PS_RUN_CI_SCALED 8u   /* PS_F64, equal spacings: Ci holds dt*lam*_dx^2*Ci (see
                                  ps_diffusion3d_scale_ci); lam, dt are then only checked */
+#define PS_RUN_TEMPORAL2 16u  /* run only: two steps per pass (temporal blocking of depth
+                                 2), bit for bit the same result; needs PS_F32 without
+                                 PS_RUN_COMPENSATED, or PS_F64 with PS_RUN_CI_SCALED (else
+                                 PS_ERR_UNSUPPORTED); grids the TMA kernels cannot serve
+                                 (nx*sizeof not a multiple of 16) run single steps */
 
 /* Library version (major*10000 + minor*100 + patch). */
 int ps_version(void);

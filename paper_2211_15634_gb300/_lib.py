@@ -24,6 +24,7 @@ PS_RUN_GRAPH = 1
 PS_RUN_COMPENSATED = 2
 PS_RUN_NATIVE_F64 = 4
 PS_RUN_CI_SCALED = 8
+PS_RUN_TEMPORAL2 = 16
 
 STATUS_NAMES = {0: "PS_OK", -1: "PS_ERR_ARG", -2: "PS_ERR_ALIAS", -3: "PS_ERR_ALIGN",
                 -4: "PS_ERR_CUDA", -5: "PS_ERR_UNSUPPORTED"}

@@ -117,8 +117,11 @@ def copy_boundary(T2, T) -> None:
 
 
 def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, graph=False,
-        native_f64=False, ci_scaled=False) -> torch.Tensor:
-    """Fig. 1 time loop on the buffer pair (T, T2); returns the tensor holding T(nt)."""
+        native_f64=False, ci_scaled=False, temporal2=False) -> torch.Tensor:
+    """Fig. 1 time loop on the buffer pair (T, T2); returns the tensor holding T(nt).
+
+    ``temporal2=True`` runs the steps in fused pairs (FP32, or FP64 with
+    ``ci_scaled``); the result is bit for bit the same."""
     code = _code(T)
     _same(T, T2, Ci)
     nx, ny, nz = _grid(T)
@@ -132,6 +135,8 @@ def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, gr
         flags |= _lib.PS_RUN_NATIVE_F64
     if ci_scaled:
         flags |= _lib.PS_RUN_CI_SCALED
+    if temporal2:
+        flags |= _lib.PS_RUN_TEMPORAL2
     odd = ctypes.c_int(0)
     check(_lib.load().ps_diffusion3d_run_ex(
         _field(T, "T", code), _field(T2, "T2", code),
@@ -294,11 +299,12 @@ def clear_graph_cache() -> None:
     check(_lib.load().ps_clear_graph_cache())
 
 
-def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing, ci_scaled=False) -> str:
-    """Name of the kernel that :func:`step` launches for these arguments."""
+def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing, ci_scaled=False, temporal2=False) -> str:
+    """Name of the kernel that :func:`step` (or, with ``temporal2``, a fused pair
+    of :func:`run`) launches for these arguments."""
     code = _code(T)
     nx, ny, nz = _grid(T)
-    flags = _lib.PS_RUN_CI_SCALED if ci_scaled else 0
+    flags = (_lib.PS_RUN_CI_SCALED if ci_scaled else 0) | (_lib.PS_RUN_TEMPORAL2 if temporal2 else 0)
     name = _lib.load().ps_diffusion3d_step_kernel(T2.data_ptr(), T.data_ptr(), Ci.data_ptr(), lam,
                                                   dt, *inv_spacing, nx, ny, nz, code, flags)
     return name.decode()
@@ -306,7 +312,9 @@ def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing, ci_scaled=False) -> str:
 
 KERNEL_SOURCES = {
     "k_zmarch": ["paper_2211_15634_gb300/csrc/zmarch.cu", "paper_2211_15634_gb300/csrc/emu64.cuh",
-                 "paper_2211_15634_gb300/csrc/tma.cuh"],
+                 "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],
+    "k_zmarch2": ["paper_2211_15634_gb300/csrc/zmarch2.cu", "paper_2211_15634_gb300/csrc/emu64.cuh",
+                  "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],
     "k_step_basic_emu": ["paper_2211_15634_gb300/csrc/stencil_basic.cuh",
                          "paper_2211_15634_gb300/csrc/emu64.cuh"],
     "k_step_basic": ["paper_2211_15634_gb300/csrc/stencil_basic.cuh"],

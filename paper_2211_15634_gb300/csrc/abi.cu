@@ -130,14 +130,40 @@ static cudaError_t enqueue_step(void *T2, const void *T, void *comp, const void 
     return launch_step_f32((float *)T2, (const float *)T, (const float *)Ci, c, g, s);
 }
 
-// Boundary copy followed by nt steps with alternating buffers.
+// True when PS_RUN_TEMPORAL2 can fuse step pairs for these arguments (the mode
+// is checked by the caller: FP32 plain, or FP64 on the pre-scaled coefficient).
+static bool temporal2_ok(Grid3 g, int dtype, const void *T, const void *T2, const void *Ci) {
+    return zmarch2_supported(g, elem_bytes(dtype), T, T2, Ci) &&
+           zmarch2_supported(g, elem_bytes(dtype), T2, T, Ci);
+}
+
+static cudaError_t enqueue_step2(void *T2, const void *T, const void *Ci, StepCoef c, Grid3 g,
+                                 int dtype, cudaStream_t s) {
+    if (dtype == PS_F64) return launch_step2_f64_scaled((double *)T2, (const double *)T, (const double *)Ci, g, s);
+    return launch_step2_f32((float *)T2, (const float *)T, (const float *)Ci, c, g, s);
+}
+
+// Boundary copy followed by nt steps with alternating buffers.  With
+// PS_RUN_TEMPORAL2 the steps go in fused pairs; when the number of passes would
+// leave the result in the other buffer than nt's parity says, one pair is run
+// as two single steps.
 static cudaError_t enqueue_run(void *T, void *T2, void *comp, const void *Ci, StepCoef c, Grid3 g,
                                int nt, int dtype, unsigned flags, cudaStream_t s) {
     cudaError_t e = launch_copy_boundary(T2, T, g, elem_bytes(dtype), s);
-    for (int it = 0; it < nt && e == cudaSuccess; ++it) {
+    int pairs = 0, singles = nt;
+    if ((flags & PS_RUN_TEMPORAL2) && temporal2_ok(g, dtype, T, T2, Ci)) {
+        pairs = nt / 2;
+        singles = nt & 1;
+        if (((pairs + singles) & 1) != (nt & 1)) {
+            pairs -= 1;
+            singles += 2;
+        }
+    }
+    for (int it = 0; it < pairs + singles && e == cudaSuccess; ++it) {
         void *src = (it & 1) ? T2 : T;
         void *dst = (it & 1) ? T : T2;
-        e = enqueue_step(dst, src, comp, Ci, c, g, dtype, flags, s);
+        e = it < pairs ? enqueue_step2(dst, src, Ci, c, g, dtype, s)
+                       : enqueue_step(dst, src, comp, Ci, c, g, dtype, flags, s);
     }
     return e;
 }
@@ -207,7 +233,7 @@ const char *ps_last_error(void) { return g_err.c_str(); }
 int ps_device_error(unsigned *out_host, int clear) {
     if (!out_host) return fail(PS_ERR_ARG, "out_host is NULL");
     *out_host = zmarch_device_error(clear != 0) | adjoint_device_error(clear != 0) |
-                adjoint_scaled_device_error(clear != 0);
+                adjoint_scaled_device_error(clear != 0) | zmarch2_device_error(clear != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ps_device_error");
     return PS_OK;
@@ -217,6 +243,10 @@ const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void
                                        double dt, double _dx, double _dy, double _dz, int64_t nx,
                                        int64_t ny, int64_t nz, int dtype, unsigned flags) {
     const Grid3 g{nx, ny, nz};
+    if ((flags & PS_RUN_TEMPORAL2) && temporal2_ok(g, dtype, T, T2, Ci)) {
+        if (dtype == PS_F32 && !(flags & PS_RUN_COMPENSATED)) return "k_zmarch2<F32>";
+        if (dtype == PS_F64 && (flags & PS_RUN_CI_SCALED)) return "k_zmarch2<F64_SCALED>";
+    }
     if (dtype == PS_F64)
         return step_f64_kernel_name(g, T2, T, Ci, make_coef(lam, dt, _dx, _dy, _dz),
                                     (flags & PS_RUN_CI_SCALED) != 0);
@@ -302,9 +332,14 @@ int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double 
                           int nt, int dtype, unsigned flags, void *stream, int *result_in_T2) {
     PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, dtype));
     if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
-    if (flags & ~(PS_RUN_GRAPH | PS_RUN_COMPENSATED | PS_RUN_NATIVE_F64 | PS_RUN_CI_SCALED))
+    if (flags & ~(PS_RUN_GRAPH | PS_RUN_COMPENSATED | PS_RUN_NATIVE_F64 | PS_RUN_CI_SCALED |
+                  PS_RUN_TEMPORAL2))
         return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
     PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
+    if ((flags & PS_RUN_TEMPORAL2) &&
+        !(dtype == PS_F32 ? !(flags & PS_RUN_COMPENSATED) : (flags & PS_RUN_CI_SCALED) != 0))
+        return fail(PS_ERR_UNSUPPORTED,
+                    "PS_RUN_TEMPORAL2 needs PS_F32 (not compensated) or PS_F64 with PS_RUN_CI_SCALED");
     if (flags & PS_RUN_COMPENSATED) {
         if (dtype != PS_F32) return fail(PS_ERR_UNSUPPORTED, "PS_RUN_COMPENSATED needs PS_F32");
         PS_TRY(check_ptr(comp, "comp"));

@@ -44,6 +44,14 @@ cudaError_t launch_step_f32_comp(float *T2, const float *T, float *comp, const f
 cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
                                    cudaStream_t s);
 cudaError_t launch_scale_ci(double *Cs, const double *Ci, double K, int64_t n, cudaStream_t s);
+// two steps per pass (zmarch2.cu): T2 = step(step(T)); the caller checks zmarch2_supported
+// (the same preconditions as the one-step TMA kernel)
+bool zmarch2_supported(Grid3 g, int esz, const void *a, const void *b, const void *c);
+cudaError_t launch_step2_f32(float *T2, const float *T, const float *Ci, StepCoef c, Grid3 g,
+                             cudaStream_t s);
+cudaError_t launch_step2_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
+                                    cudaStream_t s);
+unsigned zmarch2_device_error(bool clear);
 const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c,
                                  bool scaled);
 const char *step_f32_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci);

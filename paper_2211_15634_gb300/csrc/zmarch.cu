@@ -25,6 +25,7 @@
 
 #include "emu64.cuh"
 #include "internal.h"
+#include "node.cuh"
 #include "tma.cuh"
 #include "zmarch.h"
 
@@ -272,13 +273,13 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
                     const double d2x = (xp - c) - (c - xm), d2y = (yp - c) - (c - ym);
                     const double d2z = (zp - c) - (c - zm);
                     r = c + p.ek.dtlam * (ci * ((d2x * p.ek.ax + d2y * p.ek.ay) + d2z * p.ek.az));
+                } else if constexpr (MODE == Z_F32) {
+                    r = f32_node(c, xm, xp, ym, yp, zm, zp, ci, p.fdtlam, p.fax, p.fay, p.faz);
                 } else {
                     const float d2x = (xp - c) - (c - xm), d2y = (yp - c) - (c - ym);
                     const float d2z = (zp - c) - (c - zm);
                     const float lap = (d2x * p.fax + d2y * p.fay) + d2z * p.faz;
-                    if constexpr (MODE == Z_F32) {
-                        r = c + p.fdtlam * (ci * lap);
-                    } else {
+                    {
                         const float delta = p.fdtlam * (ci * lap);
                         const float yv = delta - vget<V, E>(cv, i);
                         const float t = c + yv;

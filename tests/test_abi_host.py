@@ -219,3 +219,18 @@ def test_scaled_adjoint_rejects_fp32_anisotropic_and_unknown_flags(lib):
     assert adj(flags=_lib.PS_RUN_GRAPH) == _lib.PS_ERR_ARG
     assert lib.ps_diffusion3d_adjoint_ex(A, B, A, C, D, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8,
                                          _lib.PS_F64, S, None) == _lib.PS_ERR_ALIAS
+
+
+def test_temporal2_rejects_unsupported_modes(lib):
+    odd = ctypes.c_int(-1)
+    T2F = _lib.PS_RUN_TEMPORAL2
+
+    def run(dtype, flags, comp=None):
+        return lib.ps_diffusion3d_run_ex(A, B, comp, C, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8, 4, dtype,
+                                         flags, None, ctypes.byref(odd))
+
+    assert run(_lib.PS_F64, T2F) == _lib.PS_ERR_UNSUPPORTED
+    assert run(_lib.PS_F64, T2F | _lib.PS_RUN_NATIVE_F64) == _lib.PS_ERR_UNSUPPORTED
+    assert run(_lib.PS_F32, T2F | _lib.PS_RUN_COMPENSATED, comp=0x490000000) == _lib.PS_ERR_UNSUPPORTED
+    assert b"TEMPORAL2" in lib.ps_last_error()
+    assert run(_lib.PS_F64, 0x40) == _lib.PS_ERR_ARG
