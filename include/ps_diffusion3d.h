@@ -140,6 +140,15 @@ int ps_diffusion3d_step_comp_f32(float *T2, const float *T, float *comp, const f
 int ps_diffusion3d_copy_boundary(void *T2, const void *T, int64_t nx, int64_t ny, int64_t nz,
                                  int dtype, void *stream);
 
+/* The same for `count` grids stored one after another from dst, grid i at
+ * dst + i*grid_stride elements (grid_stride >= nx*ny*nz and a multiple of 16
+ * bytes, so that every grid keeps the 16-byte alignment the other calls
+ * need), in one launch: state buffers that all keep T's boundary.  T must not
+ * overlap them. */
+int ps_diffusion3d_copy_boundary_many(void *dst, int64_t count, int64_t grid_stride,
+                                      const void *T, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                                      void *stream);
+
 /* ---------------------------------------------------------------------
  * Time loop (Fig. 1): copy T's boundary into T2, then nt steps, swapping
  * the roles of T and T2 after each.  On return *result_in_T2 (host int,

@@ -59,6 +59,7 @@ SIGNATURES = {
     "ps_diffusion3d_step": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_step_comp_f32": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _P]),
     "ps_diffusion3d_copy_boundary": (_I, [_P, _P, _I64, _I64, _I64, _I, _P]),
+    "ps_diffusion3d_copy_boundary_many": (_I, [_P, _I64, _I64, _P, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_run": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _I, _P,
                                 ctypes.POINTER(_I)]),
     "ps_diffusion3d_run_ex": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _I, _U,

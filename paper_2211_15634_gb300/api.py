@@ -116,6 +116,22 @@ def copy_boundary(T2, T) -> None:
                                                    nx, ny, nz, code, _stream(T)))
 
 
+def state_block(T0, count: int):
+    """``count`` state buffers of T0's shape from one allocation, every one holding
+    T0's boundary (one launch) and starting on a 16-byte boundary; returns the list
+    of (nz, ny, nx) tensors."""
+    code = _code(T0)
+    nx, ny, nz = _grid(T0)
+    n = nx * ny * nz
+    per16 = 16 // T0.element_size()
+    stride = (n + per16 - 1) // per16 * per16
+    flat = torch.empty(count * stride, dtype=T0.dtype, device=T0.device)
+    if count:
+        check(_lib.load().ps_diffusion3d_copy_boundary_many(
+            flat.data_ptr(), count, stride, _field(T0, "T0", code), nx, ny, nz, code, _stream(T0)))
+    return [flat[i * stride:i * stride + n].view(T0.shape) for i in range(count)]
+
+
 def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, graph=False,
         native_f64=False, ci_scaled=False, temporal2=False) -> torch.Tensor:
     """Fig. 1 time loop on the buffer pair (T, T2); returns the tensor holding T(nt).

@@ -34,30 +34,20 @@ def coefficient(Ci, lam, dt, inv):
     return Ci, False
 
 
-class _Pool:
-    """Two work buffers plus the checkpoints, all with T0's boundary."""
-
-    def __init__(self, T0: torch.Tensor):
-        self.T0 = T0
-
-    def fresh(self) -> torch.Tensor:
-        t = torch.empty_like(self.T0)
-        api.copy_boundary(t, self.T0)
-        return t
-
-
 def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
     """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...]).
 
     ``coef`` = :func:`coefficient` (computed here when None)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
-    pool = _Pool(T0)
+    # checkpoints and two work buffers in one block, all with T0's boundary (one launch)
+    nck = (nt - 1) // every if nt > 0 else 0
+    block = api.state_block(T0, nck + 2)
+    work = [block[nck], block[nck + 1]]
     ckpts = [T0]
-    work = [pool.fresh(), pool.fresh()]
     cur = T0
     for t in range(nt):
         if (t + 1) % every == 0 and t + 1 < nt:
-            dst = pool.fresh()  # the step writes straight into the next checkpoint
+            dst = block[len(ckpts) - 1]  # the step writes straight into the next checkpoint
         else:
             dst = work[0] if cur is not work[0] else work[1]
         api.step(dst, cur, C, lam, dt, inv, ci_scaled=scaled)
@@ -75,8 +65,8 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     ybar = ybar_nt.contiguous().clone()
     tbar = torch.empty_like(ybar)
     cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
-    pool = _Pool(ckpts[0])
-    seg_bufs = []
+    # buffers for the recomputed states of one segment, with the boundary of T0
+    seg_bufs = api.state_block(ckpts[0], max(0, min(every, nt) - 1))
     nseg = len(ckpts)
     for s in range(nseg - 1, -1, -1):
         t0 = s * every
@@ -84,8 +74,6 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
         states = [ckpts[s]]
         for t in range(t0 + 1, t1):
             idx = t - t0 - 1
-            if idx >= len(seg_bufs):
-                seg_bufs.append(pool.fresh())
             api.step(seg_bufs[idx], states[-1], C, lam, dt, inv, ci_scaled=scaled)
             states.append(seg_bufs[idx])
         for t in range(t1 - 1, t0 - 1, -1):

@@ -327,6 +327,28 @@ int ps_diffusion3d_copy_boundary(void *T2, const void *T, int64_t nx, int64_t ny
     return PS_OK;
 }
 
+int ps_diffusion3d_copy_boundary_many(void *dst, int64_t count, int64_t grid_stride,
+                                      const void *T, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                                      void *stream) {
+    PS_TRY(check_dtype(dtype));
+    PS_TRY(check_grid(nx, ny, nz));
+    PS_TRY(check_ptr(dst, "dst"));
+    PS_TRY(check_ptr(T, "T"));
+    if (count < 1) return fail(PS_ERR_ARG, "count = %lld < 1", (long long)count);
+    const int64_t n = nx * ny * nz;
+    if (grid_stride < n || (grid_stride * elem_bytes(dtype)) % 16 != 0)
+        return fail(PS_ERR_ARG, "grid_stride = %lld: need >= nx*ny*nz and a multiple of 16 bytes",
+                    (long long)grid_stride);
+    const size_t gbytes = (size_t)grid_stride * elem_bytes(dtype);
+    if ((const char *)T < (const char *)dst + gbytes * (size_t)count &&
+        (const char *)dst < (const char *)T + (size_t)n * elem_bytes(dtype))
+        return fail(PS_ERR_ALIAS, "T overlaps the destination grids");
+    cudaError_t e = launch_copy_boundary_many(dst, count, grid_stride, T, Grid3{nx, ny, nz},
+                                              elem_bytes(dtype), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_copy_boundary_many");
+    return PS_OK;
+}
+
 int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double lam, double dt,
                           double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
                           int nt, int dtype, unsigned flags, void *stream, int *result_in_T2) {

@@ -61,6 +61,8 @@ unsigned adjoint_scaled_device_error(bool clear);
 
 // ---- helpers (misc.cu) ----
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);
+cudaError_t launch_copy_boundary_many(void *dst, int64_t count, int64_t gstride, const void *T,
+                                      Grid3 g, int elem_bytes, cudaStream_t s);
 cudaError_t launch_to_deviation(float *D, const double *T, double t_ref, int64_t n, cudaStream_t s);
 cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64_t n,
                                   cudaStream_t s);

@@ -4,13 +4,14 @@
 
 namespace psd {
 
-// blockIdx.y selects the face: 0/1 z = 0 / nz-1, 2/3 y = 0 / ny-1, 4/5 x = 0 / nx-1.
-// Edges and corners belong to several faces and are written with the same
-// value more than once.
+// blockIdx.y selects the face: 0/1 z = 0 / nz-1, 2/3 y = 0 / ny-1, 4/5 x = 0 / nx-1;
+// blockIdx.z the destination grid (dst + blockIdx.z * gstride).  Edges and corners
+// belong to several faces and are written with the same value more than once.
 template <typename E>
 __global__ void k_copy_boundary(E *__restrict__ dst, const E *__restrict__ src, int64_t nx,
-                                int64_t ny, int64_t nz) {
+                                int64_t ny, int64_t nz, int64_t gstride) {
     const int face = blockIdx.y;
+    dst += (int64_t)blockIdx.z * gstride;
     const int64_t count = face < 2 ? nx * ny : (face < 4 ? nx * nz : ny * nz);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
@@ -31,20 +32,33 @@ __global__ void k_copy_boundary(E *__restrict__ dst, const E *__restrict__ src, 
     }
 }
 
-cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes,
-                                 cudaStream_t s) {
+cudaError_t launch_copy_boundary_many(void *dst, int64_t count, int64_t gstride, const void *T,
+                                      Grid3 g, int elem_bytes, cudaStream_t s) {
     const int64_t maxface = g.nx * g.ny > g.nx * g.nz ? g.nx * g.ny : g.nx * g.nz;
     const int64_t mf = maxface > g.ny * g.nz ? maxface : g.ny * g.nz;
     int64_t blocks = (mf + 255) / 256;
-    if (blocks > 4LL * sm_count()) blocks = 4LL * sm_count();
-    const dim3 grid((unsigned)blocks, 6, 1);
-    if (elem_bytes == 8)
-        k_copy_boundary<unsigned long long><<<grid, 256, 0, s>>>(
-            (unsigned long long *)T2, (const unsigned long long *)T, g.nx, g.ny, g.nz);
-    else
-        k_copy_boundary<unsigned><<<grid, 256, 0, s>>>((unsigned *)T2, (const unsigned *)T, g.nx,
-                                                      g.ny, g.nz);
-    return cudaGetLastError();
+    const int64_t cap = (4LL * sm_count() + count - 1) / count;  // about 4 blocks per SM in all
+    if (blocks > cap) blocks = cap;
+    for (int64_t c0 = 0; c0 < count; c0 += 65535) {
+        const int64_t c = count - c0 < 65535 ? count - c0 : 65535;
+        const dim3 grid((unsigned)blocks, 6, (unsigned)c);
+        if (elem_bytes == 8)
+            k_copy_boundary<unsigned long long><<<grid, 256, 0, s>>>(
+                (unsigned long long *)dst + c0 * gstride, (const unsigned long long *)T, g.nx, g.ny,
+                g.nz, gstride);
+        else
+            k_copy_boundary<unsigned><<<grid, 256, 0, s>>>((unsigned *)dst + c0 * gstride,
+                                                          (const unsigned *)T, g.nx, g.ny, g.nz,
+                                                          gstride);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes,
+                                 cudaStream_t s) {
+    return launch_copy_boundary_many(T2, 1, g.nx * g.ny * g.nz, T, g, elem_bytes, s);
 }
 
 __global__ void k_to_deviation(float *__restrict__ D, const double *__restrict__ T, double t_ref,

@@ -234,3 +234,11 @@ def test_temporal2_rejects_unsupported_modes(lib):
     assert run(_lib.PS_F32, T2F | _lib.PS_RUN_COMPENSATED, comp=0x490000000) == _lib.PS_ERR_UNSUPPORTED
     assert b"TEMPORAL2" in lib.ps_last_error()
     assert run(_lib.PS_F64, 0x40) == _lib.PS_ERR_ARG
+
+
+def test_copy_boundary_many_rejects_bad_stride_and_overlap(lib):
+    many = lib.ps_diffusion3d_copy_boundary_many
+    assert many(B, 3, 511, A, 8, 8, 8, _lib.PS_F64, None) == _lib.PS_ERR_ARG   # < nx*ny*nz
+    assert many(B, 3, 514, A, 8, 8, 8, _lib.PS_F32, None) == _lib.PS_ERR_ARG   # not 16-byte
+    assert many(B, 0, 512, A, 8, 8, 8, _lib.PS_F64, None) == _lib.PS_ERR_ARG
+    assert many(A, 3, 512, A + 4096, 8, 8, 8, _lib.PS_F64, None) == _lib.PS_ERR_ALIAS

@@ -401,3 +401,23 @@ def test_fp64_512_one_step_samples():
     ref = light_cone_reference(oracle, T0, Ci, lam, dt, inv, 1, pts)
     vals = np.array([got[k, j, i] for (i, j, k) in pts])
     assert np.max(np.abs(vals - ref)) <= 1e-15 * np.max(np.abs(T0))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_state_block_copies_boundary_into_every_grid(dtype):
+    """One launch writes T's six faces into each of several padded grids and
+    leaves their interiors alone; every grid starts on a 16-byte boundary."""
+    nx, ny, nz = 7, 5, 3  # n = 105: odd, so the grids need a padded stride
+    T = to_dev(inputs.random_field((nz, ny, nx), 31), dtype)
+    grids = api.state_block(T, 5)
+    for g in grids:
+        g[1:-1, 1:-1, 1:-1] = -1.0
+    grids2 = api.state_block(T, 5)
+    for g in grids2:
+        assert g.data_ptr() % 16 == 0
+    inner = np.zeros((nz, ny, nx), dtype=bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    Th = to_host(T)
+    for g in grids:
+        gh = to_host(g)
+        assert np.array_equal(gh[~inner], Th[~inner]) and np.all(gh[inner] == -1.0)
