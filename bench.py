@@ -41,7 +41,7 @@ def log(*a):
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--size", type=int, default=512)
@@ -144,6 +144,32 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def median_ci95(xs):
+    """Median and a distribution-free 95% confidence interval of the median (order
+    statistics of the binomial(n, 1/2) law)."""
+    xs = sorted(xs)
+    n = len(xs)
+    if n < 6:
+        return statistics.median(xs), xs[0], xs[-1]
+    # largest j with P(Bin(n, 1/2) <= j-1) <= 0.025: the interval is [x_(j), x_(n-j+1)]
+    cdf, j = 0.0, 0
+    for k in range(n + 1):
+        cdf += math.comb(n, k) / 2.0 ** n
+        if cdf > 0.025:
+            j = k
+            break
+    j = max(j, 1)
+    return statistics.median(xs), xs[j - 1], xs[n - j]
+
+
+def step_samples(step_ms, bytes_per_step):
+    """Per-step device times (CUDA events around each step) as T_eff samples."""
+    med, lo, hi = median_ci95(step_ms)
+    rate = lambda ms: round(bytes_per_step / (ms / 1e3) / 1e9, 1)  # noqa: E731
+    return {"n": len(step_ms), "median_ms": round(med, 3), "ci95_ms": [round(lo, 3), round(hi, 3)],
+            "median_gbs": rate(med), "ci95_gbs": [rate(hi), rate(lo)]}
 
 
 def max_over_ranks(seconds: float, device=None) -> float:
@@ -343,6 +369,27 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- our path
+def torch_eager_teff(torch, T, T2, C, dt, inv, timed, nt=10):
+    """Fig. 1's step written as whole-field PyTorch slice expressions (one kernel per
+    operation, the analogue of the paper's GPU array-broadcast comparison), timed on
+    the same fields; T_eff by the same 3-array count."""
+    n = T.shape[0]
+    ax, ay, az = (v * v for v in inv)
+
+    def step(Ta, Tb):
+        c = Ta[1:-1, 1:-1, 1:-1]
+        d2x = (Ta[1:-1, 1:-1, 2:] - c) - (c - Ta[1:-1, 1:-1, :-2])
+        d2y = (Ta[1:-1, 2:, 1:-1] - c) - (c - Ta[1:-1, :-2, 1:-1])
+        d2z = (Ta[2:, 1:-1, 1:-1] - c) - (c - Ta[:-2, 1:-1, 1:-1])
+        Tb[1:-1, 1:-1, 1:-1] = c + dt * (1.0 * C[1:-1, 1:-1, 1:-1] * ((d2x * ax + d2y * ay) + d2z * az))
+
+    def loop():
+        for it in range(nt):
+            step(T, T2) if it % 2 == 0 else step(T2, T)
+    t = timed(loop, reps=2)
+    return round(3 * n ** 3 * T.element_size() * nt / t / 1e9, 1)
+
+
 def secondary_metrics(torch, api, ag, inputs, log):
     """FP32 512^3, gradient/forward ratio at 256^3, batched workload."""
     out = {}
@@ -372,7 +419,13 @@ def secondary_metrics(torch, api, ag, inputs, log):
     dt = api.stable_dt(C, 1.0)
     t = timed(lambda: api.run(T, T2, C, 1.0, dt, inv, nt, graph=True))
     out["fp64_512_plain_ci_teff_gbs"] = round(3 * n ** 3 * 8 * nt / t / 1e9, 1)
-    del T2
+    # FP64 in fused step pairs (temporal blocking of depth 2) on the pre-scaled coefficient
+    Cs = api.scale_ci(C, 1.0, dt, inv)
+    t = timed(lambda: api.run(T, T2, Cs, 1.0, dt, inv, nt, graph=True, ci_scaled=True, temporal2=True))
+    out["fp64_512_temporal2_teff_gbs"] = round(3 * n ** 3 * 8 * nt / t / 1e9, 1)
+    # the same step as plain PyTorch tensor expressions (slices of the whole field)
+    out["fp64_512_torch_eager_teff_gbs"] = torch_eager_teff(torch, T, T2, C, dt, inv, timed)
+    del T2, Cs
     api.clear_graph_cache()
     D = api.to_deviation(T, 1.7)
     C32 = api.to_f32(C)
@@ -384,6 +437,9 @@ def secondary_metrics(torch, api, ag, inputs, log):
     out["fp32_512_teff_gbs"] = round(3 * n ** 3 * 4 * nt / t / 1e9, 1)
     t = timed(lambda: api.run(D, D2, C32, 1.0, dt, inv, nt, comp=comp, graph=True))
     out["fp32c_512_teff_gbs"] = round(5 * n ** 3 * 4 * nt / t / 1e9, 1)
+    # fused step pairs: HBM traffic of one step per two (T_eff may exceed the copy rate)
+    t = timed(lambda: api.run(D, D2, C32, 1.0, dt, inv, nt, graph=True, temporal2=True))
+    out["fp32_512_temporal2_teff_gbs"] = round(3 * n ** 3 * 4 * nt / t / 1e9, 1)
     del D, D2, comp, C32
     api.clear_graph_cache()
     torch.cuda.empty_cache()
@@ -401,6 +457,9 @@ def secondary_metrics(torch, api, ag, inputs, log):
         t = timed(lambda: api.run(T, T2, C, 1.0, dt, inv, nt, graph=True, ci_scaled=scaled), reps=2)
         esz = 8 if dtype == torch.float64 else 4
         out[f"{name}_teff_gbs"] = round(3 * n ** 3 * esz * nt / t / 1e9, 1)
+        if not scaled:
+            t = timed(lambda: api.run(T, T2, C, 1.0, dt, inv, nt, graph=True, temporal2=True), reps=2)
+            out[f"{name}_temporal2_teff_gbs"] = round(3 * n ** 3 * esz * nt / t / 1e9, 1)
         del T, T2, C
         api.clear_graph_cache()
         torch.cuda.empty_cache()
@@ -433,7 +492,11 @@ def secondary_metrics(torch, api, ag, inputs, log):
     del Td, C32, D, D2
     torch.cuda.empty_cache()
 
-    # gradient / forward at 256^3, nt = 200, sqrt(nt) checkpoints
+    # gradient / forward at 256^3, nt = 200: L = 1/2||T(nt) - T_obs||^2, dL/dCi and dL/dT0.
+    # The forward run it is compared with is the fastest forward of the same problem
+    # (graph-captured; FP64 on the pre-scaled coefficient, as the gradient's own forward).
+    # Checkpoints every ceil(sqrt(nt)) steps (recompute per segment), and every state
+    # kept (27 GB at 256^3 FP64, no recompute).
     n, nt = 256, 200
     T0 = inputs.t0_gaussian(n, n, n)
     Ct = inputs.ci_smooth(n, n, n)
@@ -452,11 +515,23 @@ def secondary_metrics(torch, api, ag, inputs, log):
         a, b = Td.clone(), Td.clone()
         Tobs = api.run(a, b, Ctd, 1.0, dt, inv, nt).clone()
         fa, fb = Td.clone(), Td.clone()
-        t_fwd = timed(lambda: api.run(fa, fb, Cd, 1.0, dt, inv, nt, graph=True))
-        t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt), reps=2)
-        out[f"grad_over_fwd_256_{name}"] = round(t_grad / t_fwd, 3)
+        Cf, scaled = ag.coefficient(Cd, 1.0, dt, inv)
+        t_fwd = timed(lambda: api.run(fa, fb, Cf, 1.0, dt, inv, nt, graph=True, ci_scaled=scaled))
         out[f"fwd_256_{name}_ms"] = round(1e3 * t_fwd, 2)
-        del Td, Ctd, Cd, a, b, Tobs, fa, fb
+        for tag, every in (("sqrt_nt", None), ("all_states", 1)):
+            t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt, every=every), reps=2)
+            out[f"grad_over_fwd_256_{name}_{tag}"] = round(t_grad / t_fwd, 3)
+            torch.cuda.empty_cache()
+        # the transposed step alone (CUDA events, warm)
+        ybar = Td - Td.mean()
+        Tbar, Cib = torch.empty_like(Td), torch.zeros_like(Td)
+        def adj10():
+            for _ in range(10):
+                api.adjoint(Tbar, Cib, ybar, Td, Cf, 1.0, dt, inv, ci_scaled=scaled)
+        t_adj = timed(adj10, reps=3) / 10
+        out[f"adjoint_256_{name}_ms"] = round(1e3 * t_adj, 4)
+        out[f"adjoint_256_{name}_gbs"] = round(6 * n ** 3 * Td.element_size() / t_adj / 1e9, 1)
+        del Td, Ctd, Cd, Cf, a, b, Tobs, fa, fb, ybar, Tbar, Cib
         api.clear_graph_cache()
         torch.cuda.empty_cache()
 
@@ -545,16 +620,20 @@ def run_ours(args):
         dist.barrier()
     sampler = ClockSampler(local).start() if rank == 0 else None
     kev = [[[ev(), ev()] for _ in range(nt)] for _ in range(K)]
+    sev = [[ev(), ev()] for _ in range(K)]  # per-step samples
     torch.cuda.synchronize()
     t_start, t_end = ev(), ev()
     t_start.record()
     for s in range(K):
+        sev[s][0].record()
         one_step(kev[s])
+        sev[s][1].record()
     t_end.record()
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     region_s = t_start.elapsed_time(t_end) / 1e3
     launch_ms = [a.elapsed_time(b) for step in kev for (a, b) in step]
+    step_ms = [a.elapsed_time(b) for (a, b) in sev]
     region_s = max_over_ranks(region_s, dev)
     gbs = whole_job_rate(bytes_per_launch * nt * K, region_s, world) / 1e9
     # per step: max reduction (2 kernels), coefficient scaling, boundary copy, nt steps
@@ -620,6 +699,7 @@ def run_ours(args):
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
                      "launches_timed": len(launch_ms),
                      "mean_launch_ms": round(1e3 * mean_launch_s, 4)},
+        "samples": step_samples(step_ms, bytes_per_launch * nt),
         "graph_value": round(graph_gbs, 1),
         "e2e": e2e,
         "gpu_launches": gpu_launches,
