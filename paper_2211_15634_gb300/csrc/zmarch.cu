@@ -387,14 +387,14 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const vo
     const int64_t tiles = ntx * nty;
     if (kchunk <= 0) {
         // Short chunks keep many CTAs in flight (no wave tail) while consecutive
-        // CTAs - neighbouring tiles of one chunk - share their halo planes in L2.
-        // At 512^3 the best chunk measured 16 planes (FP32) and 32 (FP64); small
-        // grids go down to 4 planes so that they still fill the GPU (about 64
-        // CTAs per SM).
+        // CTAs - neighbouring tiles of one chunk - share their halo planes in L2;
+        // each chunk pays two extra planes.  Measured (sweeps at 256^3 and 512^3):
+        // FP32 is fastest at 8 planes; FP64 at 8 planes on small grids and flat from
+        // 24 to 40 planes at 512^3, so about 64 CTAs per SM between 8 and 32 planes.
         const int64_t target = 64LL * sm_count();
-        const int64_t kmax = sizeof(E) == 8 ? 32 : 16;
+        const int64_t kmax = sizeof(E) == 8 ? 32 : 8;
         int64_t kc = (g.nz - 2) * tiles / target;
-        kchunk = (int)(kc < 4 ? 4 : (kc > kmax ? kmax : kc));
+        kchunk = (int)(kc < 8 ? 8 : (kc > kmax ? kmax : kc));
     }
     const int64_t gz = (g.nz - 2 + kchunk - 1) / kchunk;
     if (tiles > 0x7fffffffLL || gz > 65535) return cudaErrorInvalidConfiguration;
