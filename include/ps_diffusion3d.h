@@ -168,6 +168,21 @@ int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double 
                           double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
                           int nt, int dtype, unsigned flags, void *stream, int *result_in_T2);
 
+/* Time loop that keeps states (the forward pass of a reverse sweep).  Runs
+ * nt steps from T0 (not modified).  The state after step t goes to grid slot
+ * t/every - 1 when every divides t, else to one of two work grids (slots
+ * nt/every and nt/every + 1; none when every == 1), never the grid the step
+ * reads.  Grid slot i is states + i*grid_stride elements (grid_stride >=
+ * nx*ny*nz, a multiple of 16 bytes); every grid's boundary must already equal
+ * T0's (ps_diffusion3d_copy_boundary_many).  *final_slot = the slot holding
+ * T(nt): >= 0 a state slot, -1 / -2 work grid 0 / 1, -3 T0 itself (nt = 0).
+ * Flags: PS_RUN_CI_SCALED, PS_RUN_NATIVE_F64 as for ps_diffusion3d_step_ex.
+ * One launch per step from a host loop in the library. */
+int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride, int every,
+                              const void *Ci, double lam, double dt, double _dx, double _dy,
+                              double _dz, int64_t nx, int64_t ny, int64_t nz, int nt, int dtype,
+                              unsigned flags, void *stream, int *final_slot);
+
 /* Destroy every cached CUDA graph. */
 int ps_clear_graph_cache(void);
 

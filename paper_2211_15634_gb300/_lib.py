@@ -64,6 +64,8 @@ SIGNATURES = {
                                 ctypes.POINTER(_I)]),
     "ps_diffusion3d_run_ex": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _I, _U,
                                    _P, ctypes.POINTER(_I)]),
+    "ps_diffusion3d_run_states": (_I, [_P, _P, _I64, _I, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
+                                       _I, _U, _P, ctypes.POINTER(_I)]),
     "ps_clear_graph_cache": (_I, []),
     "ps_diffusion3d_adjoint": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_adjoint_ex": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,

@@ -116,20 +116,55 @@ def copy_boundary(T2, T) -> None:
                                                    nx, ny, nz, code, _stream(T)))
 
 
+class StateBlock:
+    """``count`` state grids of T0's shape in one allocation, grid i starting
+    ``stride`` elements after grid i-1 (a 16-byte boundary), every one holding
+    T0's boundary (set by one launch).  ``grids[i]`` is grid i as a tensor."""
+
+    def __init__(self, T0, count: int):
+        code = _code(T0)
+        nx, ny, nz = _grid(T0)
+        n = nx * ny * nz
+        per16 = 16 // T0.element_size()
+        self.stride = (n + per16 - 1) // per16 * per16
+        self.flat = torch.empty(max(count, 1) * self.stride, dtype=T0.dtype, device=T0.device)
+        if count:
+            check(_lib.load().ps_diffusion3d_copy_boundary_many(
+                self.flat.data_ptr(), count, self.stride, _field(T0, "T0", code), nx, ny, nz, code,
+                _stream(T0)))
+        self.grids = [self.flat[i * self.stride:i * self.stride + n].view(T0.shape)
+                      for i in range(count)]
+
+    def ptr(self) -> int:
+        return self.flat.data_ptr()
+
+
 def state_block(T0, count: int):
-    """``count`` state buffers of T0's shape from one allocation, every one holding
-    T0's boundary (one launch) and starting on a 16-byte boundary; returns the list
-    of (nz, ny, nx) tensors."""
+    """The ``count`` grids of a :class:`StateBlock` as a list of tensors."""
+    return StateBlock(T0, count).grids
+
+
+def run_states(T0, block: "StateBlock", every: int, Ci, lam: float, dt: float, inv_spacing, nt: int,
+               *, ci_scaled: bool = False) -> torch.Tensor:
+    """nt steps from T0 keeping the state after step t in grid t/every - 1 of
+    ``block`` when every divides t (else in its two work grids after those);
+    returns the tensor holding T(nt).  One library call (``ps_diffusion3d_run_states``)."""
     code = _code(T0)
+    _same(T0, Ci)
     nx, ny, nz = _grid(T0)
-    n = nx * ny * nz
-    per16 = 16 // T0.element_size()
-    stride = (n + per16 - 1) // per16 * per16
-    flat = torch.empty(count * stride, dtype=T0.dtype, device=T0.device)
-    if count:
-        check(_lib.load().ps_diffusion3d_copy_boundary_many(
-            flat.data_ptr(), count, stride, _field(T0, "T0", code), nx, ny, nz, code, _stream(T0)))
-    return [flat[i * stride:i * stride + n].view(T0.shape) for i in range(count)]
+    nslots = nt // every
+    need = nslots + (2 if every > 1 and nt > 0 else 0)
+    if len(block.grids) < need:
+        raise ValueError(f"state block has {len(block.grids)} grids, needs {need}")
+    slot = ctypes.c_int(0)
+    check(_lib.load().ps_diffusion3d_run_states(
+        _field(T0, "T0", code), block.ptr(), block.stride, int(every), _field(Ci, "Ci", code), lam,
+        dt, *inv_spacing, nx, ny, nz, int(nt), code, _lib.PS_RUN_CI_SCALED if ci_scaled else 0,
+        _stream(T0), ctypes.byref(slot)))
+    s = slot.value
+    if s == -3:
+        return T0
+    return block.grids[s] if s >= 0 else block.grids[nslots + (-1 - s)]
 
 
 def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, graph=False,

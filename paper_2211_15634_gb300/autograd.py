@@ -39,23 +39,14 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
 
     ``coef`` = :func:`coefficient` (computed here when None)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
-    # checkpoints and two work buffers in one block, all with T0's boundary (one launch)
-    nck = (nt - 1) // every if nt > 0 else 0
-    block = api.state_block(T0, nck + 2)
-    work = [block[nck], block[nck + 1]]
-    ckpts = [T0]
-    cur = T0
-    for t in range(nt):
-        if (t + 1) % every == 0 and t + 1 < nt:
-            dst = block[len(ckpts) - 1]  # the step writes straight into the next checkpoint
-        else:
-            dst = work[0] if cur is not work[0] else work[1]
-        api.step(dst, cur, C, lam, dt, inv, ci_scaled=scaled)
-        cur = dst
-        if (t + 1) % every == 0 and t + 1 < nt:
-            ckpts.append(cur)
     if nt == 0:
-        cur = T0.clone()
+        return T0.clone(), [T0]
+    # checkpoints (the state after every `every`-th step) and two work grids in one block,
+    # all with T0's boundary; the steps write straight into them (one library call)
+    nslots = nt // every
+    block = api.StateBlock(T0, nslots + (2 if every > 1 else 0))
+    cur = api.run_states(T0, block, every, C, lam, dt, inv, nt, ci_scaled=scaled)
+    ckpts = [T0] + block.grids[:(nt - 1) // every]
     return cur, ckpts
 
 
@@ -65,17 +56,15 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     ybar = ybar_nt.contiguous().clone()
     tbar = torch.empty_like(ybar)
     cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
-    # buffers for the recomputed states of one segment, with the boundary of T0
-    seg_bufs = api.state_block(ckpts[0], max(0, min(every, nt) - 1))
+    # grids for the recomputed states of one segment, with the boundary of T0
+    seg = api.StateBlock(ckpts[0], max(0, min(every, nt) - 1))
     nseg = len(ckpts)
     for s in range(nseg - 1, -1, -1):
         t0 = s * every
         t1 = min(t0 + every, nt)
-        states = [ckpts[s]]
-        for t in range(t0 + 1, t1):
-            idx = t - t0 - 1
-            api.step(seg_bufs[idx], states[-1], C, lam, dt, inv, ci_scaled=scaled)
-            states.append(seg_bufs[idx])
+        if t1 - t0 > 1:  # states t0+1 .. t1-1 from the checkpoint, every one kept
+            api.run_states(ckpts[s], seg, 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
+        states = [ckpts[s]] + seg.grids[:t1 - t0 - 1]
         for t in range(t1 - 1, t0 - 1, -1):
             api.adjoint(tbar, cibar, ybar, states[t - t0], C, lam, dt, inv, ci_scaled=scaled)
             ybar, tbar = tbar, ybar

@@ -349,6 +349,54 @@ int ps_diffusion3d_copy_boundary_many(void *dst, int64_t count, int64_t grid_str
     return PS_OK;
 }
 
+int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride, int every,
+                              const void *Ci, double lam, double dt, double _dx, double _dy,
+                              double _dz, int64_t nx, int64_t ny, int64_t nz, int nt, int dtype,
+                              unsigned flags, void *stream, int *final_slot) {
+    PS_TRY(check_step_args(states, T0, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, dtype));
+    if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
+    if (every < 1) return fail(PS_ERR_ARG, "every = %d < 1", every);
+    if (!final_slot) return fail(PS_ERR_ARG, "final_slot is NULL");
+    if (flags & ~(PS_RUN_CI_SCALED | PS_RUN_NATIVE_F64)) return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
+    PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
+    if ((flags & PS_RUN_NATIVE_F64) && dtype != PS_F64)
+        return fail(PS_ERR_UNSUPPORTED, "PS_RUN_NATIVE_F64 needs PS_F64");
+    const int64_t n = nx * ny * nz;
+    const size_t esz = elem_bytes(dtype);
+    if (grid_stride < n || (grid_stride * (int64_t)esz) % 16 != 0)
+        return fail(PS_ERR_ARG, "grid_stride = %lld: need >= nx*ny*nz and a multiple of 16 bytes",
+                    (long long)grid_stride);
+    const int nslots = nt / every, nwork = (every > 1 && nt > 0) ? 2 : 0;
+    const size_t span = (size_t)grid_stride * esz * (size_t)(nslots + nwork);
+    if (span && (overlap2(states, span, T0, (size_t)n * esz) || overlap2(states, span, Ci, (size_t)n * esz)))
+        return fail(PS_ERR_ALIAS, "the state grids overlap T0 or Ci");
+    char *base = (char *)states;
+    auto grid = [&](int slot) { return (void *)(base + (size_t)slot * (size_t)grid_stride * esz); };
+    const StepCoef c = make_coef(lam, dt, _dx, _dy, _dz);
+    const Grid3 g{nx, ny, nz};
+    const void *cur = T0;
+    int cur_slot = -3, work_next = 0;  // -3: T0; -1, -2: work grids 0, 1
+    for (int t = 1; t <= nt; ++t) {
+        int slot;
+        void *dst;
+        if (t % every == 0) {
+            slot = t / every - 1;
+            dst = grid(slot);
+        } else {  // a work grid, never the one this step reads
+            if (cur_slot == -1 - work_next) work_next ^= 1;
+            slot = -1 - work_next;
+            dst = grid(nslots + work_next);
+            work_next ^= 1;
+        }
+        cudaError_t e = enqueue_step(dst, cur, nullptr, Ci, c, g, dtype, flags, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_run_states");
+        cur = dst;
+        cur_slot = slot;
+    }
+    *final_slot = cur_slot;
+    return PS_OK;
+}
+
 int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double lam, double dt,
                           double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz,
                           int nt, int dtype, unsigned flags, void *stream, int *result_in_T2) {

@@ -421,3 +421,27 @@ def test_state_block_copies_boundary_into_every_grid(dtype):
     for g in grids:
         gh = to_host(g)
         assert np.array_equal(gh[~inner], Th[~inner]) and np.all(gh[inner] == -1.0)
+
+
+@pytest.mark.parametrize("nt,every", [(0, 1), (1, 1), (7, 1), (7, 3), (9, 3), (5, 8), (12, 5)])
+def test_run_states_keeps_the_states_of_a_step_loop(nt, every):
+    """The library's state-keeping time loop: slot t/every - 1 holds the state after
+    step t (every dividing t), the returned grid holds T(nt), bit for bit the states
+    of single steps; T0 is not modified."""
+    nx, ny, nz = 34, 21, 17
+    T0h, Ci, lam, dt, inv = problem(nx, ny, nz)
+    T0 = to_dev(T0h)
+    C = to_dev(Ci)
+    block = api.StateBlock(T0, nt // every + (2 if every > 1 and nt > 0 else 0))
+    final = api.run_states(T0, block, every, C, lam, dt, inv, nt)
+    a, b = T0.clone(), T0.clone()
+    api.copy_boundary(b, a)
+    cur = a
+    for t in range(1, nt + 1):
+        dst = b if cur is a else a
+        api.step(dst, cur, C, lam, dt, inv)
+        cur = dst
+        if t % every == 0:
+            assert torch.equal(block.grids[t // every - 1], cur), t
+    assert torch.equal(final, cur)
+    assert np.array_equal(to_host(T0), T0h)
