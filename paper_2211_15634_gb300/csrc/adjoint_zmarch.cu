@@ -111,6 +111,14 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
         par ^= 1u << s;
         return mbar_wait(&bar[s], ph);
     };
+    // After a timed-out wait: bounded waits for the copies of the last NST planes issued
+    // (up to plane q_iss), so that no TMA write lands after the CTA exits.
+    auto drain = [&](int q_iss) {
+        for (int q = max(k0 - 1, q_iss - NST + 1); q <= q_iss; ++q) {
+            const int i = q - (k0 - 1);
+            mbar_wait(&bar[i % NST], (unsigned)(i / NST) & 1u);
+        }
+    };
     // w of tile position (r, c) of plane q, from a stage
     auto wval = [&](const E *Ys, const E *Cs, int r, int c, int q) -> E {
         const int x = X0 - HX + c, y = Y0 - 1 + r;
@@ -223,7 +231,10 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
             atomicOr(&g_adj_error, 1u);
         }
         __syncthreads();  // w tile k+1 complete; every thread has left iteration k-1
-        if (s_abort) return;
+        if (s_abort) {  // planes up to k-2+NST (at most k1) have been issued
+            drain(min(k - 2 + NST, k1));
+            return;
+        }
         if (threadIdx.x == 0 && k - 1 + NST <= k1) issue(s_m, k - 1 + NST);  // plane k-1's stage
 
         const E *Tk = ring + (3 * s_c) * SS;

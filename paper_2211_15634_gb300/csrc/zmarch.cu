@@ -126,6 +126,19 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
         par ^= 1u << s;
         return mbar_wait(b, ph);
     };
+    // After a timed-out wait: bounded waits for the copies of the last planes issued to
+    // each ring (T up to plane qT, Ci up to plane qC), so that no TMA write lands after
+    // the CTA exits.
+    auto drain = [&](int qT, int qC) {
+        for (int q = max(k0 - 1, qT - NST + 1); q <= qT; ++q) {
+            const int i = q - (k0 - 1);
+            mbar_wait(&bar[i % NST], (unsigned)(i / NST) & 1u);
+        }
+        for (int q = max(k0, qC - NSC + 1); q <= qC; ++q) {
+            const int i = q - k0;
+            mbar_wait(&bar[NST + i % NSC], (unsigned)(i / NSC) & 1u);
+        }
+    };
 
     const int row = ty + 1, col = HX + lane * PX;
     bool ok = acquire(&bar[0], tpar, 0);
@@ -137,7 +150,10 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
         atomicOr(&g_zmarch_error, 1u);
     }
     __syncthreads();
-    if (s_abort) return;
+    if (s_abort) {
+        drain(min(k0 - 2 + NST, k1), min(k0 - 1 + NSC, k1 - 1));
+        return;
+    }
     if (threadIdx.x == 0) {
         const int q = k0 - 1 + NST;
         if (q <= k1) {  // stage 0 held plane k0-1
@@ -309,7 +325,10 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
             atomicOr(&g_zmarch_error, 1u);
         }
         __syncthreads();  // every thread is done with plane k's T stage and Ci stage
-        if (s_abort) return;
+        if (s_abort) {
+            drain(min(k - 1 + NST, k1), min(k - 1 + NSC, k1 - 1));
+            return;
+        }
         if (threadIdx.x == 0) {
             if (k + NST <= k1) {  // plane k's T stage takes plane k + NST
                 mbar_expect_tx(&bar[sk], TB);
