@@ -93,6 +93,13 @@ size_t ps_workspace_bytes(void);
  * clear != 0 the flags are reset.  Synchronizes the device. */
 int ps_device_error(unsigned *out_host, int clear);
 
+/* Failure-path self-test (no fault): launches one CTA that waits on an
+ * mbarrier nothing ever arrives on; the bounded wait gives up after `polls`
+ * polls (1 .. 2^24) of at most `suspend_ns` ns each (1 .. 10^6) and sets bit
+ * 0 of ps_device_error - the path a pipelined kernel takes when a shared-
+ * memory stage never lands.  Asynchronous on `stream`. */
+int ps_selftest_bounded_wait(unsigned polls, unsigned suspend_ns, void *stream);
+
 /* Name of the kernel ps_diffusion3d_step_ex would launch for these arguments
  * and flags (for profiles and reports; no validation, launches nothing). */
 const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void *Ci, double lam,

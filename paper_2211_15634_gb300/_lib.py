@@ -52,6 +52,7 @@ SIGNATURES = {
     "ps_last_error": (ctypes.c_char_p, []),
     "ps_workspace_bytes": (_SZ, []),
     "ps_device_error": (_I, [ctypes.POINTER(_U), _I]),
+    "ps_selftest_bounded_wait": (_I, [_U, _U, _P]),
     "ps_diffusion3d_step_kernel": (ctypes.c_char_p, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
                                                      _U]),
     "ps_diffusion3d_step_ex": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _U, _P]),

@@ -239,6 +239,15 @@ int ps_device_error(unsigned *out_host, int clear) {
     return PS_OK;
 }
 
+int ps_selftest_bounded_wait(unsigned polls, unsigned suspend_ns, void *stream) {
+    if (polls < 1 || polls > (1u << 24)) return fail(PS_ERR_ARG, "polls = %u not in [1, 2^24]", polls);
+    if (suspend_ns < 1 || suspend_ns > 1000000u)
+        return fail(PS_ERR_ARG, "suspend_ns = %u not in [1, 10^6]", suspend_ns);
+    cudaError_t e = launch_selftest_wait(polls, suspend_ns, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_selftest_bounded_wait");
+    return PS_OK;
+}
+
 const char *ps_diffusion3d_step_kernel(const void *T2, const void *T, const void *Ci, double lam,
                                        double dt, double _dx, double _dy, double _dz, int64_t nx,
                                        int64_t ny, int64_t nz, int dtype, unsigned flags) {

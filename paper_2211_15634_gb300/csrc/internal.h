@@ -56,6 +56,7 @@ const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const v
                                  bool scaled);
 const char *step_f32_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci);
 unsigned zmarch_device_error(bool clear);
+cudaError_t launch_selftest_wait(unsigned polls, unsigned ns, cudaStream_t s);
 unsigned adjoint_device_error(bool clear);
 unsigned adjoint_scaled_device_error(bool clear);
 

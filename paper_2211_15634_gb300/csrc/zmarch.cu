@@ -346,6 +346,26 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
     }
 }
 
+// Failure-path self-test: one CTA waits on an mbarrier that nothing ever arrives on.
+// The bounded wait gives up after `polls` polls of at most `ns` nanoseconds each and
+// reports through the same device flag as a pipelined kernel's time-out.
+__global__ void k_selftest_wait(unsigned polls, unsigned ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    bool done = false;
+    for (unsigned i = 0; i < polls && !done; ++i) done = mbar_try_wait_hint(&bar, 0u, ns);
+    if (!done && threadIdx.x == 0) atomicOr(&g_zmarch_error, 1u);
+}
+
+cudaError_t launch_selftest_wait(unsigned polls, unsigned ns, cudaStream_t s) {
+    k_selftest_wait<<<1, 32, 0, s>>>(polls, ns);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ host
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -242,3 +242,10 @@ def test_copy_boundary_many_rejects_bad_stride_and_overlap(lib):
     assert many(B, 3, 514, A, 8, 8, 8, _lib.PS_F32, None) == _lib.PS_ERR_ARG   # not 16-byte
     assert many(B, 0, 512, A, 8, 8, 8, _lib.PS_F64, None) == _lib.PS_ERR_ARG
     assert many(A, 3, 512, A + 4096, 8, 8, 8, _lib.PS_F64, None) == _lib.PS_ERR_ALIAS
+
+
+def test_selftest_rejects_out_of_range_arguments(lib):
+    assert lib.ps_selftest_bounded_wait(0, 1000, None) == _lib.PS_ERR_ARG
+    assert lib.ps_selftest_bounded_wait((1 << 24) + 1, 1000, None) == _lib.PS_ERR_ARG
+    assert lib.ps_selftest_bounded_wait(16, 0, None) == _lib.PS_ERR_ARG
+    assert lib.ps_selftest_bounded_wait(16, 2000000, None) == _lib.PS_ERR_ARG
