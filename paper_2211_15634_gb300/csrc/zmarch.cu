@@ -4,8 +4,8 @@
 // thread, one warp per tile row) and a chunk of z-planes.  For every plane a
 // single thread issues one TMA box load of the tile plus a one-node halo in
 // y and a 16-byte halo in x (so every box starts on a 16-byte boundary) into
-// a ring of NST shared-memory stages, and one box of Ci into a ring of NSC
-// stages; completion is tracked with mbarrier transaction counts.  Each
+// a ring of NST shared-memory stages, together with the box of Ci of the same
+// plane (output planes only), both counted on the stage's one mbarrier.  Each
 // thread keeps its PX centre values of planes k-1, k, k+1 in registers (the
 // z-neighbours) and reads x/y neighbours of plane k from shared memory, so
 // every T value is read from HBM once (plus halos that mostly hit in L2).
@@ -63,14 +63,7 @@ __device__ __forceinline__ E vget(const V &v, int i) {
     return reinterpret_cast<const E *>(&v)[i];
 }
 
-template <int MODE>
-__device__ __forceinline__ constexpr unsigned zstage_bytes(int BY) {
-    using E = typename ZTraits<MODE>::E;
-    constexpr int PX = ZTraits<MODE>::PX;
-    return ((32 * PX + 2 * PX) * (BY + 2) * sizeof(E) + 127) / 128 * 128;
-}
-
-template <int MODE, int BY, int NST, int NSC>
+template <int MODE, int BY, int NST>
 __global__ void __launch_bounds__(32 * BY, 1)
 k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmC,
          void *__restrict__ T2v, void *__restrict__ compv, const ZParams p) {
@@ -83,7 +76,7 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
     extern __shared__ __align__(128) unsigned char smem[];
     E *sT = (E *)smem;
     E *sC = (E *)(smem + NST * TBA);
-    uint64_t *bar = (uint64_t *)(smem + NST * TBA + NSC * CBA);
+    uint64_t *bar = (uint64_t *)(smem + NST * (TBA + CBA));
     __shared__ int s_abort;
 
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -93,57 +86,43 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int s = 0; s < NST + NSC; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    // T planes k0-1 .. k1 live in stage (q - (k0-1)) % NST; Ci planes k0 .. k1-1 in (q - k0) % NSC
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < NST; ++s) {
-            const int q = k0 - 1 + s;
-            if (q <= k1) {
-                mbar_expect_tx(&bar[s], TB);
-                tma_load_3d(sT + s * (TBA / sizeof(E)), &tmT, &bar[s], X0 - HX, Y0 - 1, q);
-            }
-        }
-        for (int s = 0; s < NSC; ++s) {
-            const int q = k0 + s;
-            if (q < k1) {
-                mbar_expect_tx(&bar[NST + s], CB);
-                tma_load_3d(sC + s * (CBA / sizeof(E)), &tmC, &bar[NST + s], X0, Y0, q);
-            }
-        }
-    }
-    // Stage bookkeeping without divisions: T plane k0-1+i sits in stage i % NST
-    // and Ci plane k0+i in stage i % NSC; bit s of tpar / cpar is the parity of
-    // the next completion of stage s.
+    // Plane q (q = k0-1 .. k1) lives in stage (q - (k0-1)) % NST: its T box, and its Ci
+    // box when it is an output plane, counted on the stage's one mbarrier.
     constexpr unsigned TSTRIDE = TBA / sizeof(E), CSTRIDE = CBA / sizeof(E);
-    unsigned tpar = 0u, cpar = 0u;
-    auto tnext = [](int s) { return s + 1 == NST ? 0 : s + 1; };
-    auto cnext = [](int s) { return s + 1 == NSC ? 0 : s + 1; };
-    auto acquire = [&](uint64_t *b, unsigned &par, int s) -> bool {
-        const unsigned ph = (par >> s) & 1u;
-        par ^= 1u << s;
-        return mbar_wait(b, ph);
+    auto issue = [&](int s, int q) {
+        const bool ci = q >= k0 && q < k1;
+        mbar_expect_tx(&bar[s], TB + (ci ? CB : 0u));
+        tma_load_3d(sT + s * TSTRIDE, &tmT, &bar[s], X0 - HX, Y0 - 1, q);
+        if (ci) tma_load_3d(sC + s * CSTRIDE, &tmC, &bar[s], X0, Y0, q);
     };
-    // After a timed-out wait: bounded waits for the copies of the last planes issued to
-    // each ring (T up to plane qT, Ci up to plane qC), so that no TMA write lands after
-    // the CTA exits.
-    auto drain = [&](int qT, int qC) {
-        for (int q = max(k0 - 1, qT - NST + 1); q <= qT; ++q) {
+    if (threadIdx.x == 0)
+        for (int s = 0; s < NST; ++s)
+            if (k0 - 1 + s <= k1) issue(s, k0 - 1 + s);
+    // bit s of tpar is the parity of the next completion of stage s
+    unsigned tpar = 0u;
+    auto tnext = [](int s) { return s + 1 == NST ? 0 : s + 1; };
+    auto acquire = [&](int s) -> bool {
+        const unsigned ph = (tpar >> s) & 1u;
+        tpar ^= 1u << s;
+        return mbar_wait(&bar[s], ph);
+    };
+    // After a timed-out wait: bounded waits for the copies of the last NST planes issued
+    // (up to plane q_iss), so that no TMA write lands after the CTA exits.
+    auto drain = [&](int q_iss) {
+        for (int q = max(k0 - 1, q_iss - NST + 1); q <= q_iss; ++q) {
             const int i = q - (k0 - 1);
             mbar_wait(&bar[i % NST], (unsigned)(i / NST) & 1u);
-        }
-        for (int q = max(k0, qC - NSC + 1); q <= qC; ++q) {
-            const int i = q - k0;
-            mbar_wait(&bar[NST + i % NSC], (unsigned)(i / NSC) & 1u);
         }
     };
 
     const int row = ty + 1, col = HX + lane * PX;
-    bool ok = acquire(&bar[0], tpar, 0);
+    bool ok = acquire(0);
     V qm = *(const V *)(sT + row * W + col);
-    ok = acquire(&bar[1 % NST], tpar, 1 % NST) && ok;
+    ok = acquire(1 % NST) && ok;
     V qc = *(const V *)(sT + (1 % NST) * TSTRIDE + row * W + col);
     if (!ok) {
         s_abort = 1;
@@ -151,16 +130,10 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
     }
     __syncthreads();
     if (s_abort) {
-        drain(min(k0 - 2 + NST, k1), min(k0 - 1 + NSC, k1 - 1));
+        drain(min(k0 - 2 + NST, k1));
         return;
     }
-    if (threadIdx.x == 0) {
-        const int q = k0 - 1 + NST;
-        if (q <= k1) {  // stage 0 held plane k0-1
-            mbar_expect_tx(&bar[0], TB);
-            tma_load_3d(sT, &tmT, &bar[0], X0 - HX, Y0 - 1, q);
-        }
-    }
+    if (threadIdx.x == 0 && k0 - 1 + NST <= k1) issue(0, k0 - 1 + NST);  // stage 0 held plane k0-1
 
     const int gy = Y0 + ty;
     const int gx0 = X0 + lane * PX;
@@ -168,22 +141,21 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
     bool all_x = gx0 >= 1 && gx0 + PX - 1 <= p.nx - 2;
     E *__restrict__ T2 = (E *)T2v;
     E *__restrict__ comp = (E *)compv;
-    int sk = 1 % NST;  // T stage of plane k
-    int ck = 0;        // Ci stage of plane k
+    int sk = 1 % NST;  // stage of plane k
+    const int64_t plane = p.nx * p.ny;
+    int64_t base = (int64_t)gx0 + p.nx * ((int64_t)gy + p.ny * (int64_t)k0);  // own nodes, plane k
 
-    for (int k = k0; k < k1; ++k) {
+    for (int k = k0; k < k1; ++k, base += plane) {
         const int sk1 = tnext(sk);
-        ok = acquire(&bar[sk1], tpar, sk1);
-        ok = acquire(&bar[NST + ck], cpar, ck) && ok;
+        ok = acquire(sk1);  // plane k+1 (plane k, with its Ci, was acquired before)
         const E *Tk = sT + sk * TSTRIDE;
         const V qn = *(const V *)(sT + sk1 * TSTRIDE + row * W + col);
         const E left = Tk[row * W + col - 1], right = Tk[row * W + col + PX];
         const V up = *(const V *)(Tk + (row - 1) * W + col);
         const V dn = *(const V *)(Tk + (row + 1) * W + col);
-        const V civ = *(const V *)(sC + ck * CSTRIDE + ty * BX + lane * PX);
+        const V civ = *(const V *)(sC + sk * CSTRIDE + ty * BX + lane * PX);
 
         if (row_ok) {
-            const int64_t base = (int64_t)gx0 + p.nx * ((int64_t)gy + p.ny * (int64_t)k);
             V cv{};
             if constexpr (MODE == Z_F32_COMP) {
                 if (all_x) cv = *(const V *)(comp + base);
@@ -319,28 +291,17 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
                 }
             }
         }
-        const int ck1 = cnext(ck);
         if (!ok) {
             s_abort = 1;
             atomicOr(&g_zmarch_error, 1u);
         }
-        __syncthreads();  // every thread is done with plane k's T stage and Ci stage
+        __syncthreads();  // every thread is done with plane k's stage (T and Ci)
         if (s_abort) {
-            drain(min(k - 1 + NST, k1), min(k - 1 + NSC, k1 - 1));
+            drain(min(k - 1 + NST, k1));
             return;
         }
-        if (threadIdx.x == 0) {
-            if (k + NST <= k1) {  // plane k's T stage takes plane k + NST
-                mbar_expect_tx(&bar[sk], TB);
-                tma_load_3d(sT + sk * TSTRIDE, &tmT, &bar[sk], X0 - HX, Y0 - 1, k + NST);
-            }
-            if (k + NSC < k1) {  // plane k's Ci stage takes Ci plane k + NSC
-                mbar_expect_tx(&bar[NST + ck], CB);
-                tma_load_3d(sC + ck * CSTRIDE, &tmC, &bar[NST + ck], X0, Y0, k + NSC);
-            }
-        }
+        if (threadIdx.x == 0 && k + NST <= k1) issue(sk, k + NST);  // plane k's stage
         sk = sk1;
-        ck = ck1;
         qm = qc;
         qc = qn;
     }
@@ -402,18 +363,18 @@ bool zmarch_supported(Grid3 g, int esz, const void *a, const void *b, const void
     return encode_fn() != nullptr;
 }
 
-template <int MODE, int BY, int NST, int NSC>
+template <int MODE, int BY, int NST>
 static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const void *Ci, Grid3 g,
                                    ZParams p, int kchunk, cudaStream_t s) {
     using E = typename ZTraits<MODE>::E;
     constexpr int PX = ZTraits<MODE>::PX, BX = 32 * PX, W = BX + 2 * PX, H = BY + 2;
     constexpr unsigned TBA = (W * H * sizeof(E) + 127) / 128 * 128;
     constexpr unsigned CBA = (BX * BY * sizeof(E) + 127) / 128 * 128;
-    constexpr size_t smem = NST * TBA + NSC * CBA + (NST + NSC) * 8;
+    constexpr size_t smem = NST * (TBA + CBA) + NST * 8;
     static bool attr_done[64] = {false};
     const int dev = current_device();
     if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_zmarch<MODE, BY, NST, NSC>,
+        cudaError_t e = cudaFuncSetAttribute(k_zmarch<MODE, BY, NST>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
@@ -442,7 +403,7 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const vo
     p.nz = g.nz;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    k_zmarch<MODE, BY, NST, NSC><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
+    k_zmarch<MODE, BY, NST><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
         mT, mC, T2, comp, p);
     return cudaGetLastError();
 }
@@ -478,23 +439,23 @@ cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const v
     switch (mode) {
         case Z_F64_EMU_ISO:
         case Z_F64_EMU_ANISO:
-            if (!positive) return launch_zmarch_t<Z_F64_NATIVE, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            if (!positive) return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
             if (mode == Z_F64_EMU_ISO) {
                 if (dmul)
-                    return launch_zmarch_t<Z_F64_EMU_ISO_DMUL, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+                    return launch_zmarch_t<Z_F64_EMU_ISO_DMUL, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
                 if (by16)
-                    return launch_zmarch_t<Z_F64_EMU_ISO, 16, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
-                return launch_zmarch_t<Z_F64_EMU_ISO, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+                    return launch_zmarch_t<Z_F64_EMU_ISO, 16, 4>(T2, T, comp, Ci, g, p, kchunk, s);
+                return launch_zmarch_t<Z_F64_EMU_ISO, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
             }
-            return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F64_NATIVE:
-            return launch_zmarch_t<Z_F64_NATIVE, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F64_SCALED:
-            return launch_zmarch_t<Z_F64_SCALED, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F64_SCALED, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F32:
-            return launch_zmarch_t<Z_F32, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F32, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
         case Z_F32_COMP:
-            return launch_zmarch_t<Z_F32_COMP, 8, 4, 3>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F32_COMP, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
     }
     return cudaErrorInvalidValue;
 }
