@@ -233,7 +233,8 @@ const char *ps_last_error(void) { return g_err.c_str(); }
 int ps_device_error(unsigned *out_host, int clear) {
     if (!out_host) return fail(PS_ERR_ARG, "out_host is NULL");
     *out_host = zmarch_device_error(clear != 0) | adjoint_device_error(clear != 0) |
-                adjoint_scaled_device_error(clear != 0) | zmarch2_device_error(clear != 0);
+                adjoint_scaled_device_error(clear != 0) | zmarch2_device_error(clear != 0) |
+                adjoint_f32_device_error(clear != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ps_device_error");
     return PS_OK;

@@ -148,8 +148,10 @@ cudaError_t launch_adjoint_f64_scaled(double *Tbar, double *Csbar, const double 
 
 cudaError_t launch_adjoint_f32(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                const float *Ci, StepCoef c, Grid3 g, cudaStream_t s) {
-    if (use_tma(g, 4, Tbar, Cibar, ybar, T, Ci))
-        return launch_adjoint_zmarch<float>(Tbar, Cibar, ybar, T, Ci, c, g, s);
+    const void *ptrs[5] = {T, ybar, Ci, Cibar, Tbar};
+    const char *v = getenv("PS_ADJ_PLAIN");
+    if (!(v && v[0] == '1') && adjoint_f32_supported(g, ptrs, 5))
+        return launch_adjoint_f32_tma(Tbar, Cibar, ybar, T, Ci, c, g, s);
     return launch_adjoint_basic<float>(
         Tbar, Cibar, ybar, T, Ci,
         CoefT<float>{(float)c.dtlam, (float)c.ax, (float)c.ay, (float)c.az}, g, s);

@@ -1,4 +1,4 @@
-// Transposed step (adjoint) as a TMA-fed z-march.
+// FP64 transposed step (adjoint) on Ci as given, as a TMA-fed z-march.
 //
 // For ybar = dL/dT_{t+1} and the state T = T_t the forward step read:
 //   w[q]      = Ci[q]*ybar[q] at interior q, 0 elsewhere (and outside the grid),
@@ -22,7 +22,6 @@
 #include <cudaTypedefs.h>
 
 #include <cstdlib>
-#include <type_traits>
 
 #include "emu64.cuh"
 #include "internal.h"
@@ -37,7 +36,6 @@ struct AdjParams {
     int64_t nx, ny, nz;
     int kchunk, ntx;
     double Kx, Ky, Kz;  // dt*lam*_d^2
-    float fKx, fKy, fKz;
 };
 
 template <typename E>
@@ -46,11 +44,6 @@ template <>
 struct ATraits<double> {
     using V = double2;
     static constexpr int PX = 2;
-};
-template <>
-struct ATraits<float> {
-    using V = float4;
-    static constexpr int PX = 4;
 };
 
 template <typename V, typename E>
@@ -64,10 +57,10 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
                  const __grid_constant__ CUtensorMap tmC, E *__restrict__ Tbar,
                  E *__restrict__ Cibar, const AdjParams p) {
     using V = typename ATraits<E>::V;
-    // w tiles: FP64 holds w in 64-bit fixed point at a CTA-uniform scale, FP32 holds floats
-    constexpr bool kFix = sizeof(E) == 8;
-    using WT = std::conditional_t<kFix, long long, E>;
-    using WV = std::conditional_t<kFix, longlong2, V>;
+    static_assert(sizeof(E) == 8, "FP64 only (the FP32 transposed step is k_adjoint_f32)");
+    // w tiles hold w in 64-bit fixed point at a CTA-uniform scale
+    using WT = long long;
+    using WV = longlong2;
     constexpr int PX = ATraits<E>::PX, HX = PX, BX = 32 * PX, W = BX + 2 * HX, H = BY + 2;
     constexpr int NTH = 32 * BY, NV = (W * H + NTH - 1) / NTH;  // tile values per thread
     constexpr unsigned TB = W * H * sizeof(E);
@@ -135,7 +128,7 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
             if (idx < W * H) {
                 const int r = idx / W, c = idx - r * W;
                 wv[v] = wval(Ys, Cs, r, c, q);
-                if constexpr (kFix) em = max(em, emu_exp(dbits(wv[v])));
+                em = max(em, emu_exp(dbits(wv[v])));
             }
         }
         return em;
@@ -145,32 +138,29 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
         for (int v = 0; v < NV; ++v) {
             const int idx = threadIdx.x + v * NTH;
             if (idx < W * H) {
-                if constexpr (kFix) wt[idx] = emu_fixed(dbits(wv[v]), Esc);
-                else wt[idx] = wv[v];
+                wt[idx] = emu_fixed(dbits(wv[v]), Esc);
             }
         }
     };
-    // FP64: agree on the CTA's scale (contains a __syncthreads); entries this thread
+    // agree on the CTA's scale (contains a __syncthreads); entries this thread
     // stored earlier and its register queue are shifted down when the scale grows
     auto agree = [&](int em_local, WT *older, WT (&wreg)[PX]) {
-        if constexpr (kFix) {
-            const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)em_local);
-            if (lane == 0) s_emax[ty] = (int)m;
-            __syncthreads();
-            int e = Esc;
+        const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)em_local);
+        if (lane == 0) s_emax[ty] = (int)m;
+        __syncthreads();
+        int e = Esc;
 #pragma unroll
-            for (int w = 0; w < BY; ++w) e = max(e, s_emax[w]);
-            if (e > Esc) {
-                const int d = e - Esc;
+        for (int w = 0; w < BY; ++w) e = max(e, s_emax[w]);
+        if (e > Esc) {
+            const int d = e - Esc;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const int idx = threadIdx.x + v * NTH;
-                    if (idx < W * H) older[idx] = d >= 64 ? 0 : (older[idx] >> d);
-                }
-#pragma unroll
-                for (int i = 0; i < PX; ++i) wreg[i] = d >= 64 ? 0 : (wreg[i] >> d);
-                Esc = e;
+            for (int v = 0; v < NV; ++v) {
+                const int idx = threadIdx.x + v * NTH;
+                if (idx < W * H) older[idx] = d >= 64 ? 0 : (older[idx] >> d);
             }
+#pragma unroll
+            for (int i = 0; i < PX; ++i) wreg[i] = d >= 64 ? 0 : (wreg[i] >> d);
+            Esc = e;
         }
     };
 
@@ -185,7 +175,7 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
         wm0[i] = wval(ring + (3 * s_m + 1) * SS, ring + (3 * s_m + 2) * SS, row, col + i, k0 - 1);
-        if constexpr (kFix) em0 = max(em0, emu_exp(dbits(wm0[i])));
+        em0 = max(em0, emu_exp(dbits(wm0[i])));
     }
     ok = acquire(s_c) && ok;
     V tc = *(const V *)(ring + (3 * s_c) * SS + row * W + col);
@@ -200,8 +190,7 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
         w_store(wtile + wcur * SS, wv);
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
-            if constexpr (kFix) wm[i] = emu_fixed(dbits(wm0[i]), Esc);
-            else wm[i] = wm0[i];
+            wm[i] = emu_fixed(dbits(wm0[i]), Esc);
         }
     }
     if (!ok) {
@@ -267,114 +256,90 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
                     }
                 }
             }
-            if constexpr (sizeof(E) == 8) {
-                // ---- Tbar: exact fixed-point w-stencil sums, one DFMA per coefficient
+            // ---- Tbar: exact fixed-point w-stencil sums, one DFMA per coefficient
+#pragma unroll
+            for (int i = 0; i < PX; ++i) {
+                const long long c2 = 2 * aget<WV, WT>(wc, i);
+                const long long xm = i == 0 ? wl : aget<WV, WT>(wc, i - 1);
+                const long long xp = i == PX - 1 ? wr : aget<WV, WT>(wc, i + 1);
+                const long long sx = xm + xp - c2;
+                const long long sy = aget<WV, WT>(wu, i) + aget<WV, WT>(wd, i) - c2;
+                const long long sz = wm[i] + aget<WV, WT>(wp, i) - c2;
+                const double yb = aget<V, E>(yc, i);
+                // a non-finite w anywhere in this CTA's march: report NaN, not garbage
+                reinterpret_cast<E *>(&tb)[i] =
+                    Esc == 0x7ff ? __longlong_as_double(0x7ff8000000000000ll)
+                                 : emu_axpy3<kIso>(yb, sx, sy, sz, Esc - 1079, p.Kx, p.Ky, p.Kz);
+            }
+            // ---- Cibar: T-Laplacian, same-binade fast path when the whole warp allows it
+            if (do_ci) {
+                unsigned long long c[PX], xm[PX], xp[PX], ym[PX], yp[PX], zm[PX], zp[PX];
 #pragma unroll
                 for (int i = 0; i < PX; ++i) {
-                    const long long c2 = 2 * aget<WV, WT>(wc, i);
-                    const long long xm = i == 0 ? wl : aget<WV, WT>(wc, i - 1);
-                    const long long xp = i == PX - 1 ? wr : aget<WV, WT>(wc, i + 1);
-                    const long long sx = xm + xp - c2;
-                    const long long sy = aget<WV, WT>(wu, i) + aget<WV, WT>(wd, i) - c2;
-                    const long long sz = wm[i] + aget<WV, WT>(wp, i) - c2;
-                    const double yb = aget<V, E>(yc, i);
-                    // a non-finite w anywhere in this CTA's march: report NaN, not garbage
-                    reinterpret_cast<E *>(&tb)[i] =
-                        Esc == 0x7ff ? __longlong_as_double(0x7ff8000000000000ll)
-                                     : emu_axpy3<kIso>(yb, sx, sy, sz, Esc - 1079, p.Kx, p.Ky, p.Kz);
+                    c[i] = dbits(aget<V, E>(tc, i));
+                    xm[i] = dbits(i == 0 ? tl : aget<V, E>(tc, i - 1));
+                    xp[i] = dbits(i == PX - 1 ? tr : aget<V, E>(tc, i + 1));
+                    ym[i] = dbits(aget<V, E>(tu, i));
+                    yp[i] = dbits(aget<V, E>(td, i));
+                    zm[i] = dbits(aget<V, E>(tm, i));
+                    zp[i] = dbits(aget<V, E>(tp, i));
                 }
-                // ---- Cibar: T-Laplacian, same-binade fast path when the whole warp allows it
-                if (do_ci) {
-                    unsigned long long c[PX], xm[PX], xp[PX], ym[PX], yp[PX], zm[PX], zp[PX];
+                const unsigned hc = (unsigned)(c[0] >> 32);
+                unsigned hw[5 * PX + 1];
+                hw[0] = (unsigned)(xm[0] >> 32);
+                hw[1] = (unsigned)(xp[PX - 1] >> 32);
 #pragma unroll
-                    for (int i = 0; i < PX; ++i) {
-                        c[i] = dbits(aget<V, E>(tc, i));
-                        xm[i] = dbits(i == 0 ? tl : aget<V, E>(tc, i - 1));
-                        xp[i] = dbits(i == PX - 1 ? tr : aget<V, E>(tc, i + 1));
-                        ym[i] = dbits(aget<V, E>(tu, i));
-                        yp[i] = dbits(aget<V, E>(td, i));
-                        zm[i] = dbits(aget<V, E>(tm, i));
-                        zp[i] = dbits(aget<V, E>(tp, i));
-                    }
-                    const unsigned hc = (unsigned)(c[0] >> 32);
-                    unsigned hw[5 * PX + 1];
-                    hw[0] = (unsigned)(xm[0] >> 32);
-                    hw[1] = (unsigned)(xp[PX - 1] >> 32);
+                for (int i = 0; i < PX; ++i) {
+                    hw[2 + 4 * i] = (unsigned)(ym[i] >> 32);
+                    hw[3 + 4 * i] = (unsigned)(yp[i] >> 32);
+                    hw[4 + 4 * i] = (unsigned)(zm[i] >> 32);
+                    hw[5 + 4 * i] = (unsigned)(zp[i] >> 32);
+                }
 #pragma unroll
-                    for (int i = 0; i < PX; ++i) {
-                        hw[2 + 4 * i] = (unsigned)(ym[i] >> 32);
-                        hw[3 + 4 * i] = (unsigned)(yp[i] >> 32);
-                        hw[4 + 4 * i] = (unsigned)(zm[i] >> 32);
-                        hw[5 + 4 * i] = (unsigned)(zp[i] >> 32);
-                    }
+                for (int i = 1; i < PX; ++i) hw[1 + 4 * PX + i] = (unsigned)(c[i] >> 32);
+                bool use[PX];
 #pragma unroll
-                    for (int i = 1; i < PX; ++i) hw[1 + 4 * PX + i] = (unsigned)(c[i] >> 32);
-                    bool use[PX];
+                for (int i = 0; i < PX; ++i) use[i] = gx0 + i >= 1 && gx0 + i <= nx - 2;
+                if (!all_in) {  // unstored edge nodes must not force the general path
+                    if (!use[0]) hw[0] = hc;
+                    if (!use[PX - 1]) hw[1] = hc;
 #pragma unroll
-                    for (int i = 0; i < PX; ++i) use[i] = gx0 + i >= 1 && gx0 + i <= nx - 2;
-                    if (!all_in) {  // unstored edge nodes must not force the general path
-                        if (!use[0]) hw[0] = hc;
-                        if (!use[PX - 1]) hw[1] = hc;
+                    for (int i = 0; i < PX; ++i)
+                        if (!use[i]) hw[2 + 4 * i] = hw[3 + 4 * i] = hw[4 + 4 * i] = hw[5 + 4 * i] = hc;
 #pragma unroll
-                        for (int i = 0; i < PX; ++i)
-                            if (!use[i]) hw[2 + 4 * i] = hw[3 + 4 * i] = hw[4 + 4 * i] = hw[5 + 4 * i] = hc;
+                    for (int i = 1; i < PX; ++i)
+                        if (!(use[i] || use[i - 1] || (i + 1 < PX && use[i + 1]))) hw[1 + 4 * PX + i] = hc;
+                }
+                const bool fast = emu_same_binade_hi(hw, hc);
+                const bool wfast = __all_sync(0xffffffffu, fast);
 #pragma unroll
-                        for (int i = 1; i < PX; ++i)
-                            if (!(use[i] || use[i - 1] || (i + 1 < PX && use[i + 1]))) hw[1 + 4 * PX + i] = hc;
-                    }
-                    const bool fast = emu_same_binade_hi(hw, hc);
-                    const bool wfast = __all_sync(0xffffffffu, fast);
-#pragma unroll
-                    for (int i = 0; i < PX; ++i) {
-                        long long sx, sy, sz;
-                        int sc;
-                        double L;
-                        if (wfast || fast) {
-                            const unsigned long long c2 = c[i] + c[i];
-                            sx = (long long)(xm[i] + xp[i] - c2);
-                            sy = (long long)(ym[i] + yp[i] - c2);
-                            sz = (long long)(zm[i] + zp[i] - c2);
-                            if (c[i] >> 63) {
-                                sx = -sx;
-                                sy = -sy;
-                                sz = -sz;
-                            }
-                            const int e = emu_exp(c[i]);
-                            sc = (e ? e : 1) - 1075;
-                            L = emu_axpy3<kIso>(0.0, sx, sy, sz, sc, p.Kx, p.Ky, p.Kz);
-                        } else if (emu_sums_general(c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i],
-                                                    sx, sy, sz, sc)) {
-                            L = emu_axpy3<kIso>(0.0, sx, sy, sz, sc, p.Kx, p.Ky, p.Kz);
-                        } else {
-                            const double cc = bitsd(c[i]);
-                            L = (p.Kx * ((bitsd(xm[i]) - cc) - (cc - bitsd(xp[i]))) +
-                                 p.Ky * ((bitsd(ym[i]) - cc) - (cc - bitsd(yp[i])))) +
-                                p.Kz * ((bitsd(zm[i]) - cc) - (cc - bitsd(zp[i])));
+                for (int i = 0; i < PX; ++i) {
+                    long long sx, sy, sz;
+                    int sc;
+                    double L;
+                    if (wfast || fast) {
+                        const unsigned long long c2 = c[i] + c[i];
+                        sx = (long long)(xm[i] + xp[i] - c2);
+                        sy = (long long)(ym[i] + yp[i] - c2);
+                        sz = (long long)(zm[i] + zp[i] - c2);
+                        if (c[i] >> 63) {
+                            sx = -sx;
+                            sy = -sy;
+                            sz = -sz;
                         }
-                        reinterpret_cast<E *>(&cb)[i] = fma(aget<V, E>(yc, i), L, aget<V, E>(cb, i));
+                        const int e = emu_exp(c[i]);
+                        sc = (e ? e : 1) - 1075;
+                        L = emu_axpy3<kIso>(0.0, sx, sy, sz, sc, p.Kx, p.Ky, p.Kz);
+                    } else if (emu_sums_general(c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i],
+                                                sx, sy, sz, sc)) {
+                        L = emu_axpy3<kIso>(0.0, sx, sy, sz, sc, p.Kx, p.Ky, p.Kz);
+                    } else {
+                        const double cc = bitsd(c[i]);
+                        L = (p.Kx * ((bitsd(xm[i]) - cc) - (cc - bitsd(xp[i]))) +
+                             p.Ky * ((bitsd(ym[i]) - cc) - (cc - bitsd(yp[i])))) +
+                            p.Kz * ((bitsd(zm[i]) - cc) - (cc - bitsd(zp[i])));
                     }
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < PX; ++i) {
-                    const E c = aget<V, E>(wc, i);
-                    const E xm = i == 0 ? wl : aget<V, E>(wc, i - 1);
-                    const E xp = i == PX - 1 ? wr : aget<V, E>(wc, i + 1);
-                    const E d2x = (xp - c) - (c - xm);
-                    const E d2y = (aget<V, E>(wd, i) - c) - (c - aget<V, E>(wu, i));
-                    const E d2z = (aget<V, E>(wp, i) - c) - (c - wm[i]);
-                    reinterpret_cast<E *>(&tb)[i] =
-                        aget<V, E>(yc, i) + ((d2x * p.fKx + d2y * p.fKy) + d2z * p.fKz);
-                    if (do_ci) {
-                        const E t = aget<V, E>(tc, i);
-                        const E txm = i == 0 ? tl : aget<V, E>(tc, i - 1);
-                        const E txp = i == PX - 1 ? tr : aget<V, E>(tc, i + 1);
-                        const E t2x = (txp - t) - (t - txm);
-                        const E t2y = (aget<V, E>(td, i) - t) - (t - aget<V, E>(tu, i));
-                        const E t2z = (aget<V, E>(tp, i) - t) - (t - aget<V, E>(tm, i));
-                        const E L = (t2x * p.fKx + t2y * p.fKy) + t2z * p.fKz;
-                        reinterpret_cast<E *>(&cb)[i] = aget<V, E>(cb, i) + aget<V, E>(yc, i) * L;
-                    }
+                    reinterpret_cast<E *>(&cb)[i] = fma(aget<V, E>(yc, i), L, aget<V, E>(cb, i));
                 }
             }
             if (all_x) {
@@ -460,9 +425,6 @@ cudaError_t launch_adjoint_zmarch(E *Tbar, E *Cibar, const E *ybar, const E *T, 
     p.Kx = c.dtlam * c.ax;
     p.Ky = c.dtlam * c.ay;
     p.Kz = c.dtlam * c.az;
-    p.fKx = (float)p.Kx;
-    p.fKy = (float)p.Ky;
-    p.fKz = (float)p.Kz;
     const char *v = getenv("PS_ADJ_KCHUNK");
     const int kchunk = v ? atoi(v) : 0;
     const bool iso = c.ax == c.ay && c.ay == c.az;
@@ -472,8 +434,6 @@ cudaError_t launch_adjoint_zmarch(E *Tbar, E *Cibar, const E *ybar, const E *T, 
 
 template cudaError_t launch_adjoint_zmarch<double>(double *, double *, const double *, const double *,
                                                    const double *, StepCoef, Grid3, cudaStream_t);
-template cudaError_t launch_adjoint_zmarch<float>(float *, float *, const float *, const float *,
-                                                  const float *, StepCoef, Grid3, cudaStream_t);
 
 unsigned adjoint_device_error(bool clear) {
     unsigned v = 0;

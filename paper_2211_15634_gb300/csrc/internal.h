@@ -59,6 +59,11 @@ unsigned zmarch_device_error(bool clear);
 cudaError_t launch_selftest_wait(unsigned polls, unsigned ns, cudaStream_t s);
 unsigned adjoint_device_error(bool clear);
 unsigned adjoint_scaled_device_error(bool clear);
+// FP32 transposed step, every read staged by TMA (adjoint_f32.cu).
+bool adjoint_f32_supported(Grid3 g, const void *const *ptrs, int nptr);
+cudaError_t launch_adjoint_f32_tma(float *Tbar, float *Cibar, const float *ybar, const float *T,
+                                   const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
+unsigned adjoint_f32_device_error(bool clear);
 
 // ---- helpers (misc.cu) ----
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);
