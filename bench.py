@@ -58,7 +58,9 @@ def parse_args():
     p.add_argument("--temporal2", action="store_true",
                    help="kernel loop step: fused step pairs (each rep is two two-step passes)")
     p.add_argument("--plain-ci", action="store_true",
-                   help="kernel loop: FP64 step/adjoint on Ci as given instead of the pre-scaled field")
+                   help="kernel loop: FP64 step/adjoint/batch on Ci as given instead of the pre-scaled field")
+    p.add_argument("--batch-kernel", choices=["zmarch", "column"], default="zmarch",
+                   help="kernel loop batch: the TMA z-march on padded rows, or the column march")
     return p.parse_args()
 
 
@@ -105,8 +107,12 @@ def run_kernel_loop(args):
     return 0
 
 
-def batch_workload(torch, api, inputs, dtype, dev, count=256):
-    """The batched workload: problem q is an n_q^3 grid, n_q uniform in 32..160."""
+def batch_workload(torch, api, inputs, dtype, dev, count=256, pitched=False, ci_scaled=False):
+    """The batched workload: problem q is an n_q^3 grid, n_q uniform in 32..160.
+
+    ``pitched``: fields with rows padded to 16 bytes (the z-march batch's layout);
+    ``ci_scaled`` (FP64): each Ci field holds the pre-scaled dt*lam*_dx^2*Ci.
+    Returns the problems and the algorithmic bytes of one step (3 n^3 per problem)."""
     probs, nbytes = [], 0
     esz = 8 if dtype == torch.float64 else 4
     for q, nq in enumerate(inputs.batch_sizes(256)[:count]):
@@ -118,8 +124,13 @@ def batch_workload(torch, api, inputs, dtype, dev, count=256):
             Tq = api.to_deviation(Tq, 1.7)
             Cq = api.to_f32(Cq)
         dtq = api.stable_dt(Cq, 1.0)
-        probs.append(dict(T=Tq, T2=Tq.clone(), Ci=Cq, lam=1.0, dt=dtq,
-                          inv_spacing=inputs.inverse_spacing(nq, nq, nq)))
+        inv = inputs.inverse_spacing(nq, nq, nq)
+        if ci_scaled:
+            Cq = api.scale_ci(Cq, 1.0, dtq, inv)
+        if pitched:
+            Tq, Cq = api.pitched_copy(Tq), api.pitched_copy(Cq)
+        T2q = api.pitched_copy(Tq) if pitched else Tq.clone()
+        probs.append(dict(T=Tq, T2=T2q, Ci=Cq, lam=1.0, dt=dtq, inv_spacing=inv))
         nbytes += 3 * nq ** 3 * esz
     return probs, nbytes
 
@@ -128,13 +139,18 @@ def run_batch_loop(args):
     import torch
     from paper_2211_15634_gb300 import api, inputs
     dtype = torch.float64 if args.dtype == "f64" else torch.float32
-    probs, nbytes = batch_workload(torch, api, inputs, dtype, torch.device("cuda"), args.batch_count)
-    b = api.Batch(probs)
+    zm = args.batch_kernel == "zmarch"
+    scaled = zm and dtype == torch.float64 and not args.plain_ci
+    probs, nbytes = batch_workload(torch, api, inputs, dtype, torch.device("cuda"), args.batch_count,
+                                   pitched=zm, ci_scaled=scaled)
+    b = api.Batch(probs, kernel=args.batch_kernel, ci_scaled=scaled)
     for it in range(args.reps):
         b.step(it & 1)
     torch.cuda.synchronize()
-    log(f"kernel loop done: k_batch_step x{args.reps}, {len(probs)} problems, {nbytes / 1e9:.2f} GB "
-        f"per step, {args.dtype}, device_error={api.device_error()}")
+    name = "k_batch_zmarch" if zm else "k_batch_step"
+    log(f"kernel loop done: {name} x{args.reps}, {len(probs)} problems, {b.nitems} items, "
+        f"{nbytes / 1e9:.2f} GB per step, {args.dtype}{' pre-scaled' if scaled else ''}, "
+        f"device_error={api.device_error()}")
     return 0
 
 
@@ -535,22 +551,33 @@ def secondary_metrics(torch, api, ag, inputs, log):
         api.clear_graph_cache()
         torch.cuda.empty_cache()
 
-    # batched workload: 256 problems, n_p uniform in {32..160}, nt = 500
+    # batched workload: 256 problems, n_p uniform in {32..160}, nt = 500, one launch
+    # per step (graph-captured): the TMA z-march on padded rows (tuned z-chunks; FP64 on
+    # Ci as given and on the pre-scaled coefficient), the column march on contiguous
+    # fields, and one launch per problem
+    from paper_2211_15634_gb300 import tuner
     sizes = inputs.batch_sizes(256)
     nt = 500
     for name, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
+        variants = [("", False)] + ([("_ci_scaled", True)] if dtype == torch.float64 else [])
+        for tag, scaled in variants:
+            probs, bytes_per_step = batch_workload(torch, api, inputs, dtype, dev, len(sizes),
+                                                   pitched=True, ci_scaled=scaled)
+            best = tuner.tune(probs, kernel="zmarch", ci_scaled=scaled)  # per size class, cached
+            b = tuner.tuned_batch(probs, kernel="zmarch", ci_scaled=scaled)
+            t_b = timed(lambda: b.run(nt, graph=True), reps=2)
+            out[f"batch_{name}{tag}_teff_gbs"] = round(bytes_per_step * nt / t_b / 1e9, 1)
+            out[f"batch_{name}{tag}_tiles"] = {f"{lo}-{hi}": list(t)[2] for (lo, hi), t in sorted(best.items())}
+            del probs, b
+            api.clear_graph_cache()
+            torch.cuda.empty_cache()
+
         probs, bytes_per_step = batch_workload(torch, api, inputs, dtype, dev, len(sizes))
-        from paper_2211_15634_gb300 import tuner
-        b0 = api.Batch(probs)  # library default tile for every problem
+        b0 = api.Batch(probs, kernel="column")  # library default tile for every problem
         t_0 = timed(lambda: b0.run(nt, graph=True), reps=1)
-        out[f"batch_{name}_default_tile_teff_gbs"] = round(bytes_per_step * nt / t_0 / 1e9, 1)
+        out[f"batch_{name}_column_teff_gbs"] = round(bytes_per_step * nt / t_0 / 1e9, 1)
         del b0
         api.clear_graph_cache()
-        best = tuner.tune(probs)  # per size class, cached as JSON
-        b = tuner.tuned_batch(probs)
-        t_b = timed(lambda: b.run(nt, graph=True), reps=2)
-        out[f"batch_{name}_teff_gbs"] = round(bytes_per_step * nt / t_b / 1e9, 1)
-        out[f"batch_{name}_tiles"] = {f"{lo}-{hi}": list(t) for (lo, hi), t in sorted(best.items())}
 
         # one launch per problem, problem-major: each problem's nt steps in a row
         # (its fields stay in the 129 MB L2 across its own steps)
@@ -569,7 +596,7 @@ def secondary_metrics(torch, api, ag, inputs, log):
                     api.step(dst, src, p["Ci"], 1.0, p["dt"], p["inv_spacing"])
         t_s = timed(per_problem_stepwise, reps=1)
         out[f"batch_{name}_per_problem_stepwise_teff_gbs"] = round(bytes_per_step * 50 / t_s / 1e9, 1)
-        del probs, b
+        del probs
         api.clear_graph_cache()
         torch.cuda.empty_cache()
     return out

@@ -89,7 +89,8 @@ size_t ps_workspace_bytes(void);
 
 /* Device-side error flags of the current device, to *out_host (host
  * unsigned): bit 0 = a pipelined kernel gave up waiting for a shared-memory
- * stage (bounded wait) and left without writing its remaining output.  With
+ * stage (bounded wait) and left without writing its remaining output; bit 1 =
+ * the column-march batch kernel was given a z-march table.  With
  * clear != 0 the flags are reset.  Synchronizes the device. */
 int ps_device_error(unsigned *out_host, int clear);
 
@@ -279,39 +280,82 @@ int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *
 
 /* ---------------------------------------------------------------------
  * Batched step: many independent problems of different sizes, one launch
- * per step.  The host describes each problem with a ps_problem; the
- * library lays them out in a device table (problem records followed by a
- * static work list of (problem, x-y tile, z-chunk) items) that the caller
- * copies to device memory once.  A step processes every work item of the
- * table; `parity` 0 reads T and writes T2, parity 1 reads T2 and writes T
- * (so parity = step index & 1 reproduces the swap of Fig. 1's loop).
+ * per step (configs: many problems stepped together; Fig. 1's step per
+ * problem).  The host describes each problem with a ps_problem; the
+ * library lays them out in a table (problem records followed by a static
+ * work list of (problem, x-y tile, z-chunk) items) that the caller copies
+ * to device memory once.  A step processes every work item of the table;
+ * `parity` 0 reads T and writes T2, parity 1 reads T2 and writes T (so
+ * parity = step index & 1 reproduces the swap of Fig. 1's loop).
+ *
+ * Two kernels serve a table:
+ *  - the column march (PS_BATCH_COLUMN): one thread per interior (i, j)
+ *    column of a tile_x x tile_y x tile_z item, neighbours through the
+ *    caches; any sizes and pitches;
+ *  - the TMA z-march (PS_BATCH_ZMARCH): one CTA per item, the x-y tile of
+ *    the single-grid step kernel (64 x 8 nodes FP64, 128 x 8 FP32, boundary
+ *    included) and tile_z planes, staged by TMA, with the single-grid step's
+ *    arithmetic (a problem's result equals its single run's bit for bit).
+ *    Needs rows that start on 16-byte boundaries (pitch * element size a
+ *    multiple of 16; see `pitch`), the CUDA driver's tensor-map encoder, and
+ *    for FP64 equal spacings with dt*lam*_dx^2 > 0 (or PS_BATCH_CI_SCALED).
+ *    tile_x and tile_y do not apply.
+ * Flags 0 pick the z-march when every problem qualifies, else the column
+ * march.  The z-march table embeds tensor maps of the fields: rebuild the
+ * table when a field moves.
  * ------------------------------------------------------------------- */
 typedef struct {
-    void *T;          /* device field, nx*ny*nz of dtype */
-    void *T2;         /* device field, same size, boundary equal to T's */
-    const void *Ci;   /* device field */
+    void *T;          /* device field, nx*ny*nz of dtype, rows `pitch` apart */
+    void *T2;         /* device field, same size and pitch, boundary equal to T's */
+    const void *Ci;   /* device field, same size and pitch */
     double lam, dt, _dx, _dy, _dz;
     int64_t nx, ny, nz;
     int32_t tile_x, tile_y, tile_z; /* this problem's work-item shape; 0 = the call's */
-    int32_t reserved;               /* set to 0 */
+    int32_t pitch;    /* elements from one row (fixed y, z) to the next, >= nx; planes are
+                         pitch*ny apart; 0 = nx (contiguous fields) */
 } ps_problem;
 
-/* Bytes of the table for these problems with the given tile shape
- * (tile_x, tile_y: interior nodes per work item in x and y, tile_x*tile_y
- * <= 4096; tile_z: nodes per z-chunk; 0 picks the library default for the
- * dtype; a problem's own nonzero tile fields override these). */
-size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
-                            int tile_z);
-/* Fill host_buf (bytes >= ps_batch_table_bytes) with the table.  Checks
- * every problem like ps_diffusion3d_step.  *nitems_out = work items. */
-int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, int nprob,
-                        int dtype, int tile_x, int tile_y, int tile_z, int64_t *nitems_out);
+#define PS_BATCH_COLUMN 1u     /* the column march */
+#define PS_BATCH_ZMARCH 2u     /* the TMA z-march; PS_ERR_UNSUPPORTED if a problem cannot take it */
+#define PS_BATCH_CI_SCALED 4u  /* PS_F64, z-march, equal spacings: each Ci holds the pre-scaled
+                                  dt*lam*_dx^2*Ci (see ps_diffusion3d_scale_ci); one FP64
+                                  multiply-add per node */
+
+/* Bytes of the table for these problems, tile shape and flags (tile_x,
+ * tile_y: interior nodes per column-march item in x and y, tile_x*tile_y
+ * <= 4096; tile_z: planes per item; 0 picks the library default for the
+ * dtype and kernel (z-march: 64 planes); a problem's own nonzero tile
+ * fields override these).  0 when an
+ * argument is invalid (ps_batch_table_fill_ex reports why). */
+size_t ps_batch_table_bytes_ex(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
+                               int tile_z, unsigned flags);
+/* Fill host_buf (bytes >= ps_batch_table_bytes_ex, 64-byte aligned) with the
+ * table.  Checks every problem like ps_diffusion3d_step, over its pitch.
+ * *nitems_out = work items. */
+int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs, int nprob,
+                           int dtype, int tile_x, int tile_y, int tile_z, unsigned flags,
+                           int64_t *nitems_out);
+/* Kernel of a filled table: 0 column march, 1 z-march. */
+int ps_batch_table_kernel(const void *host_table);
 /* One step of every problem in the device table (dev_table = device copy
- * of the filled host buffer). */
-int ps_diffusion3d_batch_step(const void *dev_table, int parity, int dtype, void *stream);
+ * of the filled host buffer host_table, which the call reads on the host). */
+int ps_diffusion3d_batch_step_ex(const void *dev_table, const void *host_table, int parity,
+                                 void *stream);
 /* nt batched steps with parity 0, 1, 0, ... (the buffers of problem p hold
  * its final state in T2 when nt is odd, in T when even).  Flags: PS_RUN_GRAPH
- * captures the nt launches once per (table, nt, dtype) and replays them. */
+ * captures the nt launches once per (table address, item count, kernel, nt,
+ * dtype) and replays them. */
+int ps_diffusion3d_batch_run_ex(const void *dev_table, const void *host_table, int nt,
+                                unsigned flags, void *stream);
+
+/* Column-march forms: the _ex calls with flags PS_BATCH_COLUMN; step and run
+ * take only a column-march table (a z-march table makes them set bit 1 of
+ * ps_device_error and leave the fields unchanged). */
+size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
+                            int tile_z);
+int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, int nprob,
+                        int dtype, int tile_x, int tile_y, int tile_z, int64_t *nitems_out);
+int ps_diffusion3d_batch_step(const void *dev_table, int parity, int dtype, void *stream);
 int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned flags,
                              void *stream);
 

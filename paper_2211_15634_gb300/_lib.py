@@ -25,6 +25,9 @@ PS_RUN_COMPENSATED = 2
 PS_RUN_NATIVE_F64 = 4
 PS_RUN_CI_SCALED = 8
 PS_RUN_TEMPORAL2 = 16
+PS_BATCH_COLUMN = 1
+PS_BATCH_ZMARCH = 2
+PS_BATCH_CI_SCALED = 4
 
 STATUS_NAMES = {0: "PS_OK", -1: "PS_ERR_ARG", -2: "PS_ERR_ALIAS", -3: "PS_ERR_ALIGN",
                 -4: "PS_ERR_CUDA", -5: "PS_ERR_UNSUPPORTED"}
@@ -41,7 +44,7 @@ class PsProblem(ctypes.Structure):
                 ("lam", ctypes.c_double), ("dt", ctypes.c_double), ("_dx", ctypes.c_double),
                 ("_dy", ctypes.c_double), ("_dz", ctypes.c_double), ("nx", ctypes.c_int64),
                 ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("tile_x", ctypes.c_int32),
-                ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("pitch", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes)
@@ -85,6 +88,12 @@ SIGNATURES = {
                                  ctypes.POINTER(_I64)]),
     "ps_diffusion3d_batch_step": (_I, [_P, _I, _I, _P]),
     "ps_diffusion3d_batch_run": (_I, [_P, _I, _I, _U, _P]),
+    "ps_batch_table_bytes_ex": (_SZ, [ctypes.POINTER(PsProblem), _I, _I, _I, _I, _I, _U]),
+    "ps_batch_table_fill_ex": (_I, [_P, _SZ, ctypes.POINTER(PsProblem), _I, _I, _I, _I, _I, _U,
+                                    ctypes.POINTER(_I64)]),
+    "ps_batch_table_kernel": (_I, [_P]),
+    "ps_diffusion3d_batch_step_ex": (_I, [_P, _P, _I, _P]),
+    "ps_diffusion3d_batch_run_ex": (_I, [_P, _P, _I, _U, _P]),
 }
 
 _lock = threading.Lock()

@@ -293,19 +293,61 @@ def to_f32(A: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     return to_deviation(A, 0.0, out)
 
 
+def _pitch(t: torch.Tensor, name: str) -> int:
+    """Row pitch (elements) of a field: contiguous, or a view whose rows are
+    `pitch` elements apart and whose planes are pitch*ny apart (see
+    :func:`pitched_empty`)."""
+    if t.dim() != 3:
+        raise ValueError("fields must have shape (nz, ny, nx)")
+    nz, ny, nx = t.shape
+    if t.is_contiguous():
+        return nx
+    sz, sy, sx = t.stride()
+    if sx != 1 or sy < nx or sz != sy * ny:
+        raise ValueError(f"{name} must be contiguous or padded along x only (rows {sy} apart, planes rows*ny)")
+    return sy
+
+
+def pitched_empty(shape, dtype=torch.float64, device="cuda") -> torch.Tensor:
+    """Uninitialised (nz, ny, nx) field whose rows start on 16-byte boundaries:
+    a view of an (nz, ny, pitch) block, pitch = nx rounded up to 16 bytes.  Its
+    rows can be staged by TMA whatever nx is (the batched z-march needs this)."""
+    nz, ny, nx = shape
+    per = 16 // torch.empty((), dtype=dtype).element_size()
+    pitch = -(-nx // per) * per
+    return torch.empty((nz, ny, pitch), dtype=dtype, device=device)[:, :, :nx]
+
+
+def pitched_copy(t: torch.Tensor) -> torch.Tensor:
+    """A copy of field ``t`` in the layout of :func:`pitched_empty`."""
+    out = pitched_empty(tuple(t.shape), t.dtype, t.device)
+    out.copy_(t)
+    return out
+
+
 class Batch:
-    """Many independent problems stepped together by one persistent launch.
+    """Many independent problems stepped together, one launch per step.
 
     ``problems`` is a list of dicts with keys ``T, T2, Ci`` (CUDA tensors of
-    one dtype, any cubic or non-cubic shape), ``lam``, ``dt`` and
-    ``inv_spacing``, and optionally ``tile`` = (tile_x, tile_y, tile_z) for
-    that problem's work items (see ``tuner.tuned_batch``).  T2's boundary must
-    equal T's (e.g. ``T2 = T.clone()``).
+    one dtype, any cubic or non-cubic shape; contiguous, or padded along x as
+    :func:`pitched_empty` makes them, the three with one pitch), ``lam``,
+    ``dt`` and ``inv_spacing``, and optionally ``tile`` = (tile_x, tile_y,
+    tile_z) for that problem's work items (see ``tuner.tuned_batch``).  T2's
+    boundary must equal T's (e.g. ``T2 = T.clone()``).
+
+    ``kernel``: "auto" (the TMA z-march when every problem can take it, else
+    the column march), "zmarch" or "column".  ``ci_scaled``: FP64 problems
+    whose ``Ci`` holds the pre-scaled ``dt*lam*_dx^2*Ci`` of :func:`scale_ci`
+    (equal spacings; z-march).  The chosen kernel is ``self.kernel``.
     """
 
-    def __init__(self, problems, tile=(0, 0, 0)):
+    KERNELS = {"auto": 0, "column": _lib.PS_BATCH_COLUMN, "zmarch": _lib.PS_BATCH_ZMARCH}
+
+    def __init__(self, problems, tile=(0, 0, 0), kernel: str = "auto", ci_scaled: bool = False):
         if not problems:
             raise ValueError("empty batch")
+        if kernel not in self.KERNELS:
+            raise ValueError(f"kernel must be one of {sorted(self.KERNELS)}")
         lib = _lib.load()
         self.code = _code(problems[0]["T"])
         self.device = problems[0]["T"].device
@@ -314,32 +356,43 @@ class Batch:
         for q, p in enumerate(problems):
             _same(p["T"], p["T2"], p["Ci"])
             nx, ny, nz = _grid(p["T"])
+            pitches = {_pitch(p[k], k) for k in ("T", "T2", "Ci")}
+            if len(pitches) != 1:
+                raise ValueError(f"problem {q}: T, T2 and Ci must share one row pitch")
+            for k in ("T", "T2", "Ci"):
+                if not p[k].is_cuda or _code(p[k]) != self.code:
+                    raise TypeError(f"problem {q}: {k} must be a CUDA tensor of the batch's dtype")
             tx, ty, tz = p.get("tile", (0, 0, 0))
-            arr[q] = _lib.PsProblem(_field(p["T"], "T", self.code), _field(p["T2"], "T2", self.code),
-                                    _field(p["Ci"], "Ci", self.code), p["lam"], p["dt"],
-                                    *p["inv_spacing"], nx, ny, nz, tx, ty, tz, 0)
-        nbytes = lib.ps_batch_table_bytes(arr, len(problems), self.code, *tile)
-        if nbytes == 0:
-            raise ValueError("invalid batch description")
-        host = (ctypes.c_char * nbytes)()
+            arr[q] = _lib.PsProblem(p["T"].data_ptr(), p["T2"].data_ptr(), p["Ci"].data_ptr(),
+                                    p["lam"], p["dt"], *p["inv_spacing"], nx, ny, nz, tx, ty, tz,
+                                    pitches.pop())
+        flags = self.KERNELS[kernel] | (_lib.PS_BATCH_CI_SCALED if ci_scaled else 0)
+        nbytes = lib.ps_batch_table_bytes_ex(arr, len(problems), self.code, *tile, flags)
+        # 64-byte aligned host buffer (the z-march table embeds tensor maps)
+        raw = (ctypes.c_char * (nbytes + 64))()
+        off = (-ctypes.addressof(raw)) % 64
+        host = (ctypes.c_char * max(nbytes, 1)).from_buffer(raw, off)
         nitems = ctypes.c_int64(0)
-        check(lib.ps_batch_table_fill(host, nbytes, arr, len(problems), self.code, *tile,
-                                      ctypes.byref(nitems)))
+        check(lib.ps_batch_table_fill_ex(host, nbytes, arr, len(problems), self.code, *tile, flags,
+                                         ctypes.byref(nitems)))
+        self._host_raw = raw  # keeps `host` alive: the step and run calls read its header
+        self.host = host
         self.nitems = nitems.value
         self.tile = tile
+        self.kernel = "zmarch" if lib.ps_batch_table_kernel(host) == 1 else "column"
         cpu = torch.frombuffer(bytearray(host.raw), dtype=torch.uint8)
         self.table = cpu.to(self.device)
         torch.cuda.current_stream(self.device).synchronize()
 
     def step(self, parity: int) -> None:
-        check(_lib.load().ps_diffusion3d_batch_step(self.table.data_ptr(), int(parity), self.code,
-                                                    torch.cuda.current_stream(self.device).cuda_stream))
+        check(_lib.load().ps_diffusion3d_batch_step_ex(self.table.data_ptr(), self.host, int(parity),
+                                                       torch.cuda.current_stream(self.device).cuda_stream))
 
     def run(self, nt: int, graph: bool = True) -> None:
         """nt steps; problem p's state ends in T2 when nt is odd, in T when even."""
         flags = _lib.PS_RUN_GRAPH if graph else 0
-        check(_lib.load().ps_diffusion3d_batch_run(self.table.data_ptr(), int(nt), self.code, flags,
-                                                   torch.cuda.current_stream(self.device).cuda_stream))
+        check(_lib.load().ps_diffusion3d_batch_run_ex(self.table.data_ptr(), self.host, int(nt), flags,
+                                                      torch.cuda.current_stream(self.device).cuda_stream))
 
     def result(self, q: int, nt: int) -> torch.Tensor:
         p = self.problems[q]
@@ -362,7 +415,8 @@ def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing, ci_scaled=False, temporal2
 
 
 KERNEL_SOURCES = {
-    "k_zmarch": ["paper_2211_15634_gb300/csrc/zmarch.cu", "paper_2211_15634_gb300/csrc/emu64.cuh",
+    "k_zmarch": ["paper_2211_15634_gb300/csrc/zmarch.cu", "paper_2211_15634_gb300/csrc/zmarch_tile.cuh",
+                 "paper_2211_15634_gb300/csrc/zmarch.h", "paper_2211_15634_gb300/csrc/emu64.cuh",
                  "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],
     "k_zmarch2": ["paper_2211_15634_gb300/csrc/zmarch2.cu", "paper_2211_15634_gb300/csrc/emu64.cuh",
                   "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],

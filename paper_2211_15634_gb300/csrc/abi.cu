@@ -13,6 +13,7 @@
 
 #include "emu64.cuh"
 #include "internal.h"
+#include "zmarch.h"
 
 namespace psd {
 
@@ -234,7 +235,8 @@ int ps_device_error(unsigned *out_host, int clear) {
     if (!out_host) return fail(PS_ERR_ARG, "out_host is NULL");
     *out_host = zmarch_device_error(clear != 0) | adjoint_device_error(clear != 0) |
                 adjoint_scaled_device_error(clear != 0) | zmarch2_device_error(clear != 0) |
-                adjoint_f32_device_error(clear != 0);
+                adjoint_f32_device_error(clear != 0) | batch_device_error(clear != 0) |
+                batch_zmarch_device_error(clear != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ps_device_error");
     return PS_OK;
@@ -600,9 +602,12 @@ int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *
 // ------------------------------------------------------------------ batch
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-static int resolve_tiles(int dtype, int *tx, int *ty, int *tz) {
+// kernel 1 (z-march): the x-y tile is the kernel's own; default chunks of 64 planes
+// (measured on the 256-problem workload: 64 >= 32 > 16 > 8 planes, FP32 and FP64)
+static int resolve_tiles(int dtype, int *tx, int *ty, int *tz, int kernel = 0) {
     int dx, dy, dz;
     batch_default_tile(dtype, &dx, &dy, &dz);
+    if (kernel == 1) dz = 64;
     if (*tx == 0) *tx = dx;
     if (*ty == 0) *ty = dy;
     if (*tz == 0) *tz = dz;
@@ -614,58 +619,160 @@ static int resolve_tiles(int dtype, int *tx, int *ty, int *tz) {
 
 // A problem's own tile fields override the call's.
 static int problem_tiles(const ps_problem &p, int dtype, int tx, int ty, int tz, int *ox, int *oy,
-                         int *oz) {
+                         int *oz, int kernel) {
     *ox = p.tile_x ? p.tile_x : tx;
     *oy = p.tile_y ? p.tile_y : ty;
     *oz = p.tile_z ? p.tile_z : tz;
-    return resolve_tiles(dtype, ox, oy, oz);
+    return resolve_tiles(dtype, ox, oy, oz, kernel);
 }
 
-static int64_t items_of(const ps_problem &p, int tx, int ty, int tz) {
+static int64_t pitch_of(const ps_problem &p) { return p.pitch ? p.pitch : p.nx; }
+
+// Everything ps_diffusion3d_step checks, over fields whose rows are pitch elements apart.
+static int check_batch_problem(const ps_problem &p, int dtype) {
+    PS_TRY(check_dtype(dtype));
+    PS_TRY(check_grid(p.nx, p.ny, p.nz));
+    PS_TRY(check_ptr(p.T2, "T2"));
+    PS_TRY(check_ptr(p.T, "T"));
+    PS_TRY(check_ptr(p.Ci, "Ci"));
+    PS_TRY(check_finite(p.lam, "lam"));
+    PS_TRY(check_finite(p.dt, "dt"));
+    PS_TRY(check_finite(p._dx, "_dx"));
+    PS_TRY(check_finite(p._dy, "_dy"));
+    PS_TRY(check_finite(p._dz, "_dz"));
+    const int64_t pitch = pitch_of(p);
+    if (pitch < p.nx) return fail(PS_ERR_ARG, "pitch %d < nx = %lld", p.pitch, (long long)p.nx);
+    // column-kernel offsets are 32-bit
+    if ((double)pitch * (double)p.ny * (double)p.nz >= 2147483648.0 || p.nx + 4096 > (1LL << 31) ||
+        p.ny + 4096 > (1LL << 31) || p.nz + 32767 > (1LL << 31))
+        return fail(PS_ERR_ARG, "problem is too large for the batch table (2^31 nodes at most)");
+    const size_t span = (size_t)((pitch * p.ny) * (p.nz - 1) + pitch * (p.ny - 1) + p.nx) * elem_bytes(dtype);
+    if (overlap(p.T2, p.T, span)) return fail(PS_ERR_ALIAS, "T2 overlaps T");
+    if (overlap(p.T2, p.Ci, span)) return fail(PS_ERR_ALIAS, "T2 overlaps Ci");
+    return PS_OK;
+}
+
+// Why the z-march kernel cannot take this problem (nullptr: it can).
+static const char *zmarch_refusal(const ps_problem &p, int dtype, bool scaled) {
+    const int esz = (int)elem_bytes(dtype);
+    if (!tma_encoder_available()) return "the tensor-map encoder of the CUDA driver is not available";
+    if ((pitch_of(p) * esz) % 16 != 0) return "the row pitch is not a multiple of 16 bytes";
+    if (p.nx > (1LL << 31) - 256 || p.ny > (1LL << 31) - 64 || p.nz > (1LL << 31) - 2)
+        return "the grid is too large for 32-bit tensor coordinates";
+    if (dtype == PS_F64) {
+        if (p._dx != p._dy || p._dy != p._dz) return "FP64 needs equal spacings";
+        if (!scaled) {
+            const StepCoef c = make_coef(p.lam, p.dt, p._dx, p._dy, p._dz);
+            const double K = c.dtlam * c.ax;
+            if (!(K > 2.2250738585072014e-308 && K < 1e300))
+                return "FP64 needs a positive step coefficient dt*lam*_dx^2 in the normal range";
+        }
+    }
+    return nullptr;
+}
+
+// Kernel of a table for these problems and flags: 0 column, 1 z-march, or an error status.
+static int choose_kernel(const ps_problem *probs, int nprob, int dtype, unsigned flags) {
+    if (flags & ~(PS_BATCH_COLUMN | PS_BATCH_ZMARCH | PS_BATCH_CI_SCALED))
+        return fail(PS_ERR_ARG, "unsupported batch flags 0x%x", flags);
+    if ((flags & PS_BATCH_COLUMN) && (flags & PS_BATCH_ZMARCH))
+        return fail(PS_ERR_ARG, "PS_BATCH_COLUMN and PS_BATCH_ZMARCH exclude each other");
+    const bool scaled = (flags & PS_BATCH_CI_SCALED) != 0;
+    if (scaled && dtype != PS_F64) return fail(PS_ERR_ARG, "PS_BATCH_CI_SCALED is for FP64 problems");
+    if (scaled && (flags & PS_BATCH_COLUMN))
+        return fail(PS_ERR_ARG, "PS_BATCH_CI_SCALED needs the z-march kernel");
+    if (flags & PS_BATCH_COLUMN) return 0;
+    for (int q = 0; q < nprob; ++q) {
+        const char *why = zmarch_refusal(probs[q], dtype, scaled);
+        if (why) {
+            if ((flags & PS_BATCH_ZMARCH) || scaled)
+                return fail(PS_ERR_UNSUPPORTED, "problem %d: %s", q, why);
+            return 0;
+        }
+    }
+    return 1;
+}
+
+static int64_t items_of(const ps_problem &p, int kernel, int dtype, int tx, int ty, int tz) {
+    if (kernel == 1) return batch_zmarch_xy_tiles(dtype, p.nx, p.ny, nullptr) * ((p.nz - 2 + tz - 1) / tz);
     return ((p.nx - 2 + tx - 1) / tx) * ((p.ny - 2 + ty - 1) / ty) * ((p.nz - 2 + tz - 1) / tz);
 }
 
-static size_t table_bytes(int nprob, int64_t nitems) {
-    return align_up(sizeof(BatchHeader), 64) + align_up(sizeof(BatchProblem) * (size_t)nprob, 64) +
-           sizeof(BatchItem) * (size_t)nitems;
+struct TableLayout {
+    size_t problems, zparams, maps, items, bytes;
+};
+
+static TableLayout table_layout(int nprob, int64_t nitems, int kernel) {
+    TableLayout L{};
+    L.problems = align_up(sizeof(BatchHeader), 128);
+    size_t end = L.problems + align_up(sizeof(BatchProblem) * (size_t)nprob, 128);
+    if (kernel == 1) {
+        L.zparams = end;
+        end += align_up(sizeof(ZParams) * (size_t)nprob, 128);
+        L.maps = end;  // tensor maps want 64-byte alignment
+        end += sizeof(CUtensorMap) * kBatchZmarchMaps * (size_t)nprob;
+    }
+    L.items = end;
+    L.bytes = end + sizeof(BatchItem) * (size_t)nitems;
+    return L;
+}
+
+// Work items and layout of a table (status, or PS_OK with *nitems and *kernel set).
+static int plan_table(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y, int tile_z,
+                      unsigned flags, int64_t *nitems, int *kernel) {
+    if (!probs) return fail(PS_ERR_ARG, "probs is NULL");
+    if (nprob < 1) return fail(PS_ERR_ARG, "nprob = %d < 1", nprob);
+    PS_TRY(check_dtype(dtype));
+    {
+        int tx = tile_x, ty = tile_y, tz = tile_z;
+        PS_TRY(resolve_tiles(dtype, &tx, &ty, &tz));
+    }
+    for (int q = 0; q < nprob; ++q) {
+        const int st = check_batch_problem(probs[q], dtype);
+        if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
+    }
+    const int k = choose_kernel(probs, nprob, dtype, flags);
+    if (k < 0) return k;
+    PS_TRY(resolve_tiles(dtype, &tile_x, &tile_y, &tile_z, k));
+    int64_t n = 0;
+    for (int q = 0; q < nprob; ++q) {
+        int tx, ty, tz;
+        const int st = problem_tiles(probs[q], dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz, k);
+        if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
+        n += items_of(probs[q], k, dtype, tx, ty, tz);
+    }
+    if (k == 1 && n > 0x7fffffffLL) return fail(PS_ERR_ARG, "%lld work items: at most 2^31-1", (long long)n);
+    *nitems = n;
+    *kernel = k;
+    return PS_OK;
+}
+
+size_t ps_batch_table_bytes_ex(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
+                               int tile_z, unsigned flags) {
+    int64_t nitems = 0;
+    int kernel = 0;
+    if (plan_table(probs, nprob, dtype, tile_x, tile_y, tile_z, flags, &nitems, &kernel) != PS_OK) return 0;
+    return table_layout(nprob, nitems, kernel).bytes;
 }
 
 size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
                             int tile_z) {
-    if (!probs || nprob < 1 || check_dtype(dtype) != PS_OK) return 0;
-    if (resolve_tiles(dtype, &tile_x, &tile_y, &tile_z) != PS_OK) return 0;
-    int64_t nitems = 0;
-    for (int q = 0; q < nprob; ++q) {
-        int tx, ty, tz;
-        if (probs[q].nx < 3 || probs[q].ny < 3 || probs[q].nz < 3) return 0;
-        if (problem_tiles(probs[q], dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz) != PS_OK) return 0;
-        nitems += items_of(probs[q], tx, ty, tz);
-    }
-    return table_bytes(nprob, nitems);
+    return ps_batch_table_bytes_ex(probs, nprob, dtype, tile_x, tile_y, tile_z, PS_BATCH_COLUMN);
 }
 
-int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, int nprob, int dtype,
-                        int tile_x, int tile_y, int tile_z, int64_t *nitems_out) {
-    if (!host_buf || !probs) return fail(PS_ERR_ARG, "host_buf or probs is NULL");
-    if (nprob < 1) return fail(PS_ERR_ARG, "nprob = %d < 1", nprob);
-    PS_TRY(check_dtype(dtype));
-    PS_TRY(resolve_tiles(dtype, &tile_x, &tile_y, &tile_z));
+int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs, int nprob, int dtype,
+                           int tile_x, int tile_y, int tile_z, unsigned flags, int64_t *nitems_out) {
+    if (!host_buf) return fail(PS_ERR_ARG, "host_buf is NULL");
     int64_t nitems = 0;
-    for (int q = 0; q < nprob; ++q) {
-        const ps_problem &p = probs[q];
-        int st = check_step_args(p.T2, p.T, p.Ci, p.lam, p.dt, p._dx, p._dy, p._dz, p.nx, p.ny, p.nz, dtype);
-        if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
-        int tx, ty, tz;
-        st = problem_tiles(p, dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz);
-        if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
-        if (p.nx * p.ny * p.nz >= (1LL << 31) || p.nx + tx > (1LL << 31) || p.ny + ty > (1LL << 31) ||
-            p.nz + tz > (1LL << 31))
-            return fail(PS_ERR_ARG, "problem %d is too large for the batch table (2^31 nodes at most)", q);
-        nitems += items_of(p, tx, ty, tz);
-    }
-    const size_t need = table_bytes(nprob, nitems);
-    if (bytes < need) return fail(PS_ERR_ARG, "table buffer has %zu bytes, needs %zu", bytes, need);
-    std::memset(host_buf, 0, need);
+    int kernel = 0;
+    PS_TRY(plan_table(probs, nprob, dtype, tile_x, tile_y, tile_z, flags, &nitems, &kernel));
+    PS_TRY(resolve_tiles(dtype, &tile_x, &tile_y, &tile_z, kernel));
+    const TableLayout L = table_layout(nprob, nitems, kernel);
+    if (bytes < L.bytes) return fail(PS_ERR_ARG, "table buffer has %zu bytes, needs %zu", bytes, L.bytes);
+    if (kernel == 1 && ((uintptr_t)host_buf & 63u))
+        return fail(PS_ERR_ALIGN, "host_buf must be 64-byte aligned for the tensor maps");
+    const bool scaled = (flags & PS_BATCH_CI_SCALED) != 0;
+    std::memset(host_buf, 0, L.bytes);
     char *base = (char *)host_buf;
     BatchHeader *h = (BatchHeader *)base;
     h->nprob = nprob;
@@ -674,9 +781,13 @@ int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, i
     h->tile_x = tile_x;
     h->tile_y = tile_y;
     h->tile_z = tile_z;
-    h->problems_offset = (int64_t)align_up(sizeof(BatchHeader), 64);
-    h->items_offset = h->problems_offset + (int64_t)align_up(sizeof(BatchProblem) * (size_t)nprob, 64);
-    BatchProblem *bp = (BatchProblem *)(base + h->problems_offset);
+    h->problems_offset = (int64_t)L.problems;
+    h->items_offset = (int64_t)L.items;
+    h->kernel = kernel;
+    h->zmode = kernel == 1 ? (dtype == PS_F32 ? Z_F32 : (scaled ? Z_F64_SCALED : Z_F64_EMU_ISO_DMUL)) : -1;
+    h->zparams_offset = (int64_t)L.zparams;
+    h->maps_offset = (int64_t)L.maps;
+    BatchProblem *bp = (BatchProblem *)(base + L.problems);
     std::vector<std::pair<int64_t, BatchItem>> work;
     work.reserve((size_t)nitems);
     for (int q = 0; q < nprob; ++q) {
@@ -693,6 +804,7 @@ int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, i
         r.nx = p.nx;
         r.ny = p.ny;
         r.nz = p.nz;
+        r.pitch = pitch_of(p);
         const double K[3] = {c.dtlam * c.ax, c.dtlam * c.ay, c.dtlam * c.az};
         bool emu = true;
         for (double v : K) emu = emu && v > 2.2250738585072014e-308 && v < 1e300;
@@ -706,11 +818,31 @@ int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, i
             r.kze = kz.e;
             r.iso = (c.ax == c.ay && c.ay == c.az) ? 1 : 0;
         } else {
-            r.iso = -1;  // the kernel takes the plain FP64 expression
+            r.iso = -1;  // the column kernel takes the plain FP64 expression
         }
         bp[q] = r;
         int tx, ty, tz;
-        problem_tiles(p, dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz);
+        problem_tiles(p, dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz, kernel);
+        if (kernel == 1) {
+            if (!batch_zmarch_fill(base + L.zparams + sizeof(ZParams) * q,
+                                   base + L.maps + sizeof(CUtensorMap) * kBatchZmarchMaps * q, r, c,
+                                   dtype))
+                return fail(PS_ERR_UNSUPPORTED, "problem %d: tensor-map encoding failed", q);
+            // x-y tiles of the whole plane from the origin (boundary included), like the
+            // single-grid kernel, times z-chunks of the interior planes
+            std::vector<BatchItem> xy((size_t)batch_zmarch_xy_tiles(dtype, p.nx, p.ny, nullptr));
+            batch_zmarch_xy_tiles(dtype, p.nx, p.ny, xy.data());
+            for (int64_t k0 = 1; k0 < p.nz - 1; k0 += tz)
+                for (const BatchItem &t : xy) {
+                    BatchItem it = t;
+                    it.prob = q;
+                    it.k0 = (int32_t)k0;
+                    it.ni = it.nj = 0;
+                    it.nk = (int16_t)std::min<int64_t>(tz, p.nz - 1 - k0);
+                    work.push_back({0, it});
+                }
+            continue;
+        }
         for (int64_t k0 = 1; k0 < p.nz - 1; k0 += tz)
             for (int64_t j0 = 1; j0 < p.ny - 1; j0 += ty)
                 for (int64_t i0 = 1; i0 < p.nx - 1; i0 += tx) {
@@ -722,14 +854,66 @@ int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, i
                     work.push_back({ni * nj * nk, it});
                 }
     }
-    // largest items first: the round-robin hand-out then stays balanced
-    std::stable_sort(work.begin(), work.end(),
-                     [](const std::pair<int64_t, BatchItem> &a, const std::pair<int64_t, BatchItem> &b) {
-                         return a.first > b.first;
-                     });
-    BatchItem *items = (BatchItem *)(base + h->items_offset);
+    if (kernel == 1) {
+        // z-march: problems largest first (the block scheduler's order stays balanced:
+        // the small problems' items fill the tail), each problem's items together in
+        // chunk, row, column order, so tiles that run at the same time are neighbours
+        // and the halo rows and planes they share come from L2 (sorting single items
+        // by size measured 32% extra DRAM reads on the 256-problem workload)
+        std::vector<int64_t> pbytes(nprob);
+        for (int q = 0; q < nprob; ++q) pbytes[q] = probs[q].nx * probs[q].ny * probs[q].nz;
+        std::stable_sort(work.begin(), work.end(),
+                         [&](const std::pair<int64_t, BatchItem> &a, const std::pair<int64_t, BatchItem> &b) {
+                             const int64_t sa = pbytes[a.second.prob], sb = pbytes[b.second.prob];
+                             if (sa != sb) return sa > sb;
+                             return a.second.prob < b.second.prob;
+                         });
+    } else {
+        // column march: largest items first, so the persistent CTAs' round-robin
+        // hand-out stays balanced (measured 13% faster than the problem order above)
+        std::stable_sort(work.begin(), work.end(),
+                         [](const std::pair<int64_t, BatchItem> &a, const std::pair<int64_t, BatchItem> &b) {
+                             return a.first > b.first;
+                         });
+    }
+    BatchItem *items = (BatchItem *)(base + L.items);
     for (size_t t = 0; t < work.size(); ++t) items[t] = work[t].second;
     if (nitems_out) *nitems_out = nitems;
+    return PS_OK;
+}
+
+int ps_batch_table_fill(void *host_buf, size_t bytes, const ps_problem *probs, int nprob, int dtype,
+                        int tile_x, int tile_y, int tile_z, int64_t *nitems_out) {
+    return ps_batch_table_fill_ex(host_buf, bytes, probs, nprob, dtype, tile_x, tile_y, tile_z,
+                                  PS_BATCH_COLUMN, nitems_out);
+}
+
+int ps_batch_table_kernel(const void *host_table) {
+    if (!host_table) return fail(PS_ERR_ARG, "host_table is NULL");
+    return ((const BatchHeader *)host_table)->kernel;
+}
+
+static cudaError_t enqueue_batch(const void *dev_table, const BatchHeader &h, int parity, cudaStream_t s) {
+    if (h.kernel == 1) return launch_batch_zmarch(dev_table, h.nitems, h.zmode, parity, s);
+    return launch_batch_step(dev_table, parity, h.dtype, s);
+}
+
+static int batch_header(const void *host_table, BatchHeader *h) {
+    if (!host_table) return fail(PS_ERR_ARG, "host_table is NULL");
+    *h = *(const BatchHeader *)host_table;
+    PS_TRY(check_dtype(h->dtype));
+    if (h->kernel != 0 && h->kernel != 1) return fail(PS_ERR_ARG, "host_table is not a batch table");
+    if (h->nitems < 1) return fail(PS_ERR_ARG, "the table has no work items");
+    return PS_OK;
+}
+
+int ps_diffusion3d_batch_step_ex(const void *dev_table, const void *host_table, int parity, void *stream) {
+    if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
+    BatchHeader h;
+    PS_TRY(batch_header(host_table, &h));
+    if (parity != 0 && parity != 1) return fail(PS_ERR_ARG, "parity %d is not 0 or 1", parity);
+    cudaError_t e = enqueue_batch(dev_table, h, parity, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_batch_step");
     return PS_OK;
 }
 
@@ -742,23 +926,21 @@ int ps_diffusion3d_batch_step(const void *dev_table, int parity, int dtype, void
     return PS_OK;
 }
 
-int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned flags,
-                             void *stream) {
-    if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
-    PS_TRY(check_dtype(dtype));
+static int batch_run(const void *dev_table, const BatchHeader &h, int nt, unsigned flags, cudaStream_t s) {
     if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
     if (flags & ~PS_RUN_GRAPH) return fail(PS_ERR_ARG, "unsupported flags 0x%x", flags);
-    cudaStream_t s = (cudaStream_t)stream;
-    batch_prepare(dtype);
+    if (h.kernel == 0) batch_prepare(h.dtype);
     if (!(flags & PS_RUN_GRAPH)) {
         for (int it = 0; it < nt; ++it) {
-            cudaError_t e = launch_batch_step(dev_table, it & 1, dtype, s);
+            cudaError_t e = enqueue_batch(dev_table, h, it & 1, s);
             if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_batch_run");
         }
         return PS_OK;
     }
+    // the table's work-item count and kernel are part of the key: the z-march launch
+    // size is baked into the graph (a new table may reuse a freed table's address)
     const GraphKey key{current_device(), dev_table, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0,
-                       0.0, -1, -1, -1, nt, dtype, 0x80000000u};
+                       0.0, h.nitems, h.zmode, h.kernel, nt, h.dtype, 0x80000000u};
     std::lock_guard<std::mutex> lock(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
@@ -768,7 +950,7 @@ int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned 
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
         cudaError_t le = cudaSuccess;
-        for (int t = 0; t < nt && le == cudaSuccess; ++t) le = launch_batch_step(dev_table, t & 1, dtype, cs);
+        for (int t = 0; t < nt && le == cudaSuccess; ++t) le = enqueue_batch(dev_table, h, t & 1, cs);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cs, &graph);
         if (le != cudaSuccess) {
@@ -785,6 +967,24 @@ int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned 
     cudaError_t e = cudaGraphLaunch(it->second, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return PS_OK;
+}
+
+int ps_diffusion3d_batch_run_ex(const void *dev_table, const void *host_table, int nt, unsigned flags,
+                                void *stream) {
+    if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
+    BatchHeader h;
+    PS_TRY(batch_header(host_table, &h));
+    return batch_run(dev_table, h, nt, flags, (cudaStream_t)stream);
+}
+
+int ps_diffusion3d_batch_run(const void *dev_table, int nt, int dtype, unsigned flags,
+                             void *stream) {
+    if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
+    PS_TRY(check_dtype(dtype));
+    BatchHeader h{};
+    h.dtype = dtype;
+    h.kernel = 0;
+    return batch_run(dev_table, h, nt, flags, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -4,6 +4,7 @@
 // largest first; CTA b processes items b, b + gridDim.x, ... (no atomics and
 // no counters, so a captured graph replays the same schedule every time).
 //
+// Rows are P.pitch elements apart (nx for contiguous fields), planes pitch*ny.
 // Within an item every thread owns one interior (i, j) column of the tile and
 // marches along z with a three-value register queue; x/y neighbours are read
 // through L1/L2 (problems of 32^3..160^3 are small enough for the caches to
@@ -16,6 +17,8 @@ namespace psd {
 
 constexpr int kBatchThreads = 256;
 
+__device__ unsigned g_batch_error;  // bit 1: a table built for the z-march kernel was given
+
 template <typename F>
 __device__ __forceinline__ void batch_item(const BatchItem &item, const BatchProblem &P, int parity) {
     const F *__restrict__ T = (const F *)(parity ? P.T2 : P.T);
@@ -23,7 +26,7 @@ __device__ __forceinline__ void batch_item(const BatchItem &item, const BatchPro
     const F *__restrict__ Ci = (const F *)P.Ci;
     // batch problems hold fewer than 2^31 nodes (checked when the table is
     // built), so 32-bit offsets suffice and keep the register count low
-    const int nx = (int)P.nx, ny = (int)P.ny, sy = nx, sz = nx * ny;
+    const int ny = (int)P.ny, sy = (int)P.pitch, sz = sy * ny;
     const int ni = item.ni, nj = item.nj;
     const int k0 = item.k0, k1 = k0 + item.nk;
     for (int t = threadIdx.x; t < ni * nj; t += blockDim.x) {
@@ -104,6 +107,10 @@ template <typename F>
 __global__ void __launch_bounds__(kBatchThreads, BatchOcc<F>::min_blocks)
 k_batch_step(const char *__restrict__ table, int parity) {
     const BatchHeader *h = (const BatchHeader *)table;
+    if (h->kernel != 0) {  // items of the z-march kernel: not this kernel's work
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&g_batch_error, 2u);
+        return;
+    }
     const BatchProblem *probs = (const BatchProblem *)(table + h->problems_offset);
     const BatchItem *items = (const BatchItem *)(table + h->items_offset);
     const int64_t nitems = h->nitems;
@@ -136,6 +143,16 @@ static unsigned resident_grid() {
         if (d >= 0 && d < 64) per_sm[d] = v;
     }
     return (unsigned)(v * sm_count());
+}
+
+unsigned batch_device_error(bool clear) {
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_batch_error, sizeof(v));
+    if (clear) {
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(g_batch_error, &z, sizeof(z));
+    }
+    return v;
 }
 
 void batch_prepare(int dtype) {  // occupancy query outside any stream capture

@@ -1,0 +1,151 @@
+// Batched step as a TMA-fed z-march: one launch per step, one CTA per work item.
+//
+// The table holds, besides the header, problem records and work list of the
+// column kernel (batch.cu), the step parameters of every problem and six
+// tensor maps per problem (T and T2 with the halo box, Ci with the tile box,
+// for each of the two tile shapes), encoded on the host over the problem's own
+// row pitch.  Work item (problem, X0, Y0, k0, nk, kind) is an x-y tile at
+// (X0, Y0) (boundary included, like the single-grid tiles) and output planes
+// [k0, k0+nk): kind 0 the single-grid tile (32 lanes x PX nodes wide, 8 rows),
+// kind 1 a narrow one (16 lanes x PX wide, 16 rows, two rows per warp) that
+// closes a row of tiles when at most half a wide tile of columns is left -
+// batch grids are small, and a wide last tile would leave up to half its lanes
+// idle.  CTA b runs item b with the z-march tile body of the single-grid kernel
+// (zmarch_tile.cuh), so every problem is stepped by the very arithmetic of its
+// own single run.  The work list is static; a captured graph replays the same
+// launches every time.
+//
+// Requirements (checked when the table is built): every row pitch times the
+// element size is a multiple of 16 bytes and every base pointer is 16-byte
+// aligned (padded rows, see ps_problem.pitch); FP64 problems on Ci as given
+// have equal spacings and a positive step coefficient; FP64 problems on the
+// pre-scaled coefficient (PS_BATCH_CI_SCALED) have equal spacings.
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+#include "zmarch.h"
+#include "zmarch_tile.cuh"
+
+namespace psd {
+
+__device__ unsigned g_batchz_error;  // set when an mbarrier wait times out
+
+// tile shapes: wide = 32 lanes per row x 8 rows, narrow = 16 lanes per row x 16 rows
+constexpr int kBZ_NST = 4, kBZ_WIDE_BY = 8, kBZ_NARROW_BY = 16;
+
+// resident CTAs per SM the registers are sized for: Ci as given (two FP64 products
+// per node and the emulation constants) spills at 64 registers, so 3 CTAs there
+template <int MODE>
+struct BZOcc {
+    static constexpr int min_blocks = MODE == Z_F64_EMU_ISO_DMUL ? 3 : 4;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256, BZOcc<MODE>::min_blocks)
+k_batch_zmarch(const char *__restrict__ table, int parity) {
+    const BatchHeader *h = (const BatchHeader *)table;
+    const BatchItem item = ((const BatchItem *)(table + h->items_offset))[blockIdx.x];
+    __shared__ ZParams s_p;
+    if (threadIdx.x == 0) s_p = ((const ZParams *)(table + h->zparams_offset))[item.prob];
+    __syncthreads();
+    const BatchProblem *P = (const BatchProblem *)(table + h->problems_offset) + item.prob;
+    const CUtensorMap *maps =
+        (const CUtensorMap *)(table + h->maps_offset) + kBatchZmarchMaps * item.prob;
+    void *out = parity ? P->T : P->T2;
+    if (item.kind == 0)  // CTA-uniform
+        zmarch_tile<MODE, kBZ_WIDE_BY, kBZ_NST, 32>(maps + (parity ? 1 : 0), maps + 2, out, nullptr, s_p,
+                                                    item.i0, item.j0, item.k0, item.k0 + item.nk,
+                                                    &g_batchz_error);
+    else
+        zmarch_tile<MODE, kBZ_NARROW_BY, kBZ_NST, 16>(maps + 3 + (parity ? 1 : 0), maps + 5, out, nullptr,
+                                                      s_p, item.i0, item.j0, item.k0, item.k0 + item.nk,
+                                                      &g_batchz_error);
+}
+
+int64_t batch_zmarch_xy_tiles(int dtype, int64_t nx, int64_t ny, BatchItem *out) {
+    const int64_t wide = dtype == PS_F64 ? 64 : 128, narrow = wide / 2;
+    int64_t n = 0;
+    // interior columns 1 .. nx-2 from tile origins 0, wide, 2*wide, ...: the last
+    // origin takes a narrow tile when at most `narrow` columns are left
+    for (int64_t x0 = 0; x0 < nx - 1;) {
+        const bool nar = nx - 1 - x0 <= narrow;
+        const int64_t by = nar ? kBZ_NARROW_BY : kBZ_WIDE_BY;
+        for (int64_t y0 = 0; y0 < ny - 1; y0 += by, ++n)
+            if (out) {
+                out[n].i0 = (int32_t)x0;
+                out[n].j0 = (int32_t)y0;
+                out[n].kind = nar ? 1 : 0;
+            }
+        x0 += nar ? narrow : wide;
+    }
+    return n;
+}
+
+bool batch_zmarch_fill(void *zparams_dst, void *maps_dst, const BatchProblem &r, StepCoef c, int dtype) {
+    const int esz = dtype == PS_F64 ? 8 : 4;
+    const int px = dtype == PS_F64 ? 2 : 4;
+    const Grid3 g{r.nx, r.ny, r.nz};
+    ZParams zp = zparams_for(c, g, r.pitch);
+    zp.kchunk = 0;
+    zp.ntx = 0;
+    *(ZParams *)zparams_dst = zp;
+    CUtensorMap *m = (CUtensorMap *)maps_dst;
+    bool ok = true;
+    for (int v = 0; v < 2; ++v) {
+        const int lpr = v == 0 ? 32 : 16, by = v == 0 ? kBZ_WIDE_BY : kBZ_NARROW_BY, bx = lpr * px;
+        const unsigned W = (unsigned)(bx + 2 * px), H = (unsigned)(by + 2);
+        ok = ok && make_tensor_map_3d_pitch(&m[3 * v + 0], r.T, esz, g, r.pitch, W, H) &&
+             make_tensor_map_3d_pitch(&m[3 * v + 1], r.T2, esz, g, r.pitch, W, H) &&
+             make_tensor_map_3d_pitch(&m[3 * v + 2], r.Ci, esz, g, r.pitch, (unsigned)bx, (unsigned)by);
+    }
+    return ok;
+}
+
+template <typename E, int PX, int LPR, int BY>
+constexpr size_t bz_smem() {
+    constexpr int BX = LPR * PX, W = BX + 2 * PX, H = BY + 2;
+    constexpr unsigned TBA = (W * H * sizeof(E) + 127) / 128 * 128;
+    constexpr unsigned CBA = (BX * BY * sizeof(E) + 127) / 128 * 128;
+    return kBZ_NST * (TBA + CBA) + kBZ_NST * 8;
+}
+
+template <int MODE>
+static cudaError_t launch_bz_t(const void *dev_table, int64_t nitems, int parity, cudaStream_t s) {
+    using E = typename ZTraits<MODE>::E;
+    constexpr int PX = ZTraits<MODE>::PX;
+    constexpr size_t sw = bz_smem<E, PX, 32, kBZ_WIDE_BY>(), sn = bz_smem<E, PX, 16, kBZ_NARROW_BY>();
+    constexpr size_t smem = sw > sn ? sw : sn;
+    static bool attr_done[64] = {false};
+    const int dev = current_device();
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_zmarch<MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    if (nitems < 1 || nitems > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_batch_zmarch<MODE><<<(unsigned)nitems, 256, smem, s>>>((const char *)dev_table, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_zmarch(const void *dev_table, int64_t nitems, int zmode, int parity,
+                                cudaStream_t s) {
+    switch (zmode) {
+        case Z_F32: return launch_bz_t<Z_F32>(dev_table, nitems, parity, s);
+        case Z_F64_EMU_ISO_DMUL: return launch_bz_t<Z_F64_EMU_ISO_DMUL>(dev_table, nitems, parity, s);
+        case Z_F64_SCALED: return launch_bz_t<Z_F64_SCALED>(dev_table, nitems, parity, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+unsigned batch_zmarch_device_error(bool clear) {
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_batchz_error, sizeof(v));
+    if (clear) {
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(g_batchz_error, &z, sizeof(z));
+    }
+    return v;
+}
+
+}  // namespace psd

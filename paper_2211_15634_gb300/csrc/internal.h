@@ -96,6 +96,10 @@ struct BatchHeader {
     int64_t nprob, nitems;
     int32_t dtype, tile_x, tile_y, tile_z;
     int64_t problems_offset, items_offset;  // byte offsets from the table start
+    // kernel 0: column march (batch.cu); 1: TMA z-march (batch_tma.cu) in step mode
+    // zmode, with a ZParams record and three tensor maps per problem at these offsets
+    int32_t kernel, zmode;
+    int64_t zparams_offset, maps_offset;
 };
 struct BatchProblem {
     void *T;
@@ -103,6 +107,7 @@ struct BatchProblem {
     const void *Ci;
     double dtlam, ax, ay, az;
     int64_t nx, ny, nz;
+    int64_t pitch;  // elements between consecutive rows; planes are pitch*ny apart
     // one-DFMA-class emulated arithmetic constants (FP64): K_d = dtlam*a_d as
     // integer mantissa/exponent, and whether the three axes share one K
     unsigned long long kxm, kym, kzm;
@@ -111,9 +116,22 @@ struct BatchProblem {
 struct BatchItem {
     int32_t prob;
     int32_t i0, j0, k0;      // first interior node of the work item
-    int16_t ni, nj, nk, pad;  // extents (clipped to the interior)
+    int16_t ni, nj, nk;       // extents (clipped to the interior; z-march: ni = nj = 0)
+    int16_t kind;             // z-march: 0 a wide tile (one warp per row), 1 a narrow one
 };
 cudaError_t launch_batch_step(const void *dev_table, int parity, int dtype, cudaStream_t s);
+unsigned batch_device_error(bool clear);
+// TMA z-march batch (batch_tma.cu): tile width per dtype, tile height, the per-problem
+// records (ZParams and three tensor maps), the launch (grid = one CTA per item)
+// x-y tiles of the z-march over an nx x ny plane: (x0, y0, kind) into out[i].i0/.j0/.kind
+// when out is not null; returns their number
+int64_t batch_zmarch_xy_tiles(int dtype, int64_t nx, int64_t ny, BatchItem *out);
+constexpr int kBatchZmarchMaps = 6;  // tensor maps per problem
+bool batch_zmarch_fill(void *zparams_dst, void *maps_dst, const BatchProblem &r, StepCoef c, int dtype);
+cudaError_t launch_batch_zmarch(const void *dev_table, int64_t nitems, int zmode, int parity,
+                                cudaStream_t s);
+unsigned batch_zmarch_device_error(bool clear);
+bool tma_encoder_available();
 void batch_prepare(int dtype);
 int batch_default_tile(int dtype, int *tx, int *ty, int *tz);
 

@@ -20,6 +20,7 @@ enum ZMode {
 
 struct ZParams {
     int64_t nx, ny, nz;
+    int64_t pitch;  // elements between consecutive rows (nx for a contiguous grid)
     int kchunk, ntx;
     EmuCoef ek;
     float fdtlam, fax, fay, faz;
@@ -29,6 +30,13 @@ struct ZParams {
 bool zmarch_supported(Grid3 g, int esz, const void *a, const void *b, const void *c);
 // 3-D tiled tensor map over a (nz, ny, nx) field with a bx x by x 1 box.
 bool make_tensor_map_3d(CUtensorMap *m, const void *ptr, int esz, Grid3 g, unsigned bx, unsigned by);
+// The same over a grid whose rows are `pitch` elements apart (pitch*esz a multiple of 16).
+bool make_tensor_map_3d_pitch(CUtensorMap *m, const void *ptr, int esz, Grid3 g, int64_t pitch,
+                              unsigned bx, unsigned by);
+// True when the driver's tensor-map encoder could be loaded (a GPU driver is present).
+bool tma_encoder_available();
+// Step parameters of the z-march kernels for coefficients c on grid g with row pitch `pitch`.
+ZParams zparams_for(StepCoef c, Grid3 g, int64_t pitch);
 
 // TMA-fed transposed step (adjoint_zmarch.cu).
 bool adjoint_zmarch_supported(Grid3 g, int esz, const void *const *ptrs, int nptr);

@@ -1,10 +1,12 @@
 """Tile-shape autotuner for the batched step.
 
 Problems are grouped into size classes by their largest extent; for each class
-the batched kernel is timed (CUDA events, a few steps after warm-up) on that
-class's problems alone with every candidate work-item shape (tile_x, tile_y,
-tile_z), and the fastest shape is kept.  Results are cached as JSON keyed by
-GPU name, dtype and size class (file ``$PS_TUNER_CACHE`` or
+the batched kernel is timed (CUDA events, a few steps after warm-up) on the
+whole batch with every candidate work-item shape (tile_x, tile_y, tile_z) for
+that class, and the fastest shape is kept.  The candidates depend on the kernel
+the batch runs: the column march takes x-y tiles and z-chunks, the TMA z-march
+(fixed x-y tiles) its z-chunk length.  Results are cached as JSON keyed by GPU
+name, dtype, kernel and size class (file ``$PS_TUNER_CACHE`` or
 ``~/.cache/psdiff/tuner.json``), so later runs reuse them without timing.
 ``tuned_batch`` builds the final table with each problem's class shape.
 """
@@ -12,7 +14,7 @@ from __future__ import annotations
 
 import json
 import os
-from typing import Dict, List, Sequence, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import torch
 
@@ -32,13 +34,17 @@ CANDIDATES: List[Tile] = [DEFAULT, (32, 8, 16), (32, 8, 64), (32, 16, 16), (64, 
 def tile_for(problem, cand: Tile) -> Tile:
     """Concrete (tile_x, tile_y, tile_z) of a candidate for one problem."""
     tx, ty, tz = cand
-    if tx != 0:
+    if tx != 0 or ty == 0:  # a fixed shape, or a z-march candidate (x-y tile ignored)
         return cand
     row = problem["T"].shape[2] - 2
     rows = max(1, min(problem["T"].shape[1] - 2, -(-ty // row)))
     while row * rows > 4096:
         rows -= 1
     return row, rows, tz
+# z-march candidates: planes per work item (the x-y tile is the kernel's own)
+ZMARCH_DEFAULT: Tile = (0, 0, 64)
+ZMARCH_CANDIDATES: List[Tile] = [ZMARCH_DEFAULT, (0, 0, 16), (0, 0, 32), (0, 0, 128)]
+
 SIZE_CLASSES: List[Tuple[int, int]] = [(3, 48), (48, 80), (80, 112), (112, 144), (144, 1 << 30)]
 
 
@@ -75,14 +81,22 @@ def size_class(p) -> Tuple[int, int]:
     return SIZE_CLASSES[-1]
 
 
-def _key(device, dtype, cls) -> str:
+def _key(device, dtype, cls, kernel="column", ci_scaled=False) -> str:
     name = torch.cuda.get_device_name(device)
-    return f"{name}|{'f64' if dtype == torch.float64 else 'f32'}|{cls[0]}-{cls[1]}"
+    kern = kernel + ("-scaled" if ci_scaled else "")
+    return f"{name}|{'f64' if dtype == torch.float64 else 'f32'}|{kern}|{cls[0]}-{cls[1]}"
 
 
-def time_batch_step(problems, cand: Tile, reps: int = 5, warmup: int = 2) -> float:
+def batch_kernel(problems, kernel: str = "auto", ci_scaled: bool = False) -> str:
+    """The kernel ("column" or "zmarch") a Batch of these problems would run."""
+    return api.Batch(problems, kernel=kernel, ci_scaled=ci_scaled).kernel
+
+
+def time_batch_step(problems, cand: Tile, reps: int = 5, warmup: int = 2, kernel: str = "auto",
+                    ci_scaled: bool = False) -> float:
     """Milliseconds per batched step of these problems with one candidate shape."""
-    b = api.Batch([dict(p, tile=tile_for(p, cand)) for p in problems])
+    b = api.Batch([dict(p, tile=tile_for(p, cand)) for p in problems], kernel=kernel,
+                  ci_scaled=ci_scaled)
     for _ in range(warmup):
         b.step(0)
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -94,9 +108,10 @@ def time_batch_step(problems, cand: Tile, reps: int = 5, warmup: int = 2) -> flo
     return s.elapsed_time(e) / reps
 
 
-def _time_assignment(problems, assign: Dict[Tuple[int, int], Tile], reps: int) -> float:
+def _time_assignment(problems, assign: Dict[Tuple[int, int], Tile], reps: int, kernel: str,
+                     ci_scaled: bool) -> float:
     tagged = [dict(p, tile=tile_for(p, assign[size_class(p)])) for p in problems]
-    b = api.Batch(tagged)
+    b = api.Batch(tagged, kernel=kernel, ci_scaled=ci_scaled)
     for _ in range(2):
         b.step(0)
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -108,26 +123,34 @@ def _time_assignment(problems, assign: Dict[Tuple[int, int], Tile], reps: int) -
     return s.elapsed_time(e) / reps
 
 
-def tune(problems, candidates: Sequence[Tile] = CANDIDATES, reps: int = 5,
-         use_cache: bool = True, sweeps: int = 2) -> Dict[Tuple[int, int], Tile]:
+def tune(problems, candidates: Optional[Sequence[Tile]] = None, reps: int = 5,
+         use_cache: bool = True, sweeps: int = 2, kernel: str = "auto",
+         ci_scaled: bool = False) -> Dict[Tuple[int, int], Tile]:
     """Best tile per size class present in ``problems`` (cached).
 
     Coordinate descent on the whole batch: classes interact (they share the
-    persistent CTAs and the memory system), so each class's candidates are
-    timed with every other class held at its current choice, starting from the
-    library default, for ``sweeps`` passes over the classes.
+    GPU's CTAs and the memory system), so each class's candidates are timed
+    with every other class held at its current choice, starting from the
+    library default, for ``sweeps`` passes over the classes.  ``candidates``
+    defaults to the list of the kernel the batch runs (``kernel``, as for
+    :class:`api.Batch`).
     """
     if not problems:
         return {}
     dev = problems[0]["T"].device
     dtype = problems[0]["T"].dtype
+    kern = batch_kernel(problems, kernel, ci_scaled)
+    zm = kern == "zmarch"
+    if candidates is None:
+        candidates = ZMARCH_CANDIDATES if zm else CANDIDATES
+    start = ZMARCH_DEFAULT if zm else DEFAULT
     cache = _load_cache() if use_cache else {}
     classes = sorted({size_class(p) for p in problems})
-    keys = {cls: _key(dev, dtype, cls) for cls in classes}
+    keys = {cls: _key(dev, dtype, cls, kern, ci_scaled) for cls in classes}
     if all(keys[c] in cache for c in classes):
         return {c: tuple(cache[keys[c]]) for c in classes}
-    assign = {c: DEFAULT for c in classes}
-    best_t = _time_assignment(problems, assign, reps)
+    assign = {c: start for c in classes}
+    best_t = _time_assignment(problems, assign, reps, kernel, ci_scaled)
     for _ in range(sweeps):
         improved = False
         for c in classes:
@@ -136,7 +159,7 @@ def tune(problems, candidates: Sequence[Tile] = CANDIDATES, reps: int = 5,
                     continue
                 trial = dict(assign)
                 trial[c] = cand
-                t = _time_assignment(problems, trial, reps)
+                t = _time_assignment(problems, trial, reps, kernel, ci_scaled)
                 if t < best_t * 0.99:  # keep only clear wins
                     assign, best_t, improved = trial, t, True
         if not improved:
@@ -148,8 +171,8 @@ def tune(problems, candidates: Sequence[Tile] = CANDIDATES, reps: int = 5,
     return assign
 
 
-def tuned_batch(problems, **kw) -> api.Batch:
+def tuned_batch(problems, kernel: str = "auto", ci_scaled: bool = False, **kw) -> api.Batch:
     """A Batch whose problems carry the tuned tile of their size class."""
-    best = tune(problems, **kw)
+    best = tune(problems, kernel=kernel, ci_scaled=ci_scaled, **kw)
     tagged = [dict(p, tile=tile_for(p, best[size_class(p)])) for p in problems]
-    return api.Batch(tagged)
+    return api.Batch(tagged, kernel=kernel, ci_scaled=ci_scaled)

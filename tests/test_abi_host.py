@@ -110,25 +110,25 @@ def test_reductions_reject_bad_arguments(lib):
     assert lib.ps_diffusion3d_batch_step(A, 2, _lib.PS_F64, None) == _lib.PS_ERR_ARG
 
 
-def make_problems(sizes, base=0x100000000):
+def make_problems(sizes, base=0x100000000, pitch=0):
     arr = (_lib.PsProblem * len(sizes))()
     addr = base
     for q, n in enumerate(sizes):
-        nbytes = (n ** 3 * 8 + 4095) // 4096 * 4096
+        nbytes = ((pitch or n) * n * n * 8 + 4095) // 4096 * 4096
         T, T2, Ci = addr, addr + nbytes, addr + 2 * nbytes
         addr += 3 * nbytes
-        arr[q] = _lib.PsProblem(T, T2, Ci, 1.0, 1e-4, n - 1.0, n - 1.0, n - 1.0, n, n, n)
+        arr[q] = _lib.PsProblem(T, T2, Ci, 1.0, 1e-4, n - 1.0, n - 1.0, n - 1.0, n, n, n, 0, 0, 0, pitch)
     return arr
 
 
 ITEM = [("prob", "<i4"), ("i0", "<i4"), ("j0", "<i4"), ("k0", "<i4"), ("ni", "<i2"), ("nj", "<i2"),
-        ("nk", "<i2"), ("pad", "<i2")]
+        ("nk", "<i2"), ("kind", "<i2")]
 
 
 @pytest.mark.parametrize("own_tile", [False, True])
 def test_batch_table_layout(lib, own_tile):
-    """The table lists every interior node exactly once, largest items first;
-    a problem's own tile fields override the call's tile."""
+    """The column-march table lists every interior node exactly once, largest
+    items first; a problem's own tile fields override the call's tile."""
     import numpy as np
     sizes = [5, 33, 17, 40]
     arr = make_problems(sizes)
@@ -249,3 +249,43 @@ def test_selftest_rejects_out_of_range_arguments(lib):
     assert lib.ps_selftest_bounded_wait((1 << 24) + 1, 1000, None) == _lib.PS_ERR_ARG
     assert lib.ps_selftest_bounded_wait(16, 0, None) == _lib.PS_ERR_ARG
     assert lib.ps_selftest_bounded_wait(16, 2000000, None) == _lib.PS_ERR_ARG
+
+
+def have_driver(lib):
+    """True when the library can encode tensor maps (a GPU driver is present)."""
+    return lib.ps_diffusion3d_step_kernel(B, A, C, 1.0, 1e-3, 7.0, 7.0, 7.0, 64, 8, 8, _lib.PS_F64,
+                                          0).decode().startswith("k_zmarch")
+
+
+def test_batch_pitch_and_flags(lib):
+    """Row pitch in the problem records; pitch below nx, conflicting or unknown
+    flags, and PS_BATCH_CI_SCALED outside FP64 z-march tables are refused; without
+    a GPU driver (no tensor-map encoder) the automatic choice is the column march
+    and an explicit z-march request is refused."""
+    import numpy as np
+    arr = make_problems([9, 12], pitch=16)
+    nbytes = lib.ps_batch_table_bytes_ex(arr, 2, _lib.PS_F64, 0, 0, 0, 0)
+    assert nbytes > 0
+    buf = (ctypes.c_char * (nbytes + 64))()
+    off = (-ctypes.addressof(buf)) % 64
+    host = (ctypes.c_char * nbytes).from_buffer(buf, off)
+    assert lib.ps_batch_table_fill_ex(host, nbytes, arr, 2, _lib.PS_F64, 0, 0, 0, 0, None) == _lib.PS_OK
+    raw = bytes(host)
+    poff = int(np.frombuffer(raw[32:40], dtype=np.int64)[0])
+    if lib.ps_batch_table_kernel(host) == 0:  # the column record: 3 pointers, 4 doubles, nx ny nz, pitch
+        rec = np.frombuffer(raw[poff + 56:poff + 88], dtype=np.int64)
+        assert list(rec) == [9, 9, 9, 16]
+    bad = make_problems([9], pitch=8)
+    assert lib.ps_batch_table_fill_ex(host, nbytes, bad, 1, _lib.PS_F64, 0, 0, 0, 0, None) == _lib.PS_ERR_ARG
+    assert b"pitch" in lib.ps_last_error()
+    for flags, dtype in ((_lib.PS_BATCH_COLUMN | _lib.PS_BATCH_ZMARCH, _lib.PS_F64), (64, _lib.PS_F64),
+                         (_lib.PS_BATCH_CI_SCALED, _lib.PS_F32),
+                         (_lib.PS_BATCH_CI_SCALED | _lib.PS_BATCH_COLUMN, _lib.PS_F64)):
+        assert lib.ps_batch_table_fill_ex(host, nbytes, arr, 2, dtype, 0, 0, 0, flags, None) == _lib.PS_ERR_ARG
+    assert lib.ps_batch_table_kernel(None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_batch_step_ex(0x1000, None, 0, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_batch_run_ex(0x1000, None, 4, 0, None) == _lib.PS_ERR_ARG
+    if not have_driver(lib):
+        assert lib.ps_batch_table_kernel(host) == 0
+        st = lib.ps_batch_table_fill_ex(host, nbytes, arr, 2, _lib.PS_F64, 0, 0, 0, _lib.PS_BATCH_ZMARCH, None)
+        assert st == _lib.PS_ERR_UNSUPPORTED and b"encoder" in lib.ps_last_error()
