@@ -568,6 +568,7 @@ def secondary_metrics(torch, api, ag, inputs, log):
             t_b = timed(lambda: b.run(nt, graph=True), reps=2)
             out[f"batch_{name}{tag}_teff_gbs"] = round(bytes_per_step * nt / t_b / 1e9, 1)
             out[f"batch_{name}{tag}_tiles"] = {f"{lo}-{hi}": list(t)[2] for (lo, hi), t in sorted(best.items())}
+            out[f"batch_{name}{tag}_depth"] = 2 if b.temporal2 else 1  # tuned temporal-block depth
             del probs, b
             api.clear_graph_cache()
             torch.cuda.empty_cache()

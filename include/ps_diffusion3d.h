@@ -320,6 +320,11 @@ typedef struct {
 #define PS_BATCH_CI_SCALED 4u  /* PS_F64, z-march, equal spacings: each Ci holds the pre-scaled
                                   dt*lam*_dx^2*Ci (see ps_diffusion3d_scale_ci); one FP64
                                   multiply-add per node */
+#define PS_BATCH_TEMPORAL2 8u  /* z-march, PS_F32 or PS_F64 with PS_BATCH_CI_SCALED: the table
+                                  also lists two-steps-per-pass items (temporal blocking of
+                                  depth 2, the single-grid fused-pair kernel's tiles: 64 x 8
+                                  FP64, 128 x 8 FP32, the problem's tile_z planes) for
+                                  ps_diffusion3d_batch_run_ex with PS_RUN_TEMPORAL2 */
 
 /* Bytes of the table for these problems, tile shape and flags (tile_x,
  * tile_y: interior nodes per column-march item in x and y, tile_x*tile_y
@@ -341,10 +346,17 @@ int ps_batch_table_kernel(const void *host_table);
  * of the filled host buffer host_table, which the call reads on the host). */
 int ps_diffusion3d_batch_step_ex(const void *dev_table, const void *host_table, int parity,
                                  void *stream);
-/* nt batched steps with parity 0, 1, 0, ... (the buffers of problem p hold
- * its final state in T2 when nt is odd, in T when even).  Flags: PS_RUN_GRAPH
- * captures the nt launches once per (table address, item count, kernel, nt,
- * dtype) and replays them. */
+/* Two steps of every problem in one launch (a table built with
+ * PS_BATCH_TEMPORAL2): parity 0 reads T and writes T2, 1 the reverse.  Bit
+ * for bit two ps_diffusion3d_batch_step_ex calls, in one pass over HBM. */
+int ps_diffusion3d_batch_step2_ex(const void *dev_table, const void *host_table, int parity,
+                                  void *stream);
+/* nt batched steps (the buffers of problem p hold its final state in T2 when
+ * nt is odd, in T when even).  Flags: PS_RUN_GRAPH captures the launches once
+ * per (table address, item count, kernel, nt, dtype, pairs) and replays them;
+ * PS_RUN_TEMPORAL2 (a table built with PS_BATCH_TEMPORAL2) runs the steps as
+ * fused pairs, each launch swapping the buffers - where the pair count would
+ * leave the result in the other buffer, one pair runs as two single steps. */
 int ps_diffusion3d_batch_run_ex(const void *dev_table, const void *host_table, int nt,
                                 unsigned flags, void *stream);
 

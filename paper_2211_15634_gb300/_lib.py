@@ -28,6 +28,7 @@ PS_RUN_TEMPORAL2 = 16
 PS_BATCH_COLUMN = 1
 PS_BATCH_ZMARCH = 2
 PS_BATCH_CI_SCALED = 4
+PS_BATCH_TEMPORAL2 = 8
 
 STATUS_NAMES = {0: "PS_OK", -1: "PS_ERR_ARG", -2: "PS_ERR_ALIAS", -3: "PS_ERR_ALIGN",
                 -4: "PS_ERR_CUDA", -5: "PS_ERR_UNSUPPORTED"}
@@ -93,6 +94,7 @@ SIGNATURES = {
                                     ctypes.POINTER(_I64)]),
     "ps_batch_table_kernel": (_I, [_P]),
     "ps_diffusion3d_batch_step_ex": (_I, [_P, _P, _I, _P]),
+    "ps_diffusion3d_batch_step2_ex": (_I, [_P, _P, _I, _P]),
     "ps_diffusion3d_batch_run_ex": (_I, [_P, _P, _I, _U, _P]),
 }
 

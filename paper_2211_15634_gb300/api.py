@@ -338,12 +338,15 @@ class Batch:
     ``kernel``: "auto" (the TMA z-march when every problem can take it, else
     the column march), "zmarch" or "column".  ``ci_scaled``: FP64 problems
     whose ``Ci`` holds the pre-scaled ``dt*lam*_dx^2*Ci`` of :func:`scale_ci`
-    (equal spacings; z-march).  The chosen kernel is ``self.kernel``.
+    (equal spacings; z-march).  ``temporal2``: :meth:`run` steps in fused pairs
+    (temporal blocking of depth 2; z-march, FP32 or FP64 with ``ci_scaled``).
+    The chosen kernel is ``self.kernel``.
     """
 
     KERNELS = {"auto": 0, "column": _lib.PS_BATCH_COLUMN, "zmarch": _lib.PS_BATCH_ZMARCH}
 
-    def __init__(self, problems, tile=(0, 0, 0), kernel: str = "auto", ci_scaled: bool = False):
+    def __init__(self, problems, tile=(0, 0, 0), kernel: str = "auto", ci_scaled: bool = False,
+                 temporal2: bool = False):
         if not problems:
             raise ValueError("empty batch")
         if kernel not in self.KERNELS:
@@ -366,7 +369,9 @@ class Batch:
             arr[q] = _lib.PsProblem(p["T"].data_ptr(), p["T2"].data_ptr(), p["Ci"].data_ptr(),
                                     p["lam"], p["dt"], *p["inv_spacing"], nx, ny, nz, tx, ty, tz,
                                     pitches.pop())
-        flags = self.KERNELS[kernel] | (_lib.PS_BATCH_CI_SCALED if ci_scaled else 0)
+        flags = (self.KERNELS[kernel] | (_lib.PS_BATCH_CI_SCALED if ci_scaled else 0) |
+                 (_lib.PS_BATCH_TEMPORAL2 if temporal2 else 0))
+        self.temporal2 = temporal2
         nbytes = lib.ps_batch_table_bytes_ex(arr, len(problems), self.code, *tile, flags)
         # 64-byte aligned host buffer (the z-march table embeds tensor maps)
         raw = (ctypes.c_char * (nbytes + 64))()
@@ -388,9 +393,15 @@ class Batch:
         check(_lib.load().ps_diffusion3d_batch_step_ex(self.table.data_ptr(), self.host, int(parity),
                                                        torch.cuda.current_stream(self.device).cuda_stream))
 
+    def step2(self, parity: int) -> None:
+        """Two steps in one launch (a batch built with ``temporal2``)."""
+        check(_lib.load().ps_diffusion3d_batch_step2_ex(self.table.data_ptr(), self.host, int(parity),
+                                                        torch.cuda.current_stream(self.device).cuda_stream))
+
     def run(self, nt: int, graph: bool = True) -> None:
-        """nt steps; problem p's state ends in T2 when nt is odd, in T when even."""
-        flags = _lib.PS_RUN_GRAPH if graph else 0
+        """nt steps (fused pairs when built with ``temporal2``); problem p's state
+        ends in T2 when nt is odd, in T when even."""
+        flags = (_lib.PS_RUN_GRAPH if graph else 0) | (_lib.PS_RUN_TEMPORAL2 if self.temporal2 else 0)
         check(_lib.load().ps_diffusion3d_batch_run_ex(self.table.data_ptr(), self.host, int(nt), flags,
                                                       torch.cuda.current_stream(self.device).cuda_stream))
 

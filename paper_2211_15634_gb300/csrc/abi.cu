@@ -673,8 +673,12 @@ static const char *zmarch_refusal(const ps_problem &p, int dtype, bool scaled) {
 
 // Kernel of a table for these problems and flags: 0 column, 1 z-march, or an error status.
 static int choose_kernel(const ps_problem *probs, int nprob, int dtype, unsigned flags) {
-    if (flags & ~(PS_BATCH_COLUMN | PS_BATCH_ZMARCH | PS_BATCH_CI_SCALED))
+    if (flags & ~(PS_BATCH_COLUMN | PS_BATCH_ZMARCH | PS_BATCH_CI_SCALED | PS_BATCH_TEMPORAL2))
         return fail(PS_ERR_ARG, "unsupported batch flags 0x%x", flags);
+    if ((flags & PS_BATCH_TEMPORAL2) && (flags & PS_BATCH_COLUMN))
+        return fail(PS_ERR_ARG, "PS_BATCH_TEMPORAL2 needs the z-march kernel");
+    if ((flags & PS_BATCH_TEMPORAL2) && dtype == PS_F64 && !(flags & PS_BATCH_CI_SCALED))
+        return fail(PS_ERR_ARG, "PS_BATCH_TEMPORAL2 on FP64 needs PS_BATCH_CI_SCALED");
     if ((flags & PS_BATCH_COLUMN) && (flags & PS_BATCH_ZMARCH))
         return fail(PS_ERR_ARG, "PS_BATCH_COLUMN and PS_BATCH_ZMARCH exclude each other");
     const bool scaled = (flags & PS_BATCH_CI_SCALED) != 0;
@@ -685,7 +689,7 @@ static int choose_kernel(const ps_problem *probs, int nprob, int dtype, unsigned
     for (int q = 0; q < nprob; ++q) {
         const char *why = zmarch_refusal(probs[q], dtype, scaled);
         if (why) {
-            if ((flags & PS_BATCH_ZMARCH) || scaled)
+            if ((flags & (PS_BATCH_ZMARCH | PS_BATCH_TEMPORAL2)) || scaled)
                 return fail(PS_ERR_UNSUPPORTED, "problem %d: %s", q, why);
             return 0;
         }
@@ -699,27 +703,31 @@ static int64_t items_of(const ps_problem &p, int kernel, int dtype, int tx, int 
 }
 
 struct TableLayout {
-    size_t problems, zparams, maps, items, bytes;
+    size_t problems, zparams, z2params, maps, items, items2, bytes;
 };
 
-static TableLayout table_layout(int nprob, int64_t nitems, int kernel) {
+static TableLayout table_layout(int nprob, int64_t nitems, int64_t nitems2, int kernel) {
     TableLayout L{};
     L.problems = align_up(sizeof(BatchHeader), 128);
     size_t end = L.problems + align_up(sizeof(BatchProblem) * (size_t)nprob, 128);
     if (kernel == 1) {
         L.zparams = end;
         end += align_up(sizeof(ZParams) * (size_t)nprob, 128);
+        L.z2params = end;
+        end += align_up(batch_z2params_bytes() * (size_t)nprob, 128);
         L.maps = end;  // tensor maps want 64-byte alignment
         end += sizeof(CUtensorMap) * kBatchZmarchMaps * (size_t)nprob;
     }
     L.items = end;
-    L.bytes = end + sizeof(BatchItem) * (size_t)nitems;
+    end += sizeof(BatchItem) * (size_t)nitems;
+    L.items2 = end;
+    L.bytes = end + sizeof(BatchItem) * (size_t)nitems2;
     return L;
 }
 
 // Work items and layout of a table (status, or PS_OK with *nitems and *kernel set).
 static int plan_table(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y, int tile_z,
-                      unsigned flags, int64_t *nitems, int *kernel) {
+                      unsigned flags, int64_t *nitems, int64_t *nitems2, int *kernel) {
     if (!probs) return fail(PS_ERR_ARG, "probs is NULL");
     if (nprob < 1) return fail(PS_ERR_ARG, "nprob = %d < 1", nprob);
     PS_TRY(check_dtype(dtype));
@@ -734,25 +742,30 @@ static int plan_table(const ps_problem *probs, int nprob, int dtype, int tile_x,
     const int k = choose_kernel(probs, nprob, dtype, flags);
     if (k < 0) return k;
     PS_TRY(resolve_tiles(dtype, &tile_x, &tile_y, &tile_z, k));
-    int64_t n = 0;
+    int64_t n = 0, n2 = 0;
     for (int q = 0; q < nprob; ++q) {
         int tx, ty, tz;
         const int st = problem_tiles(probs[q], dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz, k);
         if (st != PS_OK) return fail(st, "problem %d: %s", q, g_err.c_str());
         n += items_of(probs[q], k, dtype, tx, ty, tz);
+        if (flags & PS_BATCH_TEMPORAL2)
+            n2 += batch_zmarch2_xy_tiles(dtype, probs[q].nx, probs[q].ny, nullptr) * ((probs[q].nz - 2 + tz - 1) / tz);
     }
-    if (k == 1 && n > 0x7fffffffLL) return fail(PS_ERR_ARG, "%lld work items: at most 2^31-1", (long long)n);
+    if (k == 1 && (n > 0x7fffffffLL || n2 > 0x7fffffffLL))
+        return fail(PS_ERR_ARG, "%lld work items: at most 2^31-1", (long long)std::max(n, n2));
     *nitems = n;
+    *nitems2 = n2;
     *kernel = k;
     return PS_OK;
 }
 
 size_t ps_batch_table_bytes_ex(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
                                int tile_z, unsigned flags) {
-    int64_t nitems = 0;
+    int64_t nitems = 0, nitems2 = 0;
     int kernel = 0;
-    if (plan_table(probs, nprob, dtype, tile_x, tile_y, tile_z, flags, &nitems, &kernel) != PS_OK) return 0;
-    return table_layout(nprob, nitems, kernel).bytes;
+    if (plan_table(probs, nprob, dtype, tile_x, tile_y, tile_z, flags, &nitems, &nitems2, &kernel) != PS_OK)
+        return 0;
+    return table_layout(nprob, nitems, nitems2, kernel).bytes;
 }
 
 size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int tile_x, int tile_y,
@@ -763,11 +776,11 @@ size_t ps_batch_table_bytes(const ps_problem *probs, int nprob, int dtype, int t
 int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs, int nprob, int dtype,
                            int tile_x, int tile_y, int tile_z, unsigned flags, int64_t *nitems_out) {
     if (!host_buf) return fail(PS_ERR_ARG, "host_buf is NULL");
-    int64_t nitems = 0;
+    int64_t nitems = 0, nitems2 = 0;
     int kernel = 0;
-    PS_TRY(plan_table(probs, nprob, dtype, tile_x, tile_y, tile_z, flags, &nitems, &kernel));
+    PS_TRY(plan_table(probs, nprob, dtype, tile_x, tile_y, tile_z, flags, &nitems, &nitems2, &kernel));
     PS_TRY(resolve_tiles(dtype, &tile_x, &tile_y, &tile_z, kernel));
-    const TableLayout L = table_layout(nprob, nitems, kernel);
+    const TableLayout L = table_layout(nprob, nitems, nitems2, kernel);
     if (bytes < L.bytes) return fail(PS_ERR_ARG, "table buffer has %zu bytes, needs %zu", bytes, L.bytes);
     if (kernel == 1 && ((uintptr_t)host_buf & 63u))
         return fail(PS_ERR_ALIGN, "host_buf must be 64-byte aligned for the tensor maps");
@@ -787,9 +800,13 @@ int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs
     h->zmode = kernel == 1 ? (dtype == PS_F32 ? Z_F32 : (scaled ? Z_F64_SCALED : Z_F64_EMU_ISO_DMUL)) : -1;
     h->zparams_offset = (int64_t)L.zparams;
     h->maps_offset = (int64_t)L.maps;
+    h->nitems2 = nitems2;
+    h->items2_offset = (int64_t)L.items2;
+    h->z2params_offset = (int64_t)L.z2params;
     BatchProblem *bp = (BatchProblem *)(base + L.problems);
-    std::vector<std::pair<int64_t, BatchItem>> work;
+    std::vector<std::pair<int64_t, BatchItem>> work, work2;
     work.reserve((size_t)nitems);
+    work2.reserve((size_t)nitems2);
     for (int q = 0; q < nprob; ++q) {
         const ps_problem &p = probs[q];
         const StepCoef c = make_coef(p.lam, p.dt, p._dx, p._dy, p._dz);
@@ -825,6 +842,7 @@ int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs
         problem_tiles(p, dtype, tile_x, tile_y, tile_z, &tx, &ty, &tz, kernel);
         if (kernel == 1) {
             if (!batch_zmarch_fill(base + L.zparams + sizeof(ZParams) * q,
+                                   base + L.z2params + batch_z2params_bytes() * q,
                                    base + L.maps + sizeof(CUtensorMap) * kBatchZmarchMaps * q, r, c,
                                    dtype))
                 return fail(PS_ERR_UNSUPPORTED, "problem %d: tensor-map encoding failed", q);
@@ -841,6 +859,19 @@ int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs
                     it.nk = (int16_t)std::min<int64_t>(tz, p.nz - 1 - k0);
                     work.push_back({0, it});
                 }
+            if (nitems2) {  // the fused-pair list: wide tiles only, the same z-chunks
+                std::vector<BatchItem> xy2((size_t)batch_zmarch2_xy_tiles(dtype, p.nx, p.ny, nullptr));
+                batch_zmarch2_xy_tiles(dtype, p.nx, p.ny, xy2.data());
+                for (int64_t k0 = 1; k0 < p.nz - 1; k0 += tz)
+                    for (const BatchItem &t : xy2) {
+                        BatchItem it = t;
+                        it.prob = q;
+                        it.k0 = (int32_t)k0;
+                        it.ni = it.nj = 0;
+                        it.nk = (int16_t)std::min<int64_t>(tz, p.nz - 1 - k0);
+                        work2.push_back({0, it});
+                    }
+            }
             continue;
         }
         for (int64_t k0 = 1; k0 < p.nz - 1; k0 += tz)
@@ -862,12 +893,13 @@ int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs
         // by size measured 32% extra DRAM reads on the 256-problem workload)
         std::vector<int64_t> pbytes(nprob);
         for (int q = 0; q < nprob; ++q) pbytes[q] = probs[q].nx * probs[q].ny * probs[q].nz;
-        std::stable_sort(work.begin(), work.end(),
-                         [&](const std::pair<int64_t, BatchItem> &a, const std::pair<int64_t, BatchItem> &b) {
-                             const int64_t sa = pbytes[a.second.prob], sb = pbytes[b.second.prob];
-                             if (sa != sb) return sa > sb;
-                             return a.second.prob < b.second.prob;
-                         });
+        auto by_problem = [&](const std::pair<int64_t, BatchItem> &a, const std::pair<int64_t, BatchItem> &b) {
+            const int64_t sa = pbytes[a.second.prob], sb = pbytes[b.second.prob];
+            if (sa != sb) return sa > sb;
+            return a.second.prob < b.second.prob;
+        };
+        std::stable_sort(work.begin(), work.end(), by_problem);
+        std::stable_sort(work2.begin(), work2.end(), by_problem);
     } else {
         // column march: largest items first, so the persistent CTAs' round-robin
         // hand-out stays balanced (measured 13% faster than the problem order above)
@@ -878,6 +910,8 @@ int ps_batch_table_fill_ex(void *host_buf, size_t bytes, const ps_problem *probs
     }
     BatchItem *items = (BatchItem *)(base + L.items);
     for (size_t t = 0; t < work.size(); ++t) items[t] = work[t].second;
+    BatchItem *items2 = (BatchItem *)(base + L.items2);
+    for (size_t t = 0; t < work2.size(); ++t) items2[t] = work2[t].second;
     if (nitems_out) *nitems_out = nitems;
     return PS_OK;
 }
@@ -917,6 +951,17 @@ int ps_diffusion3d_batch_step_ex(const void *dev_table, const void *host_table, 
     return PS_OK;
 }
 
+int ps_diffusion3d_batch_step2_ex(const void *dev_table, const void *host_table, int parity, void *stream) {
+    if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
+    BatchHeader h;
+    PS_TRY(batch_header(host_table, &h));
+    if (parity != 0 && parity != 1) return fail(PS_ERR_ARG, "parity %d is not 0 or 1", parity);
+    if (h.nitems2 < 1) return fail(PS_ERR_ARG, "the table was not built with PS_BATCH_TEMPORAL2");
+    cudaError_t e = launch_batch_zmarch2(dev_table, h.nitems2, h.dtype, parity, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_batch_step2_ex");
+    return PS_OK;
+}
+
 int ps_diffusion3d_batch_step(const void *dev_table, int parity, int dtype, void *stream) {
     if (!dev_table) return fail(PS_ERR_ARG, "dev_table is NULL");
     PS_TRY(check_dtype(dtype));
@@ -926,21 +971,44 @@ int ps_diffusion3d_batch_step(const void *dev_table, int parity, int dtype, void
     return PS_OK;
 }
 
+// nt steps as launches: fused pairs (PS_RUN_TEMPORAL2) then single steps, each
+// launch swapping the buffers; an odd pair count would leave the result in the
+// wrong buffer, so then one pair runs as two single steps
+static cudaError_t enqueue_batch_run(const void *dev_table, const BatchHeader &h, int nt, bool pairs,
+                                     cudaStream_t s) {
+    int m = pairs ? nt / 2 : 0, r = nt - 2 * m;
+    if (m & 1) {
+        m -= 1;
+        r += 2;
+    }
+    int launch = 0;
+    for (int i = 0; i < m; ++i, ++launch) {
+        cudaError_t e = launch_batch_zmarch2(dev_table, h.nitems2, h.dtype, launch & 1, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int i = 0; i < r; ++i, ++launch) {
+        cudaError_t e = enqueue_batch(dev_table, h, launch & 1, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static int batch_run(const void *dev_table, const BatchHeader &h, int nt, unsigned flags, cudaStream_t s) {
     if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
-    if (flags & ~PS_RUN_GRAPH) return fail(PS_ERR_ARG, "unsupported flags 0x%x", flags);
+    if (flags & ~(PS_RUN_GRAPH | PS_RUN_TEMPORAL2)) return fail(PS_ERR_ARG, "unsupported flags 0x%x", flags);
+    const bool pairs = (flags & PS_RUN_TEMPORAL2) != 0;
+    if (pairs && h.nitems2 < 1)
+        return fail(PS_ERR_ARG, "PS_RUN_TEMPORAL2 needs a table built with PS_BATCH_TEMPORAL2");
     if (h.kernel == 0) batch_prepare(h.dtype);
     if (!(flags & PS_RUN_GRAPH)) {
-        for (int it = 0; it < nt; ++it) {
-            cudaError_t e = enqueue_batch(dev_table, h, it & 1, s);
-            if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_batch_run");
-        }
+        cudaError_t e = enqueue_batch_run(dev_table, h, nt, pairs, s);
+        if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_batch_run");
         return PS_OK;
     }
     // the table's work-item count and kernel are part of the key: the z-march launch
     // size is baked into the graph (a new table may reuse a freed table's address)
     const GraphKey key{current_device(), dev_table, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0,
-                       0.0, h.nitems, h.zmode, h.kernel, nt, h.dtype, 0x80000000u};
+                       0.0, h.nitems, h.zmode, h.kernel, nt, h.dtype, 0x80000000u | (pairs ? 1u : 0u)};
     std::lock_guard<std::mutex> lock(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
@@ -949,8 +1017,7 @@ static int batch_run(const void *dev_table, const BatchHeader &h, int nt, unsign
         if (e != cudaSuccess) return cuda_fail(e, "capture stream");
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        cudaError_t le = cudaSuccess;
-        for (int t = 0; t < nt && le == cudaSuccess; ++t) le = enqueue_batch(dev_table, h, t & 1, cs);
+        const cudaError_t le = enqueue_batch_run(dev_table, h, nt, pairs, cs);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cs, &graph);
         if (le != cudaSuccess) {

@@ -24,6 +24,7 @@
 
 #include "internal.h"
 #include "zmarch.h"
+#include "zmarch2_tile.cuh"
 #include "zmarch_tile.cuh"
 
 namespace psd {
@@ -81,7 +82,42 @@ int64_t batch_zmarch_xy_tiles(int dtype, int64_t nx, int64_t ny, BatchItem *out)
     return n;
 }
 
-bool batch_zmarch_fill(void *zparams_dst, void *maps_dst, const BatchProblem &r, StepCoef c, int dtype) {
+// Fused step pairs (temporal blocking of depth 2): one CTA per item of the second work
+// list, the fused-pair tile body of the single-grid kernel (zmarch2_tile.cuh).
+template <typename E>
+__global__ void __launch_bounds__(256, Z2Ring<E>::MINB)
+k_batch_zmarch2(const char *__restrict__ table, int parity) {
+    const BatchHeader *h = (const BatchHeader *)table;
+    const BatchItem item = ((const BatchItem *)(table + h->items2_offset))[blockIdx.x];
+    __shared__ Z2Params s_p;
+    if (threadIdx.x == 0) s_p = ((const Z2Params *)(table + h->z2params_offset))[item.prob];
+    __syncthreads();
+    const BatchProblem *P = (const BatchProblem *)(table + h->problems_offset) + item.prob;
+    const CUtensorMap *maps =
+        (const CUtensorMap *)(table + h->maps_offset) + kBatchZmarchMaps * item.prob + 6;
+    E *out = (E *)(parity ? P->T : P->T2);
+    zmarch2_tile<E, 8, Z2Ring<E>::NT, Z2Ring<E>::NC>(maps + (parity ? 1 : 0), maps + 2, out, s_p, item.i0,
+                                                     item.j0, item.k0, item.k0 + item.nk,
+                                                     &g_batchz_error);
+}
+
+int64_t batch_zmarch2_xy_tiles(int dtype, int64_t nx, int64_t ny, BatchItem *out) {
+    const int64_t bx = dtype == PS_F64 ? 64 : 128, by = 8;
+    int64_t n = 0;
+    for (int64_t y0 = 0; y0 < ny - 1; y0 += by)
+        for (int64_t x0 = 0; x0 < nx - 1; x0 += bx, ++n)
+            if (out) {
+                out[n].i0 = (int32_t)x0;
+                out[n].j0 = (int32_t)y0;
+                out[n].kind = 2;
+            }
+    return n;
+}
+
+size_t batch_z2params_bytes() { return sizeof(Z2Params); }
+
+bool batch_zmarch_fill(void *zparams_dst, void *z2params_dst, void *maps_dst, const BatchProblem &r,
+                       StepCoef c, int dtype) {
     const int esz = dtype == PS_F64 ? 8 : 4;
     const int px = dtype == PS_F64 ? 2 : 4;
     const Grid3 g{r.nx, r.ny, r.nz};
@@ -98,6 +134,21 @@ bool batch_zmarch_fill(void *zparams_dst, void *maps_dst, const BatchProblem &r,
              make_tensor_map_3d_pitch(&m[3 * v + 1], r.T2, esz, g, r.pitch, W, H) &&
              make_tensor_map_3d_pitch(&m[3 * v + 2], r.Ci, esz, g, r.pitch, (unsigned)bx, (unsigned)by);
     }
+    // fused pairs: T box with a 2-row y halo, Ci box with a 1-row one, both 16-byte x halos
+    Z2Params z2{};
+    z2.nx = r.nx;
+    z2.ny = r.ny;
+    z2.nz = r.nz;
+    z2.pitch = r.pitch;
+    z2.dtlam = (float)c.dtlam;
+    z2.ax = (float)c.ax;
+    z2.ay = (float)c.ay;
+    z2.az = (float)c.az;
+    *(Z2Params *)z2params_dst = z2;
+    const unsigned W2 = (unsigned)(32 * px + 2 * (16 / esz));
+    ok = ok && make_tensor_map_3d_pitch(&m[6], r.T, esz, g, r.pitch, W2, 12) &&
+         make_tensor_map_3d_pitch(&m[7], r.T2, esz, g, r.pitch, W2, 12) &&
+         make_tensor_map_3d_pitch(&m[8], r.Ci, esz, g, r.pitch, W2, 10);
     return ok;
 }
 
@@ -136,6 +187,32 @@ cudaError_t launch_batch_zmarch(const void *dev_table, int64_t nitems, int zmode
         case Z_F64_SCALED: return launch_bz_t<Z_F64_SCALED>(dev_table, nitems, parity, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <typename E>
+static cudaError_t launch_bz2_t(const void *dev_table, int64_t nitems2, int parity, cudaStream_t s) {
+    constexpr int BY = 8, NT = Z2Ring<E>::NT, NC = Z2Ring<E>::NC, PX = Z2Traits<E>::PX,
+                  HX = 16 / (int)sizeof(E), BX = 32 * PX, W = BX + 2 * HX;
+    constexpr unsigned TBA = (W * (BY + 4) * sizeof(E) + 127) / 128 * 128;
+    constexpr unsigned CBA = (W * (BY + 2) * sizeof(E) + 127) / 128 * 128;
+    constexpr size_t smem = NT * TBA + (NC + 2) * CBA + (NT + NC) * 8;
+    static bool attr_done[64] = {false};
+    const int dev = current_device();
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_zmarch2<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    if (nitems2 < 1 || nitems2 > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_batch_zmarch2<E><<<(unsigned)nitems2, 32 * BY, smem, s>>>((const char *)dev_table, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_zmarch2(const void *dev_table, int64_t nitems2, int dtype, int parity,
+                                 cudaStream_t s) {
+    if (dtype == PS_F64) return launch_bz2_t<double>(dev_table, nitems2, parity, s);
+    return launch_bz2_t<float>(dev_table, nitems2, parity, s);
 }
 
 unsigned batch_zmarch_device_error(bool clear) {

@@ -100,6 +100,9 @@ struct BatchHeader {
     // zmode, with a ZParams record and three tensor maps per problem at these offsets
     int32_t kernel, zmode;
     int64_t zparams_offset, maps_offset;
+    // z-march tables built for fused step pairs (PS_BATCH_TEMPORAL2): a second work list
+    // of two-steps-per-pass items and a Z2Params record per problem (else nitems2 = 0)
+    int64_t nitems2, items2_offset, z2params_offset;
 };
 struct BatchProblem {
     void *T;
@@ -126,8 +129,14 @@ unsigned batch_device_error(bool clear);
 // x-y tiles of the z-march over an nx x ny plane: (x0, y0, kind) into out[i].i0/.j0/.kind
 // when out is not null; returns their number
 int64_t batch_zmarch_xy_tiles(int dtype, int64_t nx, int64_t ny, BatchItem *out);
-constexpr int kBatchZmarchMaps = 6;  // tensor maps per problem
-bool batch_zmarch_fill(void *zparams_dst, void *maps_dst, const BatchProblem &r, StepCoef c, int dtype);
+// fused-pair tiles (one width, 8 rows), kind 2; returns their number
+int64_t batch_zmarch2_xy_tiles(int dtype, int64_t nx, int64_t ny, BatchItem *out);
+constexpr int kBatchZmarchMaps = 9;  // tensor maps per problem (wide, narrow, fused pair)
+bool batch_zmarch_fill(void *zparams_dst, void *z2params_dst, void *maps_dst, const BatchProblem &r,
+                       StepCoef c, int dtype);
+size_t batch_z2params_bytes();
+cudaError_t launch_batch_zmarch2(const void *dev_table, int64_t nitems2, int dtype, int parity,
+                                 cudaStream_t s);
 cudaError_t launch_batch_zmarch(const void *dev_table, int64_t nitems, int zmode, int parity,
                                 cudaStream_t s);
 unsigned batch_zmarch_device_error(bool clear);

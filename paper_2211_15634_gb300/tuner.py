@@ -5,10 +5,14 @@ the batched kernel is timed (CUDA events, a few steps after warm-up) on the
 whole batch with every candidate work-item shape (tile_x, tile_y, tile_z) for
 that class, and the fastest shape is kept.  The candidates depend on the kernel
 the batch runs: the column march takes x-y tiles and z-chunks, the TMA z-march
-(fixed x-y tiles) its z-chunk length.  Results are cached as JSON keyed by GPU
-name, dtype, kernel and size class (file ``$PS_TUNER_CACHE`` or
+(fixed x-y tiles) its z-chunk length.  For a z-march batch that can run fused
+step pairs (FP32, or FP64 on the pre-scaled coefficient) the temporal-block
+depth (1 or 2 steps per pass) is then chosen for the whole batch by timing both
+with the tuned z-chunks.  Results are cached as JSON keyed by GPU name, dtype,
+kernel and size class (and "depth"; file ``$PS_TUNER_CACHE`` or
 ``~/.cache/psdiff/tuner.json``), so later runs reuse them without timing.
-``tuned_batch`` builds the final table with each problem's class shape.
+``tuned_batch`` builds the final table with each problem's class shape and the
+chosen depth.
 """
 from __future__ import annotations
 
@@ -171,8 +175,56 @@ def tune(problems, candidates: Optional[Sequence[Tile]] = None, reps: int = 5,
     return assign
 
 
-def tuned_batch(problems, kernel: str = "auto", ci_scaled: bool = False, **kw) -> api.Batch:
-    """A Batch whose problems carry the tuned tile of their size class."""
+def _time_pairs(problems, assign, reps: int, kernel: str, ci_scaled: bool) -> float:
+    """Milliseconds per step with fused pairs (one launch per two steps)."""
+    tagged = [dict(p, tile=tile_for(p, assign[size_class(p)])) for p in problems]
+    b = api.Batch(tagged, kernel=kernel, ci_scaled=ci_scaled, temporal2=True)
+    for _ in range(2):
+        b.step2(0)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for i in range(reps):
+        b.step2(i & 1)
+    e.record()
+    e.synchronize()
+    return s.elapsed_time(e) / (2 * reps)
+
+
+def pairs_possible(problems, kernel: str = "auto", ci_scaled: bool = False) -> bool:
+    """Whether these problems can run fused step pairs on the z-march."""
+    if batch_kernel(problems, kernel, ci_scaled) != "zmarch":
+        return False
+    return problems[0]["T"].dtype == torch.float32 or ci_scaled
+
+
+def tune_depth(problems, reps: int = 5, use_cache: bool = True, kernel: str = "auto",
+               ci_scaled: bool = False, **kw) -> int:
+    """Temporal-block depth (1 or 2 steps per pass) for the whole batch, timed with
+    each class's tuned z-chunk (cached)."""
+    if not problems or not pairs_possible(problems, kernel, ci_scaled):
+        return 1
+    dev = problems[0]["T"].device
+    dtype = problems[0]["T"].dtype
+    key = _key(dev, dtype, ("depth", "all"), "zmarch", ci_scaled)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return int(cache[key][0])
+    assign = tune(problems, reps=reps, use_cache=use_cache, kernel=kernel, ci_scaled=ci_scaled, **kw)
+    t1 = _time_assignment(problems, assign, reps, kernel, ci_scaled)
+    t2 = _time_pairs(problems, assign, reps, kernel, ci_scaled)
+    depth = 2 if t2 < 0.99 * t1 else 1  # keep only a clear win
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = [depth]
+        _save_cache(cache)
+    return depth
+
+
+def tuned_batch(problems, kernel: str = "auto", ci_scaled: bool = False, depth=None, **kw) -> api.Batch:
+    """A Batch whose problems carry the tuned tile of their size class, stepping at the
+    tuned temporal-block depth (``depth`` = 1 or 2 overrides it)."""
     best = tune(problems, kernel=kernel, ci_scaled=ci_scaled, **kw)
+    if depth is None:
+        depth = tune_depth(problems, kernel=kernel, ci_scaled=ci_scaled, **kw)
     tagged = [dict(p, tile=tile_for(p, best[size_class(p)])) for p in problems]
-    return api.Batch(tagged, kernel=kernel, ci_scaled=ci_scaled)
+    return api.Batch(tagged, kernel=kernel, ci_scaled=ci_scaled, temporal2=depth == 2)

@@ -244,3 +244,91 @@ def test_zmarch_table_covers_every_interior_node_once(dtype):
     assert sorted(seen) == list(range(len(shapes)))  # each problem's items are contiguous
     vols = [np.prod(shapes[q]) for q in seen]
     assert vols == sorted(vols, reverse=True)
+
+
+# ------------------------------------------------------------ fused step pairs
+def pair_problems(dtype, shapes, seed0=4000):
+    """Pitched problems; FP64 ones on the pre-scaled coefficient (pairs need it)."""
+    probs, host = make_batch_problems(shapes, dtype, pitched=True, seed0=seed0)
+    if dtype == torch.float64:
+        for p in probs:
+            p["Ci"] = api.pitched_copy(api.scale_ci(p["Ci"].contiguous(), p["lam"], p["dt"], p["inv_spacing"]))
+    return probs, host
+
+
+PAIR_SHAPES = [(3, 3, 3), (17, 17, 17), (33, 33, 33), (64, 20, 9), (67, 70, 12), (130, 9, 33),
+               (161, 12, 10)]
+
+
+def reset(probs, host, dtype):
+    for p, (T0, *_r) in zip(probs, host):
+        p["T"].copy_(to_dev(T0, dtype))
+        p["T2"].copy_(p["T"])
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_pairs_equal_single_steps(dtype, graph):
+    """Fused pairs give bit for bit the single steps, whatever the pair count's
+    parity (an odd count runs one pair as two steps) and the z-chunk length."""
+    scaled = dtype == torch.float64
+    probs, host = pair_problems(dtype, PAIR_SHAPES)
+    one = api.Batch(probs, ci_scaled=scaled)
+    two = api.Batch(probs, tile=(0, 0, 5), ci_scaled=scaled, temporal2=True)
+    for nt in (1, 2, 3, 4, 5, 6, 7):
+        reset(probs, host, dtype)
+        one.run(nt, graph=graph)
+        ref = [one.result(q, nt).clone() for q in range(len(probs))]
+        reset(probs, host, dtype)
+        two.run(nt, graph=graph)
+        for q in range(len(probs)):
+            assert torch.equal(two.result(q, nt), ref[q]), (nt, q)
+    assert api.device_error() == 0
+    api.clear_graph_cache()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batch_step2_is_two_steps(dtype):
+    scaled = dtype == torch.float64
+    probs, host = pair_problems(dtype, PAIR_SHAPES[:4])
+    b = api.Batch(probs, ci_scaled=scaled, temporal2=True)
+    b.step(0)
+    b.step(1)
+    ref = [p["T"].clone() for p in probs]
+    reset(probs, host, dtype)
+    b.step2(0)  # T -> T2 after two steps
+    for q, p in enumerate(probs):
+        assert torch.equal(p["T2"], ref[q]), q
+
+
+def test_batch_pairs_refusals():
+    p64, _ = make_batch_problems([(32, 32, 32)], torch.float64, pitched=True)
+    with pytest.raises(_lib.PsError):
+        api.Batch(p64, temporal2=True)  # FP64 pairs run on the pre-scaled coefficient only
+    p32, _ = make_batch_problems([(32, 32, 32)], torch.float32, pitched=True)
+    with pytest.raises(_lib.PsError):
+        api.Batch(p32, kernel="column", temporal2=True)
+    b = api.Batch(p32)
+    lib = _lib.load()
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.ps_diffusion3d_batch_run_ex(b.table.data_ptr(), b.host, 4, _lib.PS_RUN_TEMPORAL2, s) == \
+        _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_batch_step2_ex(b.table.data_ptr(), b.host, 0, s) == _lib.PS_ERR_ARG
+
+
+def test_tuned_depth_is_cached_and_correct(tmp_path, monkeypatch):
+    import json
+    monkeypatch.setenv("PS_TUNER_CACHE", str(tmp_path / "tuner.json"))
+    nt = 6
+    probs, host = pair_problems(torch.float32, [(40, 40, 40), (90, 90, 90), (131, 131, 131)])
+    depth = tuner.tune_depth(probs, reps=2)
+    assert depth in (1, 2)
+    cache = json.load(open(tmp_path / "tuner.json"))
+    assert [v for k, v in cache.items() if "depth" in k] == [[depth]]
+    reset(probs, host, torch.float32)
+    b = tuner.tuned_batch(probs, reps=2)
+    assert b.temporal2 == (depth == 2)
+    b.run(nt, graph=False)
+    for q, (T0, Ci, lam, dt, inv) in enumerate(host):
+        ref = oracle.run(T0, Ci, lam, dt, *inv, nt)
+        assert np.max(np.abs(to_host(b.result(q, nt)) - ref)) <= f32_tol(nt, T0) + 1e-30
