@@ -429,7 +429,8 @@ KERNEL_SOURCES = {
     "k_zmarch": ["paper_2211_15634_gb300/csrc/zmarch.cu", "paper_2211_15634_gb300/csrc/zmarch_tile.cuh",
                  "paper_2211_15634_gb300/csrc/zmarch.h", "paper_2211_15634_gb300/csrc/emu64.cuh",
                  "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],
-    "k_zmarch2": ["paper_2211_15634_gb300/csrc/zmarch2.cu", "paper_2211_15634_gb300/csrc/emu64.cuh",
+    "k_zmarch2": ["paper_2211_15634_gb300/csrc/zmarch2.cu", "paper_2211_15634_gb300/csrc/zmarch2_tile.cuh",
+                  "paper_2211_15634_gb300/csrc/emu64.cuh",
                   "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],
     "k_step_basic_emu": ["paper_2211_15634_gb300/csrc/stencil_basic.cuh",
                          "paper_2211_15634_gb300/csrc/emu64.cuh"],
