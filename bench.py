@@ -534,11 +534,8 @@ def secondary_metrics(torch, api, ag, inputs, log):
         Cf, scaled = ag.coefficient(Cd, 1.0, dt, inv)
         t_fwd = timed(lambda: api.run(fa, fb, Cf, 1.0, dt, inv, nt, graph=True, ci_scaled=scaled))
         out[f"fwd_256_{name}_ms"] = round(1e3 * t_fwd, 2)
-        for tag, every in (("sqrt_nt", None), ("all_states", 1)):
-            t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt, every=every), reps=2)
-            out[f"grad_over_fwd_256_{name}_{tag}"] = round(t_grad / t_fwd, 3)
-            torch.cuda.empty_cache()
-        # the transposed step alone (CUDA events, warm)
+        # the transposed step alone (CUDA events, warm), before the gradient runs: releasing
+        # their 13-27 GB state block slows later kernels on older buffers by a third
         ybar = Td - Td.mean()
         Tbar, Cib = torch.empty_like(Td), torch.zeros_like(Td)
         def adj10():
@@ -547,6 +544,10 @@ def secondary_metrics(torch, api, ag, inputs, log):
         t_adj = timed(adj10, reps=3) / 10
         out[f"adjoint_256_{name}_ms"] = round(1e3 * t_adj, 4)
         out[f"adjoint_256_{name}_gbs"] = round(6 * n ** 3 * Td.element_size() / t_adj / 1e9, 1)
+        for tag, every in (("sqrt_nt", None), ("all_states", 1)):
+            t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt, every=every), reps=2)
+            out[f"grad_over_fwd_256_{name}_{tag}"] = round(t_grad / t_fwd, 3)
+            torch.cuda.empty_cache()
         del Td, Ctd, Cd, Cf, a, b, Tobs, fa, fb, ybar, Tbar, Cib
         api.clear_graph_cache()
         torch.cuda.empty_cache()
