@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--no-secondary", action="store_true", help="skip FP32 / gradient / batch lines")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--kernel-loop", choices=["step", "adjoint", "batch"], default=None,
+    p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint2", "batch"], default=None,
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON)")
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     p.add_argument("--reps", type=int, default=4)
@@ -92,6 +92,17 @@ def run_kernel_loop(args):
                 api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
         name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled,
                                     temporal2=args.temporal2)
+    elif args.kernel_loop == "adjoint2":
+        # FP32: two transposed steps per pass (states T and T2)
+        if args.dtype != "f32":
+            raise SystemExit("--kernel-loop adjoint2 is FP32 (--dtype f32)")
+        ybar = T2 - T.mean()
+        Tbar = torch.empty_like(T)
+        Cib = torch.zeros_like(T)
+        S0 = T.clone()
+        for _ in range(args.reps):
+            api.adjoint2(Tbar, Cib, ybar, T, S0, C, 1.0, dt, inv)
+        name = "adjoint2 (fused pair)"
     else:
         # FP64: the transposed step on the pre-scaled coefficient (--plain-ci: on Ci)
         scaled = args.dtype == "f64" and not args.plain_ci

@@ -225,6 +225,19 @@ int ps_diffusion3d_adjoint_ex(void *Tbar, void *Cibar, const void *ybar, const v
                               double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
                               unsigned flags, void *stream);
 
+/* Two transposed steps in one pass (temporal blocking of depth 2 of the
+ * reverse sweep): with ybar = dL/dT_{t+2}, T_first = T_{t+1} and T_second =
+ * T_t (the inputs of steps t+1 and t), Tbar := dL/dT_t and Cibar accumulates
+ * both steps' terms - bit for bit two ps_diffusion3d_adjoint calls (the first
+ * with T_first, the second with T_second on its output), without the
+ * intermediate field leaving the chip.  PS_F32 only (PS_ERR_UNSUPPORTED for
+ * PS_F64, whose step is bound by instruction issue, or when nx*4 is not a
+ * multiple of 16); flags must be 0.  Same aliasing rules as the one-step call. */
+int ps_diffusion3d_adjoint2_ex(void *Tbar, void *Cibar, const void *ybar, const void *T_first,
+                               const void *T_second, const void *Ci, double lam, double dt, double _dx,
+                               double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                               unsigned flags, void *stream);
+
 /* ---------------------------------------------------------------------
  * Reductions in FP64 (deterministic: a fixed partition and a fixed
  * summation order, independent of timing).  A, B are device arrays of n

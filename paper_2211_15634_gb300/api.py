@@ -212,6 +212,24 @@ def adjoint(Tbar, Cibar, ybar, T, Ci, lam: float, dt: float, inv_spacing, *,
         _lib.PS_RUN_CI_SCALED if ci_scaled else 0, _stream(T)))
 
 
+def adjoint2(Tbar, Cibar, ybar, T_first, T_second, Ci, lam: float, dt: float, inv_spacing) -> None:
+    """Two transposed steps in one pass (FP32): with ybar = dL/dT_{t+2} and the
+    states T_first = T_{t+1}, T_second = T_t, Tbar := dL/dT_t and Cibar accumulates
+    both steps' terms, bit for bit two :func:`adjoint` calls."""
+    code = _code(T_first)
+    _same(T_first, T_second, Tbar, Cibar, ybar, Ci)
+    nx, ny, nz = _grid(T_first)
+    check(_lib.load().ps_diffusion3d_adjoint2_ex(
+        _field(Tbar, "Tbar", code), _field(Cibar, "Cibar", code), _field(ybar, "ybar", code),
+        _field(T_first, "T_first", code), _field(T_second, "T_second", code), _field(Ci, "Ci", code),
+        lam, dt, *inv_spacing, nx, ny, nz, code, 0, _stream(T_first)))
+
+
+def adjoint2_supported(T) -> bool:
+    """Whether :func:`adjoint2` takes fields shaped and typed like ``T``."""
+    return T.dtype == torch.float32 and T.shape[2] % 4 == 0
+
+
 def maximum_async(A, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """max(A) into a 0-dim float64 device tensor (no synchronization)."""
     code = _code(A)

@@ -12,6 +12,9 @@ maximum(Ci)).  Memory: about ``nt/every + every + 2`` fields.
 On FP64 grids with equal spacings every kernel runs on the pre-scaled
 coefficient Cs = dt*lam*_dx^2*Ci (one FP64 multiply-add per node forward);
 the sweep then accumulates dL/dCs and returns dL/dCi = dt*lam*_dx^2 * dL/dCs.
+With ``pairs=True`` (FP32 grids) the reverse sweep takes the transposed steps
+two at a time (``api.adjoint2``: one pass over HBM per pair, bit for bit two
+single steps; measured no faster than single steps on GB300, so off by default).
 """
 from __future__ import annotations
 
@@ -50,9 +53,11 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
     return cur, ckpts
 
 
-def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None):
-    """Reverse sweep; returns (dL/dT0, dL/dCi)."""
+def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None):
+    """Reverse sweep; returns (dL/dT0, dL/dCi).  ``pairs``: take the transposed
+    steps two per launch where ``api.adjoint2`` applies (default off)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
+    pairs = bool(pairs) and not scaled and api.adjoint2_supported(ybar_nt)
     ybar = ybar_nt.contiguous().clone()
     tbar = torch.empty_like(ybar)
     cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
@@ -65,8 +70,14 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
         if t1 - t0 > 1:  # states t0+1 .. t1-1 from the checkpoint, every one kept
             api.run_states(ckpts[s], seg, 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
         states = [ckpts[s]] + seg.grids[:t1 - t0 - 1]
-        for t in range(t1 - 1, t0 - 1, -1):
-            api.adjoint(tbar, cibar, ybar, states[t - t0], C, lam, dt, inv, ci_scaled=scaled)
+        t = t1 - 1
+        while t >= t0:
+            if pairs and t - 1 >= t0:  # steps t and t-1 in one pass
+                api.adjoint2(tbar, cibar, ybar, states[t - t0], states[t - 1 - t0], C, lam, dt, inv)
+                t -= 2
+            else:
+                api.adjoint(tbar, cibar, ybar, states[t - t0], C, lam, dt, inv, ci_scaled=scaled)
+                t -= 1
             ybar, tbar = tbar, ybar
     if scaled:  # dL/dCi = dt*lam*_dx^2 * dL/dCs
         api.scale_ci(cibar, lam, dt, inv, out=cibar)
@@ -100,7 +111,7 @@ class Diffusion3DFn(torch.autograd.Function):
         return dT0, dCi, None, None, None, None, None
 
 
-def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None):
+def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None):
     """L = 1/2||T(nt) - Tobs||^2 (FP64 on the GPU) and (dL/dT0, dL/dCi)."""
     every = default_every(nt) if every is None else int(every)
     inv = tuple(inv_spacing)
@@ -108,5 +119,5 @@ def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None):
     out, ckpts = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef)
     resid = torch.empty_like(out)
     L = api.half_sq_dist(out, Tobs, residual=resid)
-    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef)
+    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs)
     return L, dT0, dCi

@@ -506,6 +506,45 @@ int ps_diffusion3d_adjoint_ex(void *Tbar, void *Cibar, const void *ybar, const v
     return PS_OK;
 }
 
+int ps_diffusion3d_adjoint2_ex(void *Tbar, void *Cibar, const void *ybar, const void *T_first,
+                               const void *T_second, const void *Ci, double lam, double dt, double _dx,
+                               double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                               unsigned flags, void *stream) {
+    if (flags) return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
+    PS_TRY(check_dtype(dtype));
+    PS_TRY(check_grid(nx, ny, nz));
+    PS_TRY(check_ptr(Tbar, "Tbar"));
+    PS_TRY(check_ptr(Cibar, "Cibar"));
+    PS_TRY(check_ptr(ybar, "ybar"));
+    PS_TRY(check_ptr(T_first, "T_first"));
+    PS_TRY(check_ptr(T_second, "T_second"));
+    PS_TRY(check_ptr(Ci, "Ci"));
+    PS_TRY(check_finite(lam, "lam"));
+    PS_TRY(check_finite(dt, "dt"));
+    PS_TRY(check_finite(_dx, "_dx"));
+    PS_TRY(check_finite(_dy, "_dy"));
+    PS_TRY(check_finite(_dz, "_dz"));
+    const size_t bytes = (size_t)(nx * ny * nz) * elem_bytes(dtype);
+    if (overlap(Tbar, ybar, bytes) || overlap(Tbar, T_first, bytes) || overlap(Tbar, T_second, bytes) ||
+        overlap(Tbar, Ci, bytes) || overlap(Tbar, Cibar, bytes))
+        return fail(PS_ERR_ALIAS, "Tbar overlaps an input");
+    if (overlap(Cibar, ybar, bytes) || overlap(Cibar, T_first, bytes) || overlap(Cibar, T_second, bytes) ||
+        overlap(Cibar, Ci, bytes))
+        return fail(PS_ERR_ALIAS, "Cibar overlaps an input");
+    if (dtype != PS_F32)
+        return fail(PS_ERR_UNSUPPORTED, "fused transposed pairs are FP32 (the FP64 step is issue-bound)");
+    const Grid3 g{nx, ny, nz};
+    const void *ptrs[6] = {T_first, T_second, ybar, Ci, Cibar, Tbar};
+    if (!adjoint_f32_supported(g, ptrs, 6))
+        return fail(PS_ERR_UNSUPPORTED, "fused transposed pairs need nx*4 a multiple of 16 and a CUDA driver");
+    const StepCoef c = make_coef(lam, dt, _dx, _dy, _dz);
+    cudaError_t e = launch_adjoint2_f32((float *)Tbar, (float *)Cibar, (const float *)ybar,
+                                        (const float *)T_first, (const float *)T_second, (const float *)Ci,
+                                        c, g, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_adjoint2_ex");
+    return PS_OK;
+}
+
 static int check_reduce(const void *A, int64_t n, int dtype, const void *ws) {
     PS_TRY(check_dtype(dtype));
     if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);

@@ -64,6 +64,9 @@ bool adjoint_f32_supported(Grid3 g, const void *const *ptrs, int nptr);
 cudaError_t launch_adjoint_f32_tma(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                    const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
 unsigned adjoint_f32_device_error(bool clear);
+// two FP32 transposed steps per pass (states S1 then S0), every read staged by TMA
+cudaError_t launch_adjoint2_f32(float *Tbar, float *Cibar, const float *ybar, const float *S1,
+                                const float *S0, const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
 
 // ---- helpers (misc.cu) ----
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);

@@ -10,7 +10,8 @@ import torch
 
 import oracle
 from gpu_helpers import problem, rel_linf, to_dev, to_host
-from paper_2211_15634_gb300 import api, inputs
+from paper_2211_15634_gb300 import _lib, api, inputs
+from paper_2211_15634_gb300 import autograd as ag
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
@@ -84,3 +85,77 @@ def test_adjoint_f32_matches_plain_kernel(monkeypatch):
     (ta, ca), (tb, cb) = out
     assert rel_linf(ta, tb) <= TOL
     assert np.max(np.abs(ca - cb)) <= TOL * np.max(np.abs(cb))
+
+
+# ------------------------------------------------ two transposed steps per pass
+def pair_fields(shape, seed=21, inv_override=None):
+    nx, ny, nz = shape
+    T, Ci, lam, dt, inv = problem(nx, ny, nz, gaussian=False)
+    if inv_override is not None:
+        inv = inv_override
+        dt = 1.0 / (2.0 * sum(v * v for v in inv)) / Ci.max() / 1.05
+    S0 = f32(T)
+    S1 = f32(T + 0.01 * inputs.random_field(T.shape, seed + 3))
+    ybar = f32(inputs.random_field(T.shape, seed))
+    cib0 = f32(inputs.random_field(T.shape, seed + 1))
+    dev = [to_dev(a, torch.float32) for a in (ybar, S1, S0, f32(Ci), cib0)]
+    return dev, lam, dt, inv
+
+
+@pytest.mark.parametrize("kchunk", ["0", "1", "2", "5"])
+@pytest.mark.parametrize("shape", SHAPES + [(136, 21, 18)])
+def test_adjoint2_is_two_single_steps(monkeypatch, kchunk, shape):
+    """ps_diffusion3d_adjoint2_ex gives bit for bit two one-step launches (states
+    T_first then T_second), Tbar and Cibar, on every grid edge case and z-chunk."""
+    monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
+    inv_override = (7.0, 11.0, 5.0) if shape == (136, 21, 18) else None
+    (yb, S1, S0, C, cib0), lam, dt, inv = pair_fields(shape, inv_override=inv_override)
+    y1 = torch.empty_like(yb)
+    tb_ref = torch.empty_like(yb)
+    cib_ref = cib0.clone()
+    api.adjoint(y1, cib_ref, yb, S1, C, lam, dt, inv)
+    api.adjoint(tb_ref, cib_ref, y1, S0, C, lam, dt, inv)
+    tb = torch.empty_like(yb)
+    cib = cib0.clone()
+    api.adjoint2(tb, cib, yb, S1, S0, C, lam, dt, inv)
+    assert torch.equal(tb, tb_ref)
+    assert torch.equal(cib, cib_ref)
+    assert api.device_error() == 0
+
+
+def test_adjoint2_refusals():
+    (yb, S1, S0, C, cib), lam, dt, inv = pair_fields((32, 8, 6))
+    tb = torch.empty_like(yb)
+    with pytest.raises(_lib.PsError) as e:  # aliasing
+        api.adjoint2(yb, cib, yb, S1, S0, C, lam, dt, inv)
+    assert e.value.status == _lib.PS_ERR_ALIAS
+    d = [t.double() for t in (tb, cib, yb, S1, S0, C)]
+    with pytest.raises(_lib.PsError) as e:  # FP64
+        api.adjoint2(*d, lam, dt, inv)
+    assert e.value.status == _lib.PS_ERR_UNSUPPORTED
+    (yb, S1, S0, C, cib), lam, dt, inv = pair_fields((30, 8, 6))
+    with pytest.raises(_lib.PsError) as e:  # rows of 120 bytes
+        api.adjoint2(torch.empty_like(yb), cib, yb, S1, S0, C, lam, dt, inv)
+    assert e.value.status == _lib.PS_ERR_UNSUPPORTED
+    assert not api.adjoint2_supported(yb) and api.adjoint2_supported(torch.empty((3, 3, 8)))
+
+
+@pytest.mark.parametrize("every", [1, 4, None])
+def test_fp32_gradient_with_pairs_is_unchanged(every):
+    """The reverse sweep in pairs gives bit for bit the sweep one step at a time
+    (odd and even segment lengths)."""
+    nx, ny, nz, nt = 36, 20, 18, 11
+    T0 = inputs.t0_gaussian(nx, ny, nz)
+    Ci = inputs.ci_constant(nx, ny, nz) + 0.02 * inputs.random_field((nz, ny, nx), 8)
+    Tobs = T0 + 0.01 * inputs.random_field((nz, ny, nx), 9)
+    lam = 1.0
+    dx, dy, dz = inputs.spacing(nx, ny, nz)
+    dt = min(dx * dx, dy * dy, dz * dz) / lam / (1.5 / inputs.C0) / 6.1
+    inv = inputs.inverse_spacing(nx, ny, nz)
+    D = api.to_deviation(to_dev(T0), 1.7)
+    Dobs = api.to_deviation(to_dev(Tobs), 1.7)
+    C = api.to_f32(to_dev(Ci))
+    a = ag.loss_and_grad(D, C, Dobs, lam, dt, inv, nt, every=every, pairs=False)
+    b = ag.loss_and_grad(D, C, Dobs, lam, dt, inv, nt, every=every, pairs=True)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
