@@ -289,3 +289,36 @@ def test_batch_pitch_and_flags(lib):
         assert lib.ps_batch_table_kernel(host) == 0
         st = lib.ps_batch_table_fill_ex(host, nbytes, arr, 2, _lib.PS_F64, 0, 0, 0, _lib.PS_BATCH_ZMARCH, None)
         assert st == _lib.PS_ERR_UNSUPPORTED and b"encoder" in lib.ps_last_error()
+
+
+def test_adjoint2_and_batch_pair_calls_reject_bad_arguments(lib):
+    """The fused transposed pair and the batched pair calls check their arguments on
+    the host before any launch."""
+    D, E, F = 0x290000000, 0x390000000, 0x490000000
+    f32, f64 = _lib.PS_F32, _lib.PS_F64
+
+    def adj2(Tbar=E, Cib=F, yb=A, T1=B, T0=C, Ci=D, dtype=f32, flags=0, n=(8, 8, 8)):
+        return lib.ps_diffusion3d_adjoint2_ex(Tbar, Cib, yb, T1, T0, Ci, 1.0, 1e-3, 7.0, 7.0, 7.0, *n, dtype,
+                                              flags, None)
+    assert adj2(flags=1) == _lib.PS_ERR_ARG
+    assert adj2(T0=None) == _lib.PS_ERR_ARG
+    assert adj2(Tbar=A) == _lib.PS_ERR_ALIAS      # Tbar is ybar
+    assert adj2(Tbar=C) == _lib.PS_ERR_ALIAS      # Tbar is the second state
+    assert adj2(Cib=B) == _lib.PS_ERR_ALIAS       # Cibar is the first state
+    assert adj2(dtype=f64) == _lib.PS_ERR_UNSUPPORTED
+    assert adj2(n=(6, 8, 8)) == _lib.PS_ERR_UNSUPPORTED  # rows of 24 bytes
+    assert b"16" in lib.ps_last_error()
+    assert lib.ps_diffusion3d_batch_step2_ex(0x1000, None, 0, None) == _lib.PS_ERR_ARG
+    # a column-march table has no pair list; run_ex refuses PS_RUN_TEMPORAL2 on it
+    arr = make_problems([9, 12])
+    nbytes = lib.ps_batch_table_bytes_ex(arr, 2, f64, 0, 0, 0, _lib.PS_BATCH_COLUMN)
+    buf = (ctypes.c_char * (nbytes + 64))()
+    off = (-ctypes.addressof(buf)) % 64
+    host = (ctypes.c_char * nbytes).from_buffer(buf, off)
+    assert lib.ps_batch_table_fill_ex(host, nbytes, arr, 2, f64, 0, 0, 0, _lib.PS_BATCH_COLUMN, None) == _lib.PS_OK
+    assert lib.ps_diffusion3d_batch_run_ex(0x1000, host, 4, _lib.PS_RUN_TEMPORAL2, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_batch_step2_ex(0x1000, host, 0, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion3d_batch_step_ex(0x1000, host, 2, None) == _lib.PS_ERR_ARG  # parity
+    # pair tables: FP64 needs the pre-scaled coefficient; the column march has no pairs
+    for flags, dtype in ((_lib.PS_BATCH_TEMPORAL2, f64), (_lib.PS_BATCH_TEMPORAL2 | _lib.PS_BATCH_COLUMN, f32)):
+        assert lib.ps_batch_table_fill_ex(host, nbytes, arr, 2, dtype, 0, 0, 0, flags, None) == _lib.PS_ERR_ARG
