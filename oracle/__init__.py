@@ -15,6 +15,8 @@ Entry points and the passages they follow:
 * :func:`run` - Fig. 1 time loop: ``T2 = copy(T)``, then step and swap.
 * :func:`adjoint_step` - transpose of one ``step!`` (derived, no paper line).
 * :func:`gradient` - L = 1/2||T(nt)-T_obs||^2 and its gradient in T0 and Ci.
+* :func:`step2d`, :func:`run2d` - the 2-D form of Fig. 1's ``step!`` (the z term
+  dropped; arrays of shape ``(ny, nx)``) and its time loop.
 """
 from __future__ import annotations
 
@@ -64,6 +66,9 @@ def _load():
             lib.or_adjoint_step.argtypes = [p, p, p, p, p, d, d, d, d, d, i64, i64, i64]
             lib.or_gradient.argtypes = [p, p, p, p, p, d, d, d, d, d, i64, i64, i64, i32]
             lib.or_gradient.restype = d
+            lib.or_step2d.argtypes = [p, p, p, d, d, d, d, i64, i64]
+            lib.or_run2d.argtypes = [p, p, p, d, d, d, d, i64, i64, i32]
+            lib.or_run2d.restype = i32
             _lib = lib
     return _lib
 
@@ -153,3 +158,29 @@ def loss(T: np.ndarray, Tobs: np.ndarray) -> float:
     """``1/2 ||T - Tobs||^2`` in FP64 (numpy dot of the residual)."""
     r = (T - Tobs).ravel()
     return 0.5 * float(np.dot(r, r))
+
+
+def _f64_2d(a: np.ndarray, name: str) -> np.ndarray:
+    if a.dtype != np.float64 or not a.flags.c_contiguous or a.ndim != 2:
+        raise ValueError(f"{name}: need a C-contiguous float64 array of shape (ny, nx)")
+    return a
+
+
+def step2d(T2: np.ndarray, T: np.ndarray, Ci: np.ndarray, lam: float, dt: float, _dx: float,
+           _dy: float) -> None:
+    """2-D form of Fig. 1's ``step!`` (z term dropped), in place on T2's interior."""
+    for a, nm in ((T2, "T2"), (T, "T"), (Ci, "Ci")):
+        _f64_2d(a, nm)
+    ny, nx = T.shape
+    _load().or_step2d(_ptr(T2), _ptr(T), _ptr(Ci), lam, dt, _dx, _dy, nx, ny)
+
+
+def run2d(T0: np.ndarray, Ci: np.ndarray, lam: float, dt: float, _dx: float, _dy: float,
+          nt: int) -> np.ndarray:
+    """2-D time loop from T0 for nt steps; returns the final state (a new array)."""
+    T = np.array(_f64_2d(T0, "T0"), copy=True)
+    T2 = np.empty_like(T)
+    _f64_2d(Ci, "Ci")
+    ny, nx = T.shape
+    odd = _load().or_run2d(_ptr(T), _ptr(T2), _ptr(Ci), lam, dt, _dx, _dy, nx, ny, int(nt))
+    return T2 if odd else T

@@ -106,6 +106,38 @@ int or_run(double *T, double *T2, const double *Ci, double lam, double dt,
     return cur == T2;
 }
 
+/* 2-D form of Fig. 1's step!: the same update with the z term dropped, i.e. the
+ * kernel with FiniteDifferences2D and the dimension argument of the initialization
+ * call set to 2 (Fig. 1 shows 3):
+ *   @inn(T2) = @inn(T) + dt*(lam*@inn(Ci)*(@d2_xi(T)*_dx^2 + @d2_yi(T)*_dy^2))
+ * Arrays of nx*ny doubles, node (i,j) at offset i + nx*j; interior nodes only. */
+void or_step2d(double *T2, const double *T, const double *Ci, double lam, double dt,
+               double _dx, double _dy, int64_t nx, int64_t ny) {
+    const double _dx2 = _dx * _dx, _dy2 = _dy * _dy;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int64_t j = 1; j < ny - 1; ++j)
+        for (int64_t i = 1; i < nx - 1; ++i) {
+            int64_t p = i + nx * j;
+            double c = T[p];
+            double d2x = (T[p + 1] - c) - (c - T[p - 1]);
+            double d2y = (T[p + nx] - c) - (c - T[p - nx]);
+            T2[p] = c + dt * ((lam * Ci[p]) * (d2x * _dx2 + d2y * _dy2));
+        }
+}
+
+/* 2-D time loop: T2 = copy(T), then nt times { step; swap }.  Returns 1 if the final
+ * state is in the buffer passed as T2 (nt odd). */
+int or_run2d(double *T, double *T2, const double *Ci, double lam, double dt, double _dx,
+             double _dy, int64_t nx, int64_t ny, int nt) {
+    memcpy(T2, T, sizeof(double) * (size_t)(nx * ny));
+    double *cur = T, *nxt = T2;
+    for (int it = 0; it < nt; ++it) {
+        or_step2d(nxt, cur, Ci, lam, dt, _dx, _dy, nx, ny);
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    return cur == T2;
+}
+
 /* Transpose of one step (the step's Jacobian, applied from the left).
  * The step is T_{t+1} = T_t + diag(dt*lam*Ci*[interior]) * Lap(T_t) with
  * boundary rows equal to identity, so for a cotangent ybar = dL/dT_{t+1}:
