@@ -563,6 +563,26 @@ def secondary_metrics(torch, api, ag, inputs, log):
         api.clear_graph_cache()
         torch.cuda.empty_cache()
 
+    # 2-D form of the step (z term dropped): FP64 16384^2 on the pre-scaled coefficient and
+    # FP32 32768^2 in deviation storage, nt = 100, graph-captured; T_eff = 3 n^2 elem nt / t
+    for name, n2, dtype in (("fp64", 16384, torch.float64), ("fp32", 32768, torch.float32)):
+        x = torch.arange(n2, device=dev, dtype=torch.float64) / (n2 - 1)
+        T2d = (1.7 + torch.exp(-((x[None, :] - 0.5) ** 2 + (x[:, None] - 0.5) ** 2) / 0.01)).contiguous()
+        C2d = torch.from_numpy(inputs.ci_random(n2, n2, 1)[0]).to(dev)
+        if dtype == torch.float32:
+            T2d, C2d = api.to_deviation(T2d, 1.7), api.to_f32(C2d)
+        dt2 = api.stable_dt2d(C2d)
+        inv2 = (float(n2 - 1), float(n2 - 1))
+        scaled2 = dtype == torch.float64
+        if scaled2:
+            C2d = api.scale_ci(C2d, 1.0, dt2, inv2)
+        U2d = torch.empty_like(T2d)
+        t = timed(lambda: api.run2d(T2d, U2d, C2d, 1.0, dt2, inv2, 100, graph=True, ci_scaled=scaled2))
+        out[f"diffusion2d_{name}_{n2}_teff_gbs"] = round(3 * n2 * n2 * T2d.element_size() * 100 / t / 1e9, 1)
+        del x, T2d, C2d, U2d
+        api.clear_graph_cache()
+        torch.cuda.empty_cache()
+
     # batched workload: 256 problems, n_p uniform in {32..160}, nt = 500, one launch
     # per step (graph-captured): the TMA z-march on padded rows (tuned z-chunks; FP64 on
     # Ci as given and on the pre-scaled coefficient), the column march on contiguous

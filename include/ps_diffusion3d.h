@@ -292,6 +292,27 @@ int ps_to_deviation(float *D, const double *T, double t_ref, int64_t n, void *st
 int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *stream);
 
 /* ---------------------------------------------------------------------
+ * 2-D form of the step: Fig. 1's step! with the z term dropped (the
+ * dimension argument of the initialization call set to 2):
+ *   T2[inner] = T + dt*(lam*Ci*(d2x(T)*_dx^2 + d2y(T)*_dy^2))
+ * on (ny, nx) fields, x fastest, boundary held fixed.  Same conventions as
+ * ps_diffusion3d_step: device pointers, 16-byte aligned, T2 not overlapping
+ * T or Ci, nx, ny >= 3, T2's boundary already equal to T's (run sets it).
+ * Flags: PS_RUN_CI_SCALED (PS_F64, _dx == _dy: Ci holds dt*lam*_dx^2*Ci of
+ * ps_diffusion3d_scale_ci over nx*ny values).  Kernel: a warp-level y-march
+ * (16-byte accesses when nx*elem is a multiple of 16), the 3-D step's
+ * per-node arithmetic with the z difference zero.
+ * ------------------------------------------------------------------- */
+int ps_diffusion2d_step(void *T2, const void *T, const void *Ci, double lam, double dt, double _dx,
+                        double _dy, int64_t nx, int64_t ny, int dtype, unsigned flags, void *stream);
+/* nt 2-D steps with T and T2 swapped after each (T2's edges first set to T's);
+ * *result_in_T2 = nt & 1 (may be NULL).  Flags: PS_RUN_GRAPH (capture once per
+ * argument set, replay), PS_RUN_CI_SCALED. */
+int ps_diffusion2d_run(void *T, void *T2, const void *Ci, double lam, double dt, double _dx, double _dy,
+                       int64_t nx, int64_t ny, int nt, int dtype, unsigned flags, void *stream,
+                       int *result_in_T2);
+
+/* ---------------------------------------------------------------------
  * Batched step: many independent problems of different sizes, one launch
  * per step (configs: many problems stepped together; Fig. 1's step per
  * problem).  The host describes each problem with a ps_problem; the

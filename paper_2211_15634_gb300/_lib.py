@@ -94,6 +94,8 @@ SIGNATURES = {
                                     ctypes.POINTER(_I64)]),
     "ps_batch_table_kernel": (_I, [_P]),
     "ps_diffusion3d_batch_step_ex": (_I, [_P, _P, _I, _P]),
+    "ps_diffusion2d_step": (_I, [_P, _P, _P, _D, _D, _D, _D, _I64, _I64, _I, _U, _P]),
+    "ps_diffusion2d_run": (_I, [_P, _P, _P, _D, _D, _D, _D, _I64, _I64, _I, _I, _U, _P, ctypes.POINTER(_I)]),
     "ps_diffusion3d_adjoint2_ex": (_I, [_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _U,
                                         _P]),
     "ps_diffusion3d_batch_step2_ex": (_I, [_P, _P, _I, _P]),

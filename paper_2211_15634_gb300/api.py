@@ -212,6 +212,47 @@ def adjoint(Tbar, Cibar, ybar, T, Ci, lam: float, dt: float, inv_spacing, *,
         _lib.PS_RUN_CI_SCALED if ci_scaled else 0, _stream(T)))
 
 
+def _grid2d(t: torch.Tensor):
+    if t.dim() != 2:
+        raise ValueError("2-D fields must have shape (ny, nx)")
+    ny, nx = t.shape
+    return nx, ny
+
+
+def step2d(T2, T, Ci, lam: float, dt: float, inv_spacing: Sequence[float], *,
+           ci_scaled: bool = False) -> None:
+    """One step of the 2-D form of Fig. 1 (z term dropped) on (ny, nx) fields."""
+    code = _code(T)
+    _same(T, T2, Ci)
+    nx, ny = _grid2d(T)
+    check(_lib.load().ps_diffusion2d_step(_field(T2, "T2", code), _field(T, "T", code), _field(Ci, "Ci", code),
+                                          lam, dt, inv_spacing[0], inv_spacing[1], nx, ny, code,
+                                          _lib.PS_RUN_CI_SCALED if ci_scaled else 0, _stream(T)))
+
+
+def run2d(T, T2, Ci, lam: float, dt: float, inv_spacing: Sequence[float], nt: int, *,
+          graph: bool = False, ci_scaled: bool = False) -> torch.Tensor:
+    """nt steps of the 2-D form (T2's edges set to T's first); returns the buffer
+    holding T(nt)."""
+    code = _code(T)
+    _same(T, T2, Ci)
+    nx, ny = _grid2d(T)
+    odd = ctypes.c_int(0)
+    flags = (_lib.PS_RUN_GRAPH if graph else 0) | (_lib.PS_RUN_CI_SCALED if ci_scaled else 0)
+    check(_lib.load().ps_diffusion2d_run(_field(T, "T", code), _field(T2, "T2", code), _field(Ci, "Ci", code),
+                                         lam, dt, inv_spacing[0], inv_spacing[1], nx, ny, int(nt), code, flags,
+                                         _stream(T), ctypes.byref(odd)))
+    return T2 if odd.value else T
+
+
+def stable_dt2d(Ci, lam: float = 1.0, lengths=(1.0, 1.0)) -> float:
+    """dt for the 2-D form: min(dx^2, dy^2)/lam/maximum(Ci)/4.1 (Fig. 1's rule with the
+    2-D bound 4 in place of 6), maximum(Ci) reduced on the GPU."""
+    ny, nx = Ci.shape
+    dx, dy = lengths[0] / (nx - 1), lengths[1] / (ny - 1)
+    return min(dx * dx, dy * dy) / lam / maximum(Ci) / 4.1
+
+
 def adjoint2(Tbar, Cibar, ybar, T_first, T_second, Ci, lam: float, dt: float, inv_spacing) -> None:
     """Two transposed steps in one pass (FP32): with ybar = dL/dT_{t+2} and the
     states T_first = T_{t+1}, T_second = T_t, Tbar := dL/dT_t and Cibar accumulates

@@ -188,11 +188,10 @@ static cudaError_t capture_stream(cudaStream_t *out) {
     return cudaSuccess;
 }
 
-static int run_graph(void *T, void *T2, void *comp, const void *Ci, double lam, double dt,
-                     double _dx, double _dy, double _dz, Grid3 g, int nt, int dtype,
-                     unsigned flags, cudaStream_t s) {
-    const GraphKey key{current_device(), T, T2, comp, Ci, lam, dt, _dx, _dy, _dz, g.nx, g.ny, g.nz,
-                       nt, dtype, flags & ~PS_RUN_GRAPH};
+// Replay the CUDA graph cached under `key`, capturing it first from enqueue(stream)
+// on the device's capture stream when it is not cached yet.
+template <typename F>
+static int graph_replay(const GraphKey &key, F &&enqueue, const char *what, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
@@ -201,13 +200,12 @@ static int run_graph(void *T, void *T2, void *comp, const void *Ci, double lam, 
         if (e != cudaSuccess) return cuda_fail(e, "capture stream");
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        cudaError_t le = enqueue_run(T, T2, comp, Ci, make_coef(lam, dt, _dx, _dy, _dz), g, nt, dtype,
-                                     flags, cs);
+        const cudaError_t le = enqueue(cs);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cs, &graph);
         if (le != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return cuda_fail(le, "capturing the time loop");
+            return cuda_fail(le, what);
         }
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         cudaGraphExec_t exec = nullptr;
@@ -219,6 +217,19 @@ static int run_graph(void *T, void *T2, void *comp, const void *Ci, double lam, 
     cudaError_t e = cudaGraphLaunch(it->second, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return PS_OK;
+}
+
+static int run_graph(void *T, void *T2, void *comp, const void *Ci, double lam, double dt,
+                     double _dx, double _dy, double _dz, Grid3 g, int nt, int dtype,
+                     unsigned flags, cudaStream_t s) {
+    const GraphKey key{current_device(), T, T2, comp, Ci, lam, dt, _dx, _dy, _dz, g.nx, g.ny, g.nz,
+                       nt, dtype, flags & ~PS_RUN_GRAPH};
+    return graph_replay(
+        key,
+        [&](cudaStream_t cs) {
+            return enqueue_run(T, T2, comp, Ci, make_coef(lam, dt, _dx, _dy, _dz), g, nt, dtype, flags, cs);
+        },
+        "capturing the time loop", s);
 }
 
 }  // namespace psd
@@ -542,6 +553,80 @@ int ps_diffusion3d_adjoint2_ex(void *Tbar, void *Cibar, const void *ybar, const 
                                         (const float *)T_first, (const float *)T_second, (const float *)Ci,
                                         c, g, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_adjoint2_ex");
+    return PS_OK;
+}
+
+// ------------------------------------------------------------------ 2-D
+static int check_2d(const void *T2, const void *T, const void *Ci, double lam, double dt, double _dx,
+                    double _dy, int64_t nx, int64_t ny, int dtype, unsigned flags, unsigned allowed) {
+    if (flags & ~allowed) return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
+    PS_TRY(check_dtype(dtype));
+    if (nx < 3 || ny < 3) return fail(PS_ERR_ARG, "grid %lld x %lld: every size must be >= 3", (long long)nx,
+                                      (long long)ny);
+    if (nx > (1LL << 40) || ny > (1LL << 40) || (double)nx * (double)ny > 9.0e15)
+        return fail(PS_ERR_ARG, "grid %lld x %lld is too large", (long long)nx, (long long)ny);
+    PS_TRY(check_ptr(T2, "T2"));
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_ptr(Ci, "Ci"));
+    PS_TRY(check_finite(lam, "lam"));
+    PS_TRY(check_finite(dt, "dt"));
+    PS_TRY(check_finite(_dx, "_dx"));
+    PS_TRY(check_finite(_dy, "_dy"));
+    const size_t bytes = (size_t)(nx * ny) * elem_bytes(dtype);
+    if (overlap(T2, T, bytes)) return fail(PS_ERR_ALIAS, "T2 overlaps T");
+    if (overlap(T2, Ci, bytes)) return fail(PS_ERR_ALIAS, "T2 overlaps Ci");
+    if (flags & PS_RUN_CI_SCALED) {
+        if (dtype != PS_F64) return fail(PS_ERR_UNSUPPORTED, "a pre-scaled Ci needs PS_F64");
+        if (_dx != _dy) return fail(PS_ERR_UNSUPPORTED, "a pre-scaled Ci needs equal spacings (_dx == _dy)");
+    }
+    return PS_OK;
+}
+
+static int mode_2d(int dtype, unsigned flags, StepCoef c) {
+    if (dtype == PS_F32) return Z_F32;
+    if (flags & PS_RUN_CI_SCALED) return Z_F64_SCALED;
+    const double K = c.dtlam * c.ax;
+    if (c.ax == c.ay && K > 2.2250738585072014e-308 && K < 1e300) return Z_F64_EMU_ISO_DMUL;
+    return Z_F64_NATIVE;
+}
+
+int ps_diffusion2d_step(void *T2, const void *T, const void *Ci, double lam, double dt, double _dx,
+                        double _dy, int64_t nx, int64_t ny, int dtype, unsigned flags, void *stream) {
+    PS_TRY(check_2d(T2, T, Ci, lam, dt, _dx, _dy, nx, ny, dtype, flags, PS_RUN_CI_SCALED));
+    const StepCoef c = make_coef(lam, dt, _dx, _dy, 0.0);
+    cudaError_t e = launch_step2d(mode_2d(dtype, flags, c), T2, T, Ci, c, nx, ny, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion2d_step");
+    return PS_OK;
+}
+
+static cudaError_t enqueue_run2d(void *T, void *T2, const void *Ci, StepCoef c, int64_t nx, int64_t ny,
+                                 int nt, int dtype, unsigned flags, cudaStream_t s) {
+    if (nt == 0) return cudaSuccess;
+    cudaError_t e = launch_copy_edges2d(T2, T, nx, ny, (int)elem_bytes(dtype), s);
+    const int mode = mode_2d(dtype, flags, c);
+    for (int it = 0; it < nt && e == cudaSuccess; ++it)
+        e = it & 1 ? launch_step2d(mode, T, T2, Ci, c, nx, ny, s) : launch_step2d(mode, T2, T, Ci, c, nx, ny, s);
+    return e;
+}
+
+int ps_diffusion2d_run(void *T, void *T2, const void *Ci, double lam, double dt, double _dx, double _dy,
+                       int64_t nx, int64_t ny, int nt, int dtype, unsigned flags, void *stream,
+                       int *result_in_T2) {
+    PS_TRY(check_2d(T2, T, Ci, lam, dt, _dx, _dy, nx, ny, dtype, flags, PS_RUN_CI_SCALED | PS_RUN_GRAPH));
+    if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
+    if (result_in_T2) *result_in_T2 = nt & 1;
+    const StepCoef c = make_coef(lam, dt, _dx, _dy, 0.0);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags & PS_RUN_GRAPH) {
+        // 2-D keys: nz = -2 marks them apart from the 3-D time loops
+        const GraphKey key{current_device(), T, T2, nullptr, Ci, lam, dt, _dx, _dy, 0.0, nx, ny, -2, nt, dtype,
+                           flags & ~PS_RUN_GRAPH};
+        return graph_replay(
+            key, [&](cudaStream_t cs) { return enqueue_run2d(T, T2, Ci, c, nx, ny, nt, dtype, flags, cs); },
+            "capturing the 2-D time loop", s);
+    }
+    cudaError_t e = enqueue_run2d(T, T2, Ci, c, nx, ny, nt, dtype, flags, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion2d_run");
     return PS_OK;
 }
 
@@ -1048,31 +1133,9 @@ static int batch_run(const void *dev_table, const BatchHeader &h, int nt, unsign
     // size is baked into the graph (a new table may reuse a freed table's address)
     const GraphKey key{current_device(), dev_table, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0,
                        0.0, h.nitems, h.zmode, h.kernel, nt, h.dtype, 0x80000000u | (pairs ? 1u : 0u)};
-    std::lock_guard<std::mutex> lock(g_graph_mu);
-    auto it = g_graphs.find(key);
-    if (it == g_graphs.end()) {
-        cudaStream_t cs;
-        cudaError_t e = capture_stream(&cs);
-        if (e != cudaSuccess) return cuda_fail(e, "capture stream");
-        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        const cudaError_t le = enqueue_batch_run(dev_table, h, nt, pairs, cs);
-        cudaGraph_t graph = nullptr;
-        e = cudaStreamEndCapture(cs, &graph);
-        if (le != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return cuda_fail(le, "capturing the batch loop");
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        it = g_graphs.emplace(key, exec).first;
-    }
-    cudaError_t e = cudaGraphLaunch(it->second, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-    return PS_OK;
+    return graph_replay(
+        key, [&](cudaStream_t cs) { return enqueue_batch_run(dev_table, h, nt, pairs, cs); },
+        "capturing the batch loop", s);
 }
 
 int ps_diffusion3d_batch_run_ex(const void *dev_table, const void *host_table, int nt, unsigned flags,

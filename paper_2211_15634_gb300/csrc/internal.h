@@ -64,6 +64,11 @@ bool adjoint_f32_supported(Grid3 g, const void *const *ptrs, int nptr);
 cudaError_t launch_adjoint_f32_tma(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                    const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
 unsigned adjoint_f32_device_error(bool clear);
+// 2-D form of the step (diffusion2d.cu); mode is a ZMode: Z_F32, Z_F64_SCALED,
+// Z_F64_EMU_ISO_DMUL or Z_F64_NATIVE
+cudaError_t launch_step2d(int mode, void *T2, const void *T, const void *Ci, StepCoef c, int64_t nx,
+                          int64_t ny, cudaStream_t s);
+cudaError_t launch_copy_edges2d(void *T2, const void *T, int64_t nx, int64_t ny, int esz, cudaStream_t s);
 // two FP32 transposed steps per pass (states S1 then S0), every read staged by TMA
 cudaError_t launch_adjoint2_f32(float *Tbar, float *Cibar, const float *ybar, const float *S1,
                                 const float *S0, const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);

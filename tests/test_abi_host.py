@@ -322,3 +322,22 @@ def test_adjoint2_and_batch_pair_calls_reject_bad_arguments(lib):
     # pair tables: FP64 needs the pre-scaled coefficient; the column march has no pairs
     for flags, dtype in ((_lib.PS_BATCH_TEMPORAL2, f64), (_lib.PS_BATCH_TEMPORAL2 | _lib.PS_BATCH_COLUMN, f32)):
         assert lib.ps_batch_table_fill_ex(host, nbytes, arr, 2, dtype, 0, 0, 0, flags, None) == _lib.PS_ERR_ARG
+
+
+def test_diffusion2d_rejects_bad_arguments(lib):
+    f64, f32 = _lib.PS_F64, _lib.PS_F32
+
+    def step2d(T2=B, T=A, Ci=C, nx=8, ny=8, dtype=f64, flags=0, dx=7.0, dy=7.0):
+        return lib.ps_diffusion2d_step(T2, T, Ci, 1.0, 1e-3, dx, dy, nx, ny, dtype, flags, None)
+    assert step2d(nx=2) == _lib.PS_ERR_ARG
+    assert step2d(T=None) == _lib.PS_ERR_ARG
+    assert step2d(T2=A) == _lib.PS_ERR_ALIAS
+    assert step2d(T=A + 8) == _lib.PS_ERR_ALIGN
+    assert step2d(flags=_lib.PS_RUN_GRAPH) == _lib.PS_ERR_ARG  # run only
+    assert step2d(flags=_lib.PS_RUN_CI_SCALED, dtype=f32) == _lib.PS_ERR_UNSUPPORTED
+    assert step2d(flags=_lib.PS_RUN_CI_SCALED, dy=6.0) == _lib.PS_ERR_UNSUPPORTED
+    odd = ctypes.c_int(-1)
+    assert lib.ps_diffusion2d_run(A, B, C, 1.0, 1e-3, 7.0, 7.0, 8, 8, -1, f64, 0, None,
+                                  ctypes.byref(odd)) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion2d_run(A, B, C, 1.0, 1e-3, 7.0, 7.0, 8, 8, 3, f64, 0x40, None,
+                                  ctypes.byref(odd)) == _lib.PS_ERR_ARG
