@@ -1,0 +1,125 @@
+"""Full-size parity in the launch configurations bench.py times, on outputs the
+oracle can compute one by one (each sampled node from its dependency cone) or,
+for the batch, on whole problems.
+
+* FP64 512^3, nt = 100: dt from maximum(Ci) on the GPU, the pre-scaled
+  coefficient, the graph-captured loop of the TMA step (the headline path).
+* FP32 1024^3, nt = 100, deviation storage (the bench's FP32 1024^3 row).
+* The 256-problem batch, nt = 500, padded rows, the TMA z-march with tuned
+  z-chunks (FP64 on the pre-scaled coefficient, and FP32): the smallest
+  problems and the largest one against the oracle's own runs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle
+from gpu_helpers import light_cone_reference, problem, to_dev, to_host
+from paper_2211_15634_gb300 import api, inputs, tuner
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+FP64_TOL = 1e-12
+U32 = 2.0 ** -24
+
+
+def sample(t: torch.Tensor, pts):
+    """Values of a device field at nodes (i, j, k), gathered on the device."""
+    k = torch.tensor([p[2] for p in pts], device=t.device)
+    j = torch.tensor([p[1] for p in pts], device=t.device)
+    i = torch.tensor([p[0] for p in pts], device=t.device)
+    return t[k, j, i].double().cpu().numpy()
+
+
+PTS512 = [(256, 256, 256), (1, 1, 1), (510, 300, 7), (255, 3, 509), (120, 400, 256), (0, 17, 30)]
+
+
+def test_fp64_512_bench_path():
+    n, nt = 512, 100
+    T0, Ci, inv = bench.fields(n)
+    dev = torch.device("cuda")
+    T = torch.from_numpy(T0).to(dev)
+    C = torch.from_numpy(Ci).to(dev)
+    dt = api.stable_dt(C, 1.0)
+    assert dt == oracle.stable_dt(1 / (n - 1), 1 / (n - 1), 1 / (n - 1), 1.0, oracle.maximum(Ci))
+    Cs = api.scale_ci(C, 1.0, dt, inv)
+    assert api.step_kernel_name(T, T, Cs, 1.0, dt, inv, ci_scaled=True) == "k_zmarch<F64_SCALED>"
+    res = api.run(T, torch.empty_like(T), Cs, 1.0, dt, inv, nt, graph=True, ci_scaled=True)
+    got = sample(res, PTS512)
+    oracle.set_threads(max(1, oracle.max_threads()))
+    try:
+        ref = light_cone_reference(oracle, T0, Ci, 1.0, dt, inv, nt, PTS512)
+    finally:
+        oracle.set_threads(1)
+    assert np.max(np.abs(got - ref)) <= FP64_TOL * np.max(np.abs(T0))
+    assert float(res.min()) >= T0.min() - 1e-12 and float(res.max()) <= T0.max() + 1e-12
+    assert api.device_error() == 0
+    api.clear_graph_cache()
+
+
+PTS1024 = [(512, 512, 512), (1, 1022, 3), (1000, 40, 700), (300, 800, 1022)]
+
+
+def test_fp32_1024_bench_path():
+    n, nt = 1024, 100
+    T0, Ci, inv = bench.fields(n)
+    dev = torch.device("cuda")
+    D = api.to_deviation(torch.from_numpy(T0).to(dev), 1.7)
+    C32 = api.to_f32(torch.from_numpy(Ci).to(dev))
+    dt = api.stable_dt(C32, 1.0)
+    res = api.run(D, torch.empty_like(D), C32, 1.0, dt, inv, nt, graph=True)
+    got = sample(res, PTS1024)
+    # the oracle on the FP32-rounded inputs, on each sample's cone only
+    D0 = (T0 - 1.7).astype(np.float32).astype(np.float64)
+    C0 = Ci.astype(np.float32).astype(np.float64)
+    oracle.set_threads(max(1, oracle.max_threads()))
+    try:
+        ref = light_cone_reference(oracle, D0, C0, 1.0, dt, inv, nt, PTS1024)
+    finally:
+        oracle.set_threads(1)
+    assert np.max(np.abs(got - ref)) <= nt * 13 * U32 * np.max(np.abs(D0))
+    api.clear_graph_cache()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batch_256_bench_path(tmp_path, monkeypatch, dtype):
+    monkeypatch.setenv("PS_TUNER_CACHE", str(tmp_path / "tuner.json"))
+    nt = 500
+    dev = torch.device("cuda")
+    scaled = dtype == torch.float64
+    probs, _ = bench.batch_workload(torch, api, inputs, dtype, dev, 256, pitched=True, ci_scaled=scaled)
+    sizes = [int(p["T"].shape[0]) for p in probs]
+    b = tuner.tuned_batch(probs, kernel="zmarch", ci_scaled=scaled)  # as the bench runs it
+    # the tuner stepped the fields: start again from T0
+    order = np.argsort(sizes)
+    check = [int(q) for q in order[:3]] + [int(order[-1])]
+    for q, p in enumerate(probs):
+        T0q, _ = inputs.batch_problem(q, sizes[q])
+        Tq = torch.from_numpy(T0q).to(dev)
+        if dtype == torch.float32:
+            Tq = api.to_deviation(Tq, 1.7)
+        p["T"].copy_(Tq)
+        p["T2"].copy_(Tq)
+    b.run(nt, graph=True)
+    oracle.set_threads(max(1, oracle.max_threads()))
+    try:
+        for q in check:
+            n = sizes[q]
+            T0q, Ciq = inputs.batch_problem(q, n)
+            dtq = probs[q]["dt"]
+            inv = inputs.inverse_spacing(n, n, n)
+            got = to_host(b.result(q, nt))
+            if dtype == torch.float64:
+                ref = oracle.run(T0q, Ciq, 1.0, dtq, *inv, nt)
+                assert np.max(np.abs(got - ref)) <= FP64_TOL * np.max(np.abs(ref)), (q, n)
+            else:
+                D0 = (T0q - 1.7).astype(np.float32).astype(np.float64)
+                C0 = Ciq.astype(np.float32).astype(np.float64)
+                ref = oracle.run(D0, C0, 1.0, dtq, *inv, nt)
+                assert np.max(np.abs(got - ref)) <= nt * 13 * U32 * np.max(np.abs(D0)), (q, n)
+    finally:
+        oracle.set_threads(1)
+    assert api.device_error() == 0
+    api.clear_graph_cache()
