@@ -8,6 +8,9 @@ for the batch, on whole problems.
 * The 256-problem batch, nt = 500, padded rows, the TMA z-march with tuned
   z-chunks (FP64 on the pre-scaled coefficient, and FP32): the smallest
   problems and the largest one against the oracle's own runs.
+* FP64 768^3 (byte offsets past 2^32), sampled like 512^3.
+* The gradient workload (256^3, nt = 200, FP64): directional derivatives of the
+  adjoint against central differences of FP64 forward runs, to 1e-6.
 """
 import numpy as np
 import pytest
@@ -123,3 +126,62 @@ def test_batch_256_bench_path(tmp_path, monkeypatch, dtype):
         oracle.set_threads(1)
     assert api.device_error() == 0
     api.clear_graph_cache()
+
+
+def test_fp64_768_bench_path():
+    """The bench's 768^3 FP64 row (3.4 GiB per field: byte offsets past 2^32)."""
+    n, nt = 768, 100
+    T0, Ci, inv = bench.fields(n)
+    dev = torch.device("cuda")
+    T = torch.from_numpy(T0).to(dev)
+    C = torch.from_numpy(Ci).to(dev)
+    dt = api.stable_dt(C, 1.0)
+    Cs = api.scale_ci(C, 1.0, dt, inv)
+    res = api.run(T, torch.empty_like(T), Cs, 1.0, dt, inv, nt, graph=True, ci_scaled=True)
+    pts = [(384, 384, 384), (766, 1, 500), (2, 700, 766), (700, 5, 3)]
+    got = sample(res, pts)
+    oracle.set_threads(max(1, oracle.max_threads()))
+    try:
+        ref = light_cone_reference(oracle, T0, Ci, 1.0, dt, inv, nt, pts)
+    finally:
+        oracle.set_threads(1)
+    assert np.max(np.abs(got - ref)) <= FP64_TOL * np.max(np.abs(T0))
+    api.clear_graph_cache()
+
+
+@pytest.mark.parametrize("every", [None, 1])
+def test_gradient_256_directional_derivatives(every):
+    """The bench's gradient workload (256^3, nt = 200, FP64, sqrt(nt) checkpoints or
+    every state kept): the adjoint's directional derivatives in T0 and Ci against
+    central differences of the loss computed by FP64 forward runs.  L is exactly
+    quadratic in T0 (the central difference is exact up to rounding); in Ci the
+    difference error is O(h^2)."""
+    from paper_2211_15634_gb300 import autograd as ag
+    n, nt = 256, 200
+    dev = torch.device("cuda")
+    T0 = torch.from_numpy(inputs.t0_gaussian(n, n, n)).to(dev)
+    inv = inputs.inverse_spacing(n, n, n)
+    dx = 1.0 / (n - 1)
+    dt = dx * dx / 1.0 / (1.5 / inputs.C0) / 6.1
+    Ct = torch.from_numpy(inputs.ci_smooth(n, n, n)).to(dev)
+    Tobs = api.run(T0.clone(), T0.clone(), Ct, 1.0, dt, inv, nt).clone()
+    Ci = torch.full_like(T0, 1.0 / inputs.C0) + 0.02 * torch.from_numpy(
+        inputs.random_field((n, n, n), 8)).to(dev)
+    L, dT0, dCi = ag.loss_and_grad(T0, Ci, Tobs, 1.0, dt, inv, nt, every=every)
+
+    def loss(T0_, Ci_):
+        out = api.run(T0_.clone(), T0_.clone(), Ci_, 1.0, dt, inv, nt)
+        return float(api.half_sq_dist(out, Tobs))
+
+    assert abs(loss(T0, Ci) - float(L)) <= 1e-12 * float(L)
+    v = torch.from_numpy(inputs.random_field((n, n, n), 11)).to(dev)
+    v[0, :, :] = v[-1, :, :] = v[:, 0, :] = v[:, -1, :] = v[:, :, 0] = v[:, :, -1] = 0.0
+    h = 1e-4
+    fd = (loss(T0, Ci + h * v) - loss(T0, Ci - h * v)) / (2 * h)
+    ad = float(api.dot(dCi, v))
+    assert abs(fd - ad) <= 1e-6 * abs(ad)
+    w = torch.from_numpy(inputs.random_field((n, n, n), 12)).to(dev)
+    h = 1e-3
+    fd = (loss(T0 + h * w, Ci) - loss(T0 - h * w, Ci)) / (2 * h)
+    ad = float(api.dot(dT0, w))
+    assert abs(fd - ad) <= 1e-6 * abs(ad)
