@@ -45,7 +45,10 @@ cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs
 
 const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c,
                                  bool scaled) {
-    if (scaled) return zmarch_supported(g, 8, T2, T, Ci) ? "k_zmarch<F64_SCALED>" : "k_step_basic_emu";
+    if (scaled) {
+        if (!zmarch_supported(g, 8, T2, T, Ci)) return "k_step_basic_emu";
+        return f64_scaled_wide(g, T2, T, Ci) ? "k_zmarch<F64_SCALED4>" : "k_zmarch<F64_SCALED>";
+    }
     if (!emu_ok(c)) return "k_step_basic<double>";
     const bool iso = c.ax == c.ay && c.ay == c.az;
     if (zmarch_supported(g, 8, T2, T, Ci)) return iso ? "k_zmarch<F64_EMU_ISO>" : "k_zmarch<F64_EMU_ANISO>";

@@ -16,6 +16,7 @@ enum ZMode {
     Z_F32_COMP = 4,
     Z_F64_EMU_ISO_DMUL = 5,  // two FP64 ops per node: fma(Ci*K, S, T)
     Z_F64_SCALED = 6,        // Ci already holds dt*lam*_d^2*Ci: fma(Cs, S, T)
+    Z_F64_SCALED4 = 7,       // as Z_F64_SCALED, four nodes per thread (32-byte accesses)
 };
 
 struct ZParams {
@@ -35,6 +36,9 @@ bool make_tensor_map_3d_pitch(CUtensorMap *m, const void *ptr, int esz, Grid3 g,
                               unsigned bx, unsigned by);
 // True when the driver's tensor-map encoder could be loaded (a GPU driver is present).
 bool tma_encoder_available();
+// Whether the pre-scaled FP64 step takes the four-nodes-per-thread kernel (rows of a
+// multiple of 32 bytes, 32-byte aligned fields; PS_F64_VARIANT=px2 turns it off).
+bool f64_scaled_wide(Grid3 g, const void *T2, const void *T, const void *Ci);
 // Step parameters of the z-march kernels for coefficients c on grid g with row pitch `pitch`.
 ZParams zparams_for(StepCoef c, Grid3 g, int64_t pitch);
 

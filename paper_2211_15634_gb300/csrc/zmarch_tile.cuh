@@ -42,6 +42,12 @@ struct ZTraits<Z_F64_EMU_ISO_DMUL> : ZTraits<Z_F64_EMU_ISO> {};
 template <>
 struct ZTraits<Z_F64_SCALED> : ZTraits<Z_F64_EMU_ISO> {};
 template <>
+struct ZTraits<Z_F64_SCALED4> {
+    using E = double;
+    using V = double4;
+    static constexpr int PX = 4;
+};
+template <>
 struct ZTraits<Z_F32> {
     using E = float;
     using V = float4;
@@ -167,10 +173,10 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
             }
             V out;
             if constexpr (MODE == Z_F64_EMU_ISO || MODE == Z_F64_EMU_ANISO ||
-                          MODE == Z_F64_EMU_ISO_DMUL || MODE == Z_F64_SCALED) {
+                          MODE == Z_F64_EMU_ISO_DMUL || MODE == Z_F64_SCALED || MODE == Z_F64_SCALED4) {
                 constexpr bool kIso = MODE != Z_F64_EMU_ANISO;
                 constexpr bool kDmul = MODE == Z_F64_EMU_ISO_DMUL;
-                constexpr bool kScaled = MODE == Z_F64_SCALED;
+                constexpr bool kScaled = MODE == Z_F64_SCALED || MODE == Z_F64_SCALED4;
                 unsigned long long c[PX], xm[PX], xp[PX], ym[PX], yp[PX], zm[PX], zp[PX];
 #pragma unroll
                 for (int i = 0; i < PX; ++i) {

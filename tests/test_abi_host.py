@@ -203,7 +203,8 @@ def test_kernel_names_for_the_fp64_step(lib):
     # the TMA kernel needs the driver's tensor-map encoder (absent without a GPU driver)
     tma = name(64, 0) == "k_zmarch<F64_EMU_ISO>"
     assert name(64, 0) == ("k_zmarch<F64_EMU_ISO>" if tma else "k_step_basic_emu")
-    assert name(64, _lib.PS_RUN_CI_SCALED) == ("k_zmarch<F64_SCALED>" if tma else "k_step_basic_emu")
+    assert name(64, _lib.PS_RUN_CI_SCALED) == ("k_zmarch<F64_SCALED4>" if tma else "k_step_basic_emu")
+    assert name(66, _lib.PS_RUN_CI_SCALED) == ("k_zmarch<F64_SCALED>" if tma else "k_step_basic_emu")
     assert name(63, _lib.PS_RUN_CI_SCALED) == "k_step_basic_emu"
 
 

@@ -48,7 +48,7 @@ def test_fp64_512_bench_path():
     dt = api.stable_dt(C, 1.0)
     assert dt == oracle.stable_dt(1 / (n - 1), 1 / (n - 1), 1 / (n - 1), 1.0, oracle.maximum(Ci))
     Cs = api.scale_ci(C, 1.0, dt, inv)
-    assert api.step_kernel_name(T, T, Cs, 1.0, dt, inv, ci_scaled=True) == "k_zmarch<F64_SCALED>"
+    assert api.step_kernel_name(T, T, Cs, 1.0, dt, inv, ci_scaled=True) == "k_zmarch<F64_SCALED4>"
     res = api.run(T, torch.empty_like(T), Cs, 1.0, dt, inv, nt, graph=True, ci_scaled=True)
     got = sample(res, PTS512)
     oracle.set_threads(max(1, oracle.max_threads()))

@@ -168,7 +168,7 @@ def test_fp64_prescaled_step_kernel_and_in_place_scale():
     T, C = to_dev(T0), to_dev(Ci)
     T2 = torch.empty_like(T)
     api.copy_boundary(T2, T)
-    assert api.step_kernel_name(T2, T, C, lam, dt, inv, ci_scaled=True) == "k_zmarch<F64_SCALED>"
+    assert api.step_kernel_name(T2, T, C, lam, dt, inv, ci_scaled=True) == "k_zmarch<F64_SCALED4>"
     api.scale_ci(C, lam, dt, inv, out=C)  # in place
     api.step(T2, T, C, lam, dt, inv, ci_scaled=True)
     ref = T0.copy()
