@@ -593,7 +593,7 @@ def secondary_metrics(torch, api, ag, inputs, log):
         t_adj = timed(adj10, reps=3) / 10
         out[f"adjoint_256_{name}_ms"] = round(1e3 * t_adj, 4)
         out[f"adjoint_256_{name}_gbs"] = round(6 * n ** 3 * Td.element_size() / t_adj / 1e9, 1)
-        for tag, every in (("sqrt_nt", None), ("all_states", 1)):
+        for tag, every in (("sqrt_nt", ag.default_every(nt)), ("all_states", 1)):
             t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt, every=every), reps=2)
             out[f"grad_over_fwd_256_{name}_{tag}"] = round(t_grad / t_fwd, 3)
             torch.cuda.empty_cache()

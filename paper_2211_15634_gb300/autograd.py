@@ -2,7 +2,9 @@
 
 ``Diffusion3DFn.apply(T0, Ci, lam, dt, inv_spacing, nt, every)`` runs the
 Fig. 1 time loop forward, keeping a checkpoint of the state every ``every``
-steps (``every = ceil(sqrt(nt))`` by default).  ``backward`` walks the
+steps.  By default (``every=None``) every state is kept when the nt fields fit
+in the device's free memory with a margin (no recompute: the reverse sweep
+reads each state once), else every ``ceil(sqrt(nt))`` steps.  ``backward`` walks the
 segments in reverse: it recomputes the states of one segment from its
 checkpoint with the forward kernel, then applies the transposed step
 (``ps_diffusion3d_adjoint``) from the segment's last step to its first,
@@ -26,7 +28,31 @@ from . import api
 
 
 def default_every(nt: int) -> int:
+    """The sqrt(nt) checkpoint interval."""
     return max(1, int(math.ceil(math.sqrt(nt))))
+
+
+# fields the sweep holds besides the states: the coefficient (and Cs), the residual,
+# ybar / Tbar, dL/dCi (or dL/dCs) and the two gradients returned
+WORK_FIELDS = 8
+
+
+def choose_every(nt: int, field_bytes: int, free_bytes: int, margin: float = 0.8) -> int:
+    """1 (every state kept) when nt state fields and the sweep's working fields fit in
+    ``margin`` of ``free_bytes``; else the sqrt(nt) interval."""
+    if (nt + WORK_FIELDS) * field_bytes <= margin * free_bytes:
+        return 1
+    return default_every(nt)
+
+
+def auto_every(T0: torch.Tensor, nt: int) -> int:
+    """Checkpoint interval for T0's device: free memory as the driver reports it plus
+    what the caching allocator holds unused."""
+    if not T0.is_cuda:
+        return default_every(nt)
+    free, _ = torch.cuda.mem_get_info(T0.device)
+    free += torch.cuda.memory_reserved(T0.device) - torch.cuda.memory_allocated(T0.device)
+    return choose_every(nt, T0.numel() * T0.element_size(), free)
 
 
 def coefficient(Ci, lam, dt, inv):
@@ -91,7 +117,7 @@ class Diffusion3DFn(torch.autograd.Function):
     def forward(ctx, T0, Ci, lam, dt, inv_spacing, nt, every=None):
         T0 = T0.detach().contiguous()
         Ci = Ci.detach().contiguous()
-        every = default_every(nt) if every is None else int(every)
+        every = auto_every(T0, int(nt)) if every is None else int(every)
         coef = coefficient(Ci, lam, dt, tuple(inv_spacing))
         out, ckpts = forward_checkpointed(T0, Ci, lam, dt, tuple(inv_spacing), int(nt), every, coef)
         ctx.cfg = (lam, dt, tuple(inv_spacing), int(nt), every)
@@ -112,8 +138,9 @@ class Diffusion3DFn(torch.autograd.Function):
 
 
 def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None):
-    """L = 1/2||T(nt) - Tobs||^2 (FP64 on the GPU) and (dL/dT0, dL/dCi)."""
-    every = default_every(nt) if every is None else int(every)
+    """L = 1/2||T(nt) - Tobs||^2 (FP64 on the GPU) and (dL/dT0, dL/dCi); ``every``
+    as for :class:`Diffusion3DFn` (None: every state kept when it fits)."""
+    every = auto_every(T0, int(nt)) if every is None else int(every)
     inv = tuple(inv_spacing)
     coef = coefficient(Ci.contiguous(), lam, dt, inv)
     out, ckpts = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef)

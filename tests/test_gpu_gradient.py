@@ -150,3 +150,16 @@ def test_adjoint_short_z_chunks(monkeypatch, kchunk):
         assert rel_linf(to_host(Tbar), ref) <= tol
         assert np.max(np.abs(to_host(C) - cib)) <= tol * np.max(np.abs(cib))
     assert api.device_error() == 0
+
+
+def test_default_interval_keeps_every_state_when_it_fits():
+    """every=None: a small grid's nt states fit, so every state is kept (interval 1);
+    the gradient equals the sqrt(nt)-checkpoint one bit for bit."""
+    nx, ny, nz, nt = 24, 14, 18, 13
+    T0, Ci, Tobs, lam, dt, inv = inverse_problem(nx, ny, nz, nt)
+    assert ag.auto_every(to_dev(T0), nt) == 1
+    auto = ag.loss_and_grad(to_dev(T0), to_dev(Ci), to_dev(Tobs), lam, dt, inv, nt)
+    sq = ag.loss_and_grad(to_dev(T0), to_dev(Ci), to_dev(Tobs), lam, dt, inv, nt,
+                          every=ag.default_every(nt))
+    for a, b in zip(auto, sq):
+        assert torch.equal(a, b)
