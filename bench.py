@@ -385,18 +385,34 @@ def oracle_sample(T0, Ci, inv, steps, threads):
     return el
 
 
-def cpu_baseline(T0, Ci, inv, budget_s=15.0):
-    import oracle
-    threads = max(1, oracle.max_threads())
+def oracle_rate(T0, Ci, inv, threads, budget_s):
+    """(T_eff GB/s, steps, seconds) of the FP64 oracle on `threads` host threads, for about
+    budget_s seconds of steps (one probe step sizes the sample)."""
     n = T0.shape[0]
     t1 = oracle_sample(T0, Ci, inv, 1, threads)
     steps = int(max(1, min(100, budget_s / max(t1, 1e-3))))
     el = oracle_sample(T0, Ci, inv, steps, threads)
-    gbs = 3 * n ** 3 * 8 * steps / el / 1e9
+    return 3 * n ** 3 * 8 * steps / el / 1e9, steps, el
+
+
+def cpu_baseline(T0, Ci, inv, budget_s=15.0):
+    """The oracle on all host cores (OpenMP over z) on the benchmark's fields; beside it the
+    serial oracle on the same fields and both on the 256^3 fields (a few seconds each)."""
+    import oracle
+    threads = max(1, oracle.max_threads())
+    n = T0.shape[0]
+    gbs, steps, el = oracle_rate(T0, Ci, inv, threads, budget_s)
+    serial, s_steps, _ = oracle_rate(T0, Ci, inv, 1, 5.0)
+    T0s, Cis, invs = fields(256)
+    omp256, _, _ = oracle_rate(T0s, Cis, invs, threads, 2.0)
+    serial256, _, _ = oracle_rate(T0s, Cis, invs, 1, 3.0)
     oracle.set_threads(1)
     return {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
             "sample": f"{steps} FP64 oracle steps (plus the initial copy) on the full {n}^3 fields, "
-                      f"{el:.1f} s on {threads} host threads"}
+                      f"{el:.1f} s on {threads} host threads",
+            "serial_value": round(serial, 3),
+            "serial_sample": f"{s_steps} steps on the same fields, 1 thread",
+            "at_256": {"value": round(omp256, 3), "serial_value": round(serial256, 3)}}
 
 
 def run_reference(args):
