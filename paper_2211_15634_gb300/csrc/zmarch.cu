@@ -184,7 +184,8 @@ cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const v
     // Isotropic FP64 grids default to fma(Ci*K, S, T) (two FP64 ops, fewest
     // integer ops: measured fastest).  PS_F64_VARIANT selects an alternative
     // for measurements: "umul" = one DFMA plus a 64-bit high multiply,
-    // "by16" = 64 x 16 tiles; "px2" keeps the pre-scaled step at two nodes per thread.
+    // "by16" = the umul form in 64 x 16 tiles; "px2" keeps the pre-scaled step at two
+    // nodes per thread.
     const char *var = getenv("PS_F64_VARIANT");
     const bool dmul = !(var && (strcmp(var, "umul") == 0 || strcmp(var, "by16") == 0));
     const bool by16 = var && strcmp(var, "by16") == 0;
