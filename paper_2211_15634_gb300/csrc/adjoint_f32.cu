@@ -594,11 +594,19 @@ static cudaError_t launch_adj32_t(float *Tbar, float *Cibar, const float *ybar, 
         return cudaErrorInvalidValue;
     const int64_t ntx = (g.nx + BX - 1) / BX, nty = (g.ny + BY - 1) / BY, tiles = ntx * nty;
     if (kchunk <= 0) {
-        // 16-plane chunks (each chunk re-reads two planes); 32 where 16 would leave
-        // fewer than four waves of CTAs and 32 still gives one and a half.  Measured:
-        // 128^3 best at 16, 256^3 at 32 (5% ahead of 16), 512^3 and 768^3 at 16 (1-4%).
+        // One wave when it takes chunks of 32-96 planes: every tile's z-range split into
+        // as many chunks as there are CTA slots per tile, all CTAs resident at once (no
+        // tail).  Else 16-plane chunks (each chunk re-reads two planes); 32 where 16
+        // would leave fewer than four waves of CTAs and 32 still gives one and a half.
+        // Measured: 128^3 best at 16, 256^3 at 64 (one wave; 4.5% ahead of 32, 8% of
+        // 16), 512^3 and 768^3 at 16-24 (within 1%).
         const int64_t slots = (int64_t)MINB * sm_count(), cols = g.nz * tiles;
-        kchunk = (cols < 4 * 16 * slots && 2 * cols >= 3 * 32 * slots) ? 32 : 16;
+        const int64_t per_tile = tiles > 0 ? slots / tiles : 0;
+        const int64_t one_wave = per_tile > 0 ? (g.nz + per_tile - 1) / per_tile : 0;
+        if (one_wave >= 32 && one_wave <= 96)
+            kchunk = (int)one_wave;
+        else
+            kchunk = (cols < 4 * 16 * slots && 2 * cols >= 3 * 32 * slots) ? 32 : 16;
     }
     const int64_t gz = (g.nz + kchunk - 1) / kchunk;
     if (tiles > 0x7fffffffLL || gz > 65535) return cudaErrorInvalidConfiguration;
