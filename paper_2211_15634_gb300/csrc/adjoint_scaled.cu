@@ -345,9 +345,26 @@ cudaError_t launch_adjoint_scaled(double *Tbar, double *Csbar, const double *yba
     int kchunk = v ? atoi(v) : 0;
     if (kchunk <= 0) {
         // long z-chunks amortise the two prologue planes; keep at least ~3 waves of CTAs
-        const int64_t waves = 3LL * 3 * sm_count();
-        const int64_t kc = g.nz * tiles / waves;
-        kchunk = (int)(kc < 4 ? 4 : (kc > 16 ? 16 : kc));
+        // (3 per SM).  Where chunks of 16 planes or more keep that many, take the chunk
+        // of 16-24 planes whose last wave is fullest: measured 256^3 at 19 planes
+        // (3.93 waves) 0.1734 ms against 0.1777 at 16 (4.49 waves); 512^3 at 22-24
+        // planes 1.5% ahead of 16.
+        const int64_t slots = 3LL * sm_count();
+        const int64_t kc = g.nz * tiles / (3 * slots);
+        if (kc < 16) {
+            kchunk = (int)(kc < 4 ? 4 : kc);
+        } else {
+            kchunk = 16;
+            int64_t best = -1;
+            for (int c = 16; c <= 24; ++c) {
+                const int64_t ctas = tiles * ((g.nz + c - 1) / c);
+                const int64_t last = ctas % slots == 0 ? slots : ctas % slots;  // CTAs in the last wave
+                if (last > best) {
+                    best = last;
+                    kchunk = c;
+                }
+            }
+        }
     }
     const int64_t gz = (g.nz + kchunk - 1) / kchunk;
     if (tiles > 0x7fffffffLL || gz > 65535) return cudaErrorInvalidConfiguration;
