@@ -1,9 +1,9 @@
 // 2-D form of the step (Fig. 1's step! with the z term dropped) as a warp-level
 // y-march.
 //
-// Warp w owns a strip of 32*PX columns (PX nodes per lane: two 16-byte accesses in
-// FP32, one in FP64, when the rows allow them, else PX = 1) and a chunk of interior
-// rows [j0, j1).  Each
+// Warp w owns a strip of 32*PX columns (PX nodes per lane: two 16-byte accesses when
+// the rows allow them - eight FP32 or four FP64 nodes - else PX = 1) and a chunk of
+// interior rows [j0, j1).  Each
 // lane keeps its own values of rows j-1, j, j+1 and Ci of row j in registers and
 // loads row j+2 and Ci of row j+1 while it computes row j: plain coalesced loads,
 // no shared memory and no barriers - the x-neighbours come from the neighbouring
@@ -110,9 +110,11 @@ __device__ __forceinline__ void load_row(E (&v)[PX], const E *__restrict__ A, in
     for (int i = 0; i < PX; ++i) v[i] = x + i < nx ? __ldg(q + i) : E(0);
 }
 
-// 3 CTAs of 8 warps per SM: the FP64 emulated modes spill at 4 (measured 4% slower there)
-template <int MODE, int PX>
-__global__ void __launch_bounds__(256, 3)
+// MINB CTAs of 8 warps per SM: 3 for two FP64 / eight FP32 nodes per lane and the
+// scalar forms (the FP64 emulated modes spill at 4, measured 4% slower there); 2 for four
+// FP64 nodes per lane (111 registers, no spill)
+template <int MODE, int PX, int MINB = 3>
+__global__ void __launch_bounds__(256, MINB)
 k_ymarch2d(typename M2D<MODE>::E *__restrict__ T2, const typename M2D<MODE>::E *__restrict__ T,
            const typename M2D<MODE>::E *__restrict__ Ci, const P2D p) {
     using E = typename M2D<MODE>::E;
@@ -251,7 +253,7 @@ __global__ void k_copy_edges2d(E *__restrict__ T2, const E *__restrict__ T, int6
     }
 }
 
-template <int MODE, int PX>
+template <int MODE, int PX, int MINB = 3>
 static cudaError_t launch_2d_t(void *T2, const void *T, const void *Ci, P2D p, int64_t nx, int64_t ny,
                                cudaStream_t s) {
     using E = typename M2D<MODE>::E;
@@ -269,7 +271,7 @@ static cudaError_t launch_2d_t(void *T2, const void *T, const void *Ci, P2D p, i
     p.chunk = chunk;
     const int64_t nch = (ny - 2 + chunk - 1) / chunk, warps = nch * p.nstrips, blocks = (warps + 7) / 8;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_ymarch2d<MODE, PX><<<(unsigned)blocks, 256, 0, s>>>((E *)T2, (const E *)T, (const E *)Ci, p);
+    k_ymarch2d<MODE, PX, MINB><<<(unsigned)blocks, 256, 0, s>>>((E *)T2, (const E *)T, (const E *)Ci, p);
     return cudaGetLastError();
 }
 
@@ -288,16 +290,19 @@ cudaError_t launch_step2d(int mode, void *T2, const void *T, const void *Ci, Ste
     switch (mode) {
         case Z_F32:
             // eight nodes per lane (two 16-byte accesses): measured 7-9% faster than four at
-            // 16384^2 and 32768^2; FP64 keeps two per lane (four spilled and ran 25% slower)
+            // 16384^2 and 32768^2
             return vec ? launch_2d_t<Z_F32, 8>(T2, T, Ci, p, nx, ny, s) : launch_2d_t<Z_F32, 1>(T2, T, Ci, p, nx, ny, s);
+        // FP64: four nodes per lane (two 16-byte accesses) at two CTAs per SM, measured 8%
+        // faster than two per lane at three CTAs per SM at 16384^2 (6% at 8192^2); four per
+        // lane at three CTAs per SM spilled and ran 25% slower
         case Z_F64_SCALED:
-            return vec ? launch_2d_t<Z_F64_SCALED, 2>(T2, T, Ci, p, nx, ny, s)
+            return vec ? launch_2d_t<Z_F64_SCALED, 4, 2>(T2, T, Ci, p, nx, ny, s)
                        : launch_2d_t<Z_F64_SCALED, 1>(T2, T, Ci, p, nx, ny, s);
         case Z_F64_EMU_ISO_DMUL:
-            return vec ? launch_2d_t<Z_F64_EMU_ISO_DMUL, 2>(T2, T, Ci, p, nx, ny, s)
+            return vec ? launch_2d_t<Z_F64_EMU_ISO_DMUL, 4, 2>(T2, T, Ci, p, nx, ny, s)
                        : launch_2d_t<Z_F64_EMU_ISO_DMUL, 1>(T2, T, Ci, p, nx, ny, s);
         default:
-            return vec ? launch_2d_t<Z_F64_NATIVE, 2>(T2, T, Ci, p, nx, ny, s)
+            return vec ? launch_2d_t<Z_F64_NATIVE, 4, 2>(T2, T, Ci, p, nx, ny, s)
                        : launch_2d_t<Z_F64_NATIVE, 1>(T2, T, Ci, p, nx, ny, s);
     }
 }
