@@ -1,0 +1,34 @@
+"""Host-side layout helpers of the Python binding: padded-row fields for the
+batched z-march and the pitch the binding derives from a field's strides."""
+import pytest
+import torch
+
+from paper_2211_15634_gb300 import api
+
+
+@pytest.mark.parametrize("dtype,per", [(torch.float64, 2), (torch.float32, 4)])
+@pytest.mark.parametrize("nx", [3, 4, 5, 33, 64, 161])
+def test_pitched_rows_start_on_16_byte_boundaries(dtype, per, nx):
+    t = api.pitched_empty((5, 7, nx), dtype, device="cpu")
+    assert t.shape == (5, 7, nx)
+    pitch = api._pitch(t, "T")
+    assert pitch >= nx and pitch - nx < per and pitch * t.element_size() % 16 == 0
+    assert t.stride() == (7 * pitch, pitch, 1)
+    assert (pitch == nx) == t.is_contiguous()
+
+
+def test_pitched_copy_keeps_values():
+    a = torch.arange(3 * 4 * 5, dtype=torch.float64).reshape(3, 4, 5)
+    b = api.pitched_copy(a)
+    assert torch.equal(a, b) and api._pitch(b, "T") == 6
+
+
+def test_pitch_rejects_other_layouts():
+    a = torch.zeros((4, 6, 8), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        api._pitch(a[:, :, ::2], "T")  # strided along x
+    with pytest.raises(ValueError):
+        api._pitch(a[:, :3, :], "T")  # rows cut, planes not rows*ny apart
+    with pytest.raises(ValueError):
+        api._pitch(a[0], "T")  # not 3-D
+    assert api._pitch(a, "T") == 8
