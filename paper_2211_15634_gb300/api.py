@@ -301,6 +301,72 @@ def stable_dt(Ci, lam: float = 1.0, lengths=(1.0, 1.0, 1.0)) -> float:
     return v.value
 
 
+class SolvePipeline:
+    """End-to-end solves of many problems of one shape, with the host copies hidden
+    behind the computation.
+
+    Each :meth:`submit` does what :func:`solve` does for one problem - copy T0 and
+    Ci in from pinned host memory, dt from maximum(Ci) on the GPU, the pre-scaled
+    coefficient (FP64, equal spacings), the nt steps (cached CUDA graph), copy
+    T(nt) out to ``out_host`` - but the copies in run on their own stream into one
+    of two device buffer sets and the copy out on a third stream, so that the
+    inputs of problem i+1 arrive and the result of problem i-1 leaves while problem
+    i computes.  Stream order and events keep every buffer's uses in order: problem
+    i+2 overwrites a buffer set only after problem i's result has been copied out.
+    ``submit`` returns the event recorded after the copy out (``out_host`` is valid
+    once it has completed); :meth:`finish` waits for every submitted problem.  The
+    host blocks only inside ``submit``, on the maximum(Ci) of its own problem.
+    ``graph=True`` replays the nt steps from the library's graph cache, whose key
+    holds dt: worth it only for small grids whose problems share dt (each new dt
+    captures a graph); by default the steps are launched from the library's loop,
+    which keeps the GPU fed whenever a step takes longer than a launch.
+    """
+
+    def __init__(self, shape, dtype, lam: float, inv_spacing, nt: int, *, device="cuda",
+                 graph: bool = False, lengths=(1.0, 1.0, 1.0)):
+        self.lam, self.inv, self.nt, self.graph, self.lengths = lam, tuple(inv_spacing), int(nt), graph, lengths
+        self.device = torch.device(device)
+        self.sets = [tuple(torch.empty(shape, dtype=dtype, device=self.device) for _ in range(3))
+                     for _ in range(2)]
+        self.s_in = torch.cuda.Stream(self.device)
+        self.s_run = torch.cuda.Stream(self.device)
+        self.s_out = torch.cuda.Stream(self.device)
+        self.freed = [None, None]  # per set: event after its last result was copied out
+        self.count = 0
+        self.scaled = dtype == torch.float64 and self.inv[0] == self.inv[1] == self.inv[2]
+
+    def submit(self, T0_host: torch.Tensor, Ci_host: torch.Tensor, out_host: torch.Tensor):
+        k = self.count % 2
+        T, T2, Ci = self.sets[k]
+        with torch.cuda.stream(self.s_in):
+            if self.freed[k] is not None:
+                self.s_in.wait_event(self.freed[k])
+            T.copy_(T0_host, non_blocking=True)
+            Ci.copy_(Ci_host, non_blocking=True)
+            arrived = torch.cuda.Event()
+            arrived.record(self.s_in)
+        with torch.cuda.stream(self.s_run):
+            self.s_run.wait_event(arrived)
+            dt = stable_dt(Ci, self.lam, self.lengths)  # waits for this stream only
+            if self.scaled:
+                scale_ci(Ci, self.lam, dt, self.inv, out=Ci)
+            res = run(T, T2, Ci, self.lam, dt, self.inv, self.nt, graph=self.graph, ci_scaled=self.scaled)
+            done = torch.cuda.Event()
+            done.record(self.s_run)
+        with torch.cuda.stream(self.s_out):
+            self.s_out.wait_event(done)
+            out_host.copy_(res, non_blocking=True)
+            out = torch.cuda.Event()
+            out.record(self.s_out)
+        self.freed[k] = out
+        self.count += 1
+        return out
+
+    def finish(self) -> None:
+        for s in (self.s_in, self.s_run, self.s_out):
+            s.synchronize()
+
+
 def dot(A, B, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """sum(A*B) accumulated in FP64, as a 0-dim device tensor."""
     code = _code(A)
