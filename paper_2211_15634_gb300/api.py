@@ -335,7 +335,20 @@ class SolvePipeline:
         self.count = 0
         self.scaled = dtype == torch.float64 and self.inv[0] == self.inv[1] == self.inv[2]
 
+    @staticmethod
+    def check_host(shape, dtype, **tensors) -> None:
+        """Host tensors of a submit: CPU tensors of the pipeline's exact shape and dtype
+        (a copy would otherwise broadcast or convert silently)."""
+        for name, t in tensors.items():
+            if t.device.type != "cpu":
+                raise ValueError(f"{name} must be a host (CPU) tensor, pinned for overlap")
+            if tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+                raise ValueError(f"{name} has shape {tuple(t.shape)} and dtype {t.dtype}; "
+                                 f"the pipeline takes {tuple(shape)} {dtype}")
+
     def submit(self, T0_host: torch.Tensor, Ci_host: torch.Tensor, out_host: torch.Tensor):
+        self.check_host(self.sets[0][0].shape, self.sets[0][0].dtype, T0_host=T0_host, Ci_host=Ci_host,
+                        out_host=out_host)
         k = self.count % 2
         T, T2, Ci = self.sets[k]
         with torch.cuda.stream(self.s_in):

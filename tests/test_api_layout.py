@@ -32,3 +32,14 @@ def test_pitch_rejects_other_layouts():
     with pytest.raises(ValueError):
         api._pitch(a[0], "T")  # not 3-D
     assert api._pitch(a, "T") == 8
+
+
+def test_solve_pipeline_rejects_mismatched_host_tensors():
+    ok = torch.zeros((4, 5, 6), dtype=torch.float64)
+    api.SolvePipeline.check_host((4, 5, 6), torch.float64, T0_host=ok, Ci_host=ok, out_host=ok)
+    with pytest.raises(ValueError):  # would broadcast
+        api.SolvePipeline.check_host((4, 5, 6), torch.float64, T0_host=torch.zeros((1, 5, 6), dtype=torch.float64))
+    with pytest.raises(ValueError):  # would convert
+        api.SolvePipeline.check_host((4, 5, 6), torch.float64, Ci_host=ok.float())
+    with pytest.raises(ValueError):
+        api.SolvePipeline.check_host((4, 5, 6), torch.float64, out_host=torch.zeros((4, 5, 6, 1), dtype=torch.float64))
