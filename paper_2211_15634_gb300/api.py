@@ -51,14 +51,18 @@ def _stream(t: torch.Tensor) -> int:
 
 
 def workspace(device) -> torch.Tensor:
-    """Per-device scratch buffer for the reductions (allocated once, reused)."""
+    """Scratch buffer of the reductions for the device's current stream (allocated
+    once per device and stream, 16 KB, reused): reductions running on different
+    streams at the same time, e.g. in two :class:`SolvePipeline` objects, never share
+    one."""
     device = torch.device(device)
     idx = device.index if device.index is not None else torch.cuda.current_device()
-    ws = _WS.get(idx)
+    key = (idx, torch.cuda.current_stream(idx).cuda_stream)
+    ws = _WS.get(key)
     if ws is None:
         n = _lib.load().ps_workspace_bytes()
         ws = torch.empty(n, dtype=torch.uint8, device=f"cuda:{idx}")
-        _WS[idx] = ws
+        _WS[key] = ws
     return ws
 
 
