@@ -84,7 +84,10 @@ int ps_version(void);
  * ("" if none).  The pointer stays valid until the thread's next call. */
 const char *ps_last_error(void);
 
-/* Bytes of device workspace the reduction entry points need. */
+/* Bytes of device workspace the reduction entry points need.  A reduction
+ * reads and writes its workspace on its stream until it completes: one
+ * workspace must not serve two reductions that may run at the same time (on
+ * different streams); give each stream its own. */
 size_t ps_workspace_bytes(void);
 
 /* Device-side error flags of the current device, to *out_host (host
