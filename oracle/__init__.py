@@ -15,8 +15,8 @@ Entry points and the passages they follow:
 * :func:`run` - Fig. 1 time loop: ``T2 = copy(T)``, then step and swap.
 * :func:`adjoint_step` - transpose of one ``step!`` (derived, no paper line).
 * :func:`gradient` - L = 1/2||T(nt)-T_obs||^2 and its gradient in T0 and Ci.
-* :func:`step2d`, :func:`run2d` - the 2-D form of Fig. 1's ``step!`` (the z term
-  dropped; arrays of shape ``(ny, nx)``) and its time loop.
+* :func:`stable_dt2d`, :func:`step2d`, :func:`run2d` - the 2-D form of Fig. 1's ``step!`` (the z term
+  dropped; arrays of shape ``(ny, nx)``), its ``dt`` and its time loop.
 """
 from __future__ import annotations
 
@@ -60,6 +60,8 @@ def _load():
             lib.or_maximum.restype = d
             lib.or_stable_dt.argtypes = [d, d, d, d, d]
             lib.or_stable_dt.restype = d
+            lib.or_stable_dt2d.argtypes = [d, d, d, d]
+            lib.or_stable_dt2d.restype = d
             lib.or_step.argtypes = [p, p, p, d, d, d, d, d, i64, i64, i64]
             lib.or_run.argtypes = [p, p, p, d, d, d, d, d, i64, i64, i64, i32]
             lib.or_run.restype = i32
@@ -158,6 +160,11 @@ def loss(T: np.ndarray, Tobs: np.ndarray) -> float:
     """``1/2 ||T - Tobs||^2`` in FP64 (numpy dot of the residual)."""
     r = (T - Tobs).ravel()
     return 0.5 * float(np.dot(r, r))
+
+
+def stable_dt2d(dx: float, dy: float, lam: float, maxCi: float) -> float:
+    """2-D form of Fig. 1's ``dt`` line: ``min(dx^2,dy^2)/lam/maximum(Ci)/4.1``."""
+    return _load().or_stable_dt2d(dx, dy, lam, maxCi)
 
 
 def _f64_2d(a: np.ndarray, name: str) -> np.ndarray:

@@ -106,6 +106,16 @@ int or_run(double *T, double *T2, const double *Ci, double lam, double dt,
     return cur == T2;
 }
 
+/* 2-D form of Fig. 1's dt line (a reading: the paper's solver is 3-D): the
+ * explicit scheme on two axes is stable while dt*lam*Ci*(2/dx^2 + 2/dy^2) <= 1,
+ * and 4.1 stands to that bound (4 for equal spacings) as Fig. 1's 6.1 stands to
+ * the three-axis bound 6: dt = min(dx^2,dy^2)/lam/maximum(Ci)/4.1. */
+double or_stable_dt2d(double dx, double dy, double lam, double maxCi) {
+    double m = dx * dx;
+    if (dy * dy < m) m = dy * dy;
+    return m / lam / maxCi / 4.1;
+}
+
 /* 2-D form of Fig. 1's step!: the same update with the z term dropped, i.e. the
  * kernel with FiniteDifferences2D and the dimension argument of the initialization
  * call set to 2 (Fig. 1 shows 3):

@@ -104,3 +104,29 @@ def test_step_writes_interior_only(oracle_mod):
     T2 = np.full_like(T0, -5.0)
     oracle_mod.step2d(T2, T0, Ci, 1.0, dt, *inv)
     assert np.all(T2[~interior2d(nx, ny)] == -5.0) and np.all(T2[interior2d(nx, ny)] != -5.0)
+
+
+@pytest.mark.parametrize("shape", [(17, 17), (31, 9), (8, 40)])
+def test_stable_dt2d_is_just_inside_the_stability_bound(oracle_mod, shape):
+    """The 2-D dt keeps the explicit scheme stable with a small margin: the
+    highest-frequency Dirichlet mode (a checkerboard in the interior) decays under
+    the oracle's dt.  On equal spacings it grows under 1.06 times that dt (the
+    margin is small); on unequal spacings it grows under the dt the larger spacing
+    would give (the smaller spacing sets dt)."""
+    nx, ny = shape
+    lam, Ci0 = 0.7, 0.45
+    dx, dy = 1.0 / (nx - 1), 1.0 / (ny - 1)
+    Ci = np.full((ny, nx), Ci0)
+    dt = oracle_mod.stable_dt2d(dx, dy, lam, oracle_mod.maximum(Ci))
+    kx, ky = nx - 2, ny - 2  # highest interior frequencies
+    sx = np.sin(kx * np.pi * np.arange(nx) * dx)
+    sy = np.sin(ky * np.pi * np.arange(ny) * dy)
+    mode = sy[:, None] * sx[None, :]
+    mode[~interior2d(nx, ny)] = 0.0
+    amp = np.max(np.abs(mode))
+    nt = 40
+    stable = oracle_mod.run2d(mode, Ci, lam, dt, 1 / dx, 1 / dy, nt)
+    assert np.max(np.abs(stable)) < amp
+    grow = 1.06 if nx == ny else max(dx, dy) ** 2 / min(dx, dy) ** 2
+    unstable = oracle_mod.run2d(mode, Ci, lam, grow * dt, 1 / dx, 1 / dy, nt)
+    assert np.max(np.abs(unstable)) > amp
