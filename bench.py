@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--no-secondary", action="store_true", help="skip FP32 / gradient / batch lines")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
-    p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint2", "batch", "step2d"],
+    p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint_fx", "adjoint2", "batch", "step2d"],
                    default=None,
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON); "
                         "step2d on a --size^2 grid")
@@ -61,6 +61,9 @@ def parse_args():
                    help="kernel loop step: fused step pairs (each rep is two two-step passes)")
     p.add_argument("--plain-ci", action="store_true",
                    help="kernel loop: FP64 step/adjoint/batch on Ci as given instead of the pre-scaled field")
+    p.add_argument("--zslab", action="store_true",
+                   help="one problem of 512 x 512 x (510 N + 2) nodes split into z-slabs over the N "
+                        "ranks (each rank 512^3 with its halos), halo exchange per step (NCCL)")
     p.add_argument("--batch-kernel", choices=["zmarch", "column"], default="zmarch",
                    help="kernel loop batch: the TMA z-march on padded rows, or the column march")
     return p.parse_args()
@@ -96,6 +99,15 @@ def run_kernel_loop(args):
                 api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
         name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled,
                                     temporal2=args.temporal2)
+    elif args.kernel_loop == "adjoint_fx":
+        # FP64: the fixed-point reverse sweep's transposed step on the pre-scaled coefficient
+        Cs = api.scale_ci(C, 1.0, dt, inv)
+        sw = api.FixedPointSweep(T)
+        sw.start(T2 - T.mean())
+        Cib = torch.zeros_like(T)
+        for _ in range(args.reps):
+            sw.step(Cib, T, Cs)
+        name = "adjoint_fx (fixed-point sweep)"
     elif args.kernel_loop == "adjoint2":
         # FP32: two transposed steps per pass (states T and T2)
         if args.dtype != "f32":
@@ -456,25 +468,73 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- our path
-def torch_eager_teff(torch, T, T2, C, dt, inv, timed, nt=10):
-    """Fig. 1's step written as whole-field PyTorch slice expressions (one kernel per
-    operation, the analogue of the paper's GPU array-broadcast comparison), timed on
-    the same fields; T_eff by the same 3-array count."""
-    n = T.shape[0]
+def torch_eager_step(Ta, Tb, C, lam, dt, inv):
+    """Fig. 1's step! written as whole-field PyTorch slice expressions on (nz, ny, nx)
+    tensors (one kernel per operation): the analogue of the paper's GPU array-broadcast
+    comparison solver.  Writes Tb's interior from Ta; Tb's boundary is left as it is.
+    Same association order as Fig. 1: T + dt*(lam*Ci*((d2x*_dx^2 + d2y*_dy^2) + d2z*_dz^2))."""
     ax, ay, az = (v * v for v in inv)
+    c = Ta[1:-1, 1:-1, 1:-1]
+    d2x = (Ta[1:-1, 1:-1, 2:] - c) - (c - Ta[1:-1, 1:-1, :-2])
+    d2y = (Ta[1:-1, 2:, 1:-1] - c) - (c - Ta[1:-1, :-2, 1:-1])
+    d2z = (Ta[2:, 1:-1, 1:-1] - c) - (c - Ta[:-2, 1:-1, 1:-1])
+    Tb[1:-1, 1:-1, 1:-1] = c + dt * (lam * C[1:-1, 1:-1, 1:-1] * ((d2x * ax + d2y * ay) + d2z * az))
 
-    def step(Ta, Tb):
-        c = Ta[1:-1, 1:-1, 1:-1]
-        d2x = (Ta[1:-1, 1:-1, 2:] - c) - (c - Ta[1:-1, 1:-1, :-2])
-        d2y = (Ta[1:-1, 2:, 1:-1] - c) - (c - Ta[1:-1, :-2, 1:-1])
-        d2z = (Ta[2:, 1:-1, 1:-1] - c) - (c - Ta[:-2, 1:-1, 1:-1])
-        Tb[1:-1, 1:-1, 1:-1] = c + dt * (1.0 * C[1:-1, 1:-1, 1:-1] * ((d2x * ax + d2y * ay) + d2z * az))
 
-    def loop():
-        for it in range(nt):
-            step(T, T2) if it % 2 == 0 else step(T2, T)
-    t = timed(loop, reps=2)
+def torch_eager_run(T, T2, C, lam, dt, inv, nt):
+    """nt eager steps with the buffers swapped (T2's boundary must equal T's); returns
+    the tensor holding T(nt)."""
+    for it in range(nt):
+        if it % 2 == 0:
+            torch_eager_step(T, T2, C, lam, dt, inv)
+        else:
+            torch_eager_step(T2, T, C, lam, dt, inv)
+    return T2 if nt % 2 else T
+
+
+def torch_eager_teff(torch, T, T2, C, dt, inv, timed, nt=10):
+    """T_eff of the eager slice-expression solver on the same fields, by the same
+    3-array count (checked against the oracle in the GPU tests)."""
+    n = T.shape[0]
+    t = timed(lambda: torch_eager_run(T, T2, C, 1.0, dt, inv, nt), reps=2)
     return round(3 * n ** 3 * T.element_size() * nt / t / 1e9, 1)
+
+
+def general_path_warp_fraction(torch, T):
+    """Share of the warp-planes of the pre-scaled FP64 step (k_zmarch<F64_SCALED4>: a warp
+    owns 128 consecutive nodes of a row, four per lane) in which some lane's stencil
+    values do not all share the sign and exponent of its first centre, so that the
+    warp takes the general fixed-point path - on the field T as given (a host-side
+    count over the field, not a device counter; nodes at the x edges are counted like
+    the others)."""
+    n = T.shape[2]
+    H = ((T.view(torch.int64) >> 52) & 0xFFF).to(torch.int16)
+    L = n // 4
+    A = H[1:-1, 1:-1, :].reshape(n - 2, n - 2, L, 4)
+    ref = A[..., 0]
+    f = (A == ref[..., None]).all(-1)
+    for nb in (H[1:-1, :-2, :], H[1:-1, 2:, :], H[:-2, 1:-1, :], H[2:, 1:-1, :]):
+        f &= (nb.reshape(n - 2, n - 2, L, 4) == ref[..., None]).all(-1)
+    f[..., 1:] &= A[..., :-1, 3] == ref[..., 1:]
+    f[..., :-1] &= A[..., 1:, 0] == ref[..., :-1]
+    pad = (-L) % 32  # lanes past the grid's last tile compute nothing
+    if pad:
+        f = torch.cat([f, torch.ones(n - 2, n - 2, pad, dtype=torch.bool, device=f.device)], dim=-1)
+    warp_fast = f.reshape(n - 2, n - 2, (L + pad) // 32, 32).all(-1)
+    return round(1.0 - float(warp_fast.float().mean()), 4)
+
+
+def general_path_fields(torch, n, dev):
+    """Fields on which the FP64 step leaves the one-binade fast path: the sine mode
+    shifted to cross zero, sin(pi x) sin(pi y) sin(pi z) - 1/2 (signs and many binades
+    near its zero set), and the Gaussian stored as its deviation from 1.7 in FP64
+    (exp(-r^2/0.01): positive, but a new binade every few nodes in its tails)."""
+    from paper_2211_15634_gb300 import inputs
+    x = torch.from_numpy(inputs.node_coords(n)).to(dev)
+    s = torch.sin(torch.pi * x)
+    yield "sine", (s[:, None, None] * s[None, :, None] * s[None, None, :] - 0.5).contiguous()
+    d = (x - 0.5) ** 2
+    yield "gauss_dev", torch.exp(-((d[:, None, None] + d[None, :, None]) + d[None, None, :]) / 0.01).contiguous()
 
 
 def secondary_metrics(torch, api, ag, inputs, log):
@@ -512,13 +572,23 @@ def secondary_metrics(torch, api, ag, inputs, log):
     out["fp64_512_temporal2_teff_gbs"] = round(3 * n ** 3 * 8 * nt / t / 1e9, 1)
     # the same step as plain PyTorch tensor expressions (slices of the whole field)
     out["fp64_512_torch_eager_teff_gbs"] = torch_eager_teff(torch, T, T2, C, dt, inv, timed)
+    # the headline field's share of warps on the general path, then the same pre-scaled
+    # step on fields that leave one binade (general fixed-point path)
+    out["fp64_512_gauss_general_warp_fraction"] = general_path_warp_fraction(torch, T)
+    for name, Tg in general_path_fields(torch, n, dev):
+        out[f"fp64_512_{name}_general_warp_fraction"] = general_path_warp_fraction(torch, Tg)
+        T2.copy_(Tg)
+        t = timed(lambda: api.run(Tg, T2, Cs, 1.0, dt, inv, nt, graph=True, ci_scaled=True))
+        out[f"fp64_512_{name}_teff_gbs"] = round(3 * n ** 3 * 8 * nt / t / 1e9, 1)
+        del Tg
+        api.clear_graph_cache()
     del T2, Cs
     api.clear_graph_cache()
     D = api.to_deviation(T, 1.7)
     C32 = api.to_f32(C)
     del T, C
     D2 = D.clone()
-    comp = torch.zeros_like(D)
+    comp = api.compensation_fields(D)
     dt = api.stable_dt(C32, 1.0)
     t = timed(lambda: api.run(D, D2, C32, 1.0, dt, inv, nt, graph=True))
     out["fp32_512_teff_gbs"] = round(3 * n ** 3 * 4 * nt / t / 1e9, 1)
@@ -551,7 +621,11 @@ def secondary_metrics(torch, api, ag, inputs, log):
         api.clear_graph_cache()
         torch.cuda.empty_cache()
 
-    # FP32 error against the FP64 oracle at 256^3 (nt = 100 and 1000, plain and compensated)
+    # FP32 error against the FP64 oracle at 256^3 (nt = 100 and 1000), plain and compensated
+    # (two-float state started from the two-float deviation of T0), each split in two:
+    #   arithmetic: the oracle run on exactly the state the GPU starts from (D0, or D0 + E0,
+    #               in FP64) and on the FP32-rounded Ci - the step's own roundings only;
+    #   storage:    the oracle run on the FP64 T0 and Ci - rounding the inputs counts too.
     import oracle
     n = 256
     T0, Ci, inv = fields(n)
@@ -559,24 +633,36 @@ def secondary_metrics(torch, api, ag, inputs, log):
     oracle.set_threads(max(1, oracle.max_threads()))
     Td = torch.from_numpy(T0).to(dev)
     C32 = api.to_f32(torch.from_numpy(Ci).to(dev))
+    Ci32 = C32.double().cpu().numpy()
+    D0p = api.to_deviation(Td, 1.7)
+    D0c, E0c = api.to_deviation_pair(Td, 1.7)
+    start_plain = D0p.double().cpu().numpy()
+    start_comp = api.from_deviation_pair(D0c, E0c, 0.0).cpu().numpy()
     for nt in (100, 1000):
-        ref = oracle.run(T0, Ci, 1.0, dt, *inv, nt)
-        scale = float(np.max(np.abs(ref)))
+        ref_store = oracle.run(T0, Ci, 1.0, dt, *inv, nt)
+        scale = float(np.max(np.abs(ref_store)))
         for tag, comp in (("fp32", False), ("fp32c", True)):
-            D = api.to_deviation(Td, 1.7)
-            D2 = D.clone()
-            cbuf = torch.zeros_like(D) if comp else None
-            res = api.run(D, D2, C32, 1.0, dt, inv, nt, comp=cbuf)
-            got = api.from_deviation(res, 1.7).cpu().numpy()
-            out[f"{tag}_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref)) / scale:.3e}")
+            if comp:
+                D = D0c.clone()
+                cbuf = api.compensation_fields(D, E0c)
+                res = api.run(D, torch.empty_like(D), C32, 1.0, dt, inv, nt, comp=cbuf)
+                got = api.from_deviation_pair(res, cbuf[nt % 2], 1.7).cpu().numpy()
+                ref_arith = oracle.run(start_comp, Ci32, 1.0, dt, *inv, nt) + 1.7
+            else:
+                D = D0p.clone()
+                res = api.run(D, torch.empty_like(D), C32, 1.0, dt, inv, nt)
+                got = api.from_deviation(res, 1.7).cpu().numpy()
+                ref_arith = oracle.run(start_plain, Ci32, 1.0, dt, *inv, nt) + 1.7
+            out[f"{tag}_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref_store)) / scale:.3e}")
+            out[f"{tag}_arith_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref_arith)) / scale:.3e}")
         C64 = torch.from_numpy(Ci).to(dev)
         for tag, scaled in (("fp64", True), ("fp64_plain_ci", False)):
             T64, T64b = Td.clone(), Td.clone()
             Cx = api.scale_ci(C64, 1.0, dt, inv) if scaled else C64
             got = api.run(T64, T64b, Cx, 1.0, dt, inv, nt, ci_scaled=scaled).cpu().numpy()
-            out[f"{tag}_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref)) / scale:.3e}")
+            out[f"{tag}_relerr_256_nt{nt}"] = float(f"{np.max(np.abs(got - ref_store)) / scale:.3e}")
     oracle.set_threads(1)
-    del Td, C32, D, D2
+    del Td, C32, D, D0p, D0c, E0c
     torch.cuda.empty_cache()
 
     # gradient / forward at 256^3, nt = 200: L = 1/2||T(nt) - T_obs||^2, dL/dCi and dL/dT0.
@@ -615,6 +701,17 @@ def secondary_metrics(torch, api, ag, inputs, log):
         t_adj = timed(adj10, reps=3) / 10
         out[f"adjoint_256_{name}_ms"] = round(1e3 * t_adj, 4)
         out[f"adjoint_256_{name}_gbs"] = round(6 * n ** 3 * Td.element_size() / t_adj / 1e9, 1)
+        if scaled:  # the fixed-point sweep's transposed step (the gradient's default on FP64)
+            sw = api.FixedPointSweep(Td)
+            sw.start(ybar)
+
+            def fx10():
+                for _ in range(10):
+                    sw.step(Cib, Td, Cf)
+            t_fx = timed(fx10, reps=3) / 10
+            out[f"adjoint_fx_256_{name}_ms"] = round(1e3 * t_fx, 4)
+            out[f"adjoint_fx_256_{name}_gbs"] = round(6 * n ** 3 * 8 / t_fx / 1e9, 1)
+            del sw
         for tag, every in (("sqrt_nt", ag.default_every(nt)), ("all_states", 1)):
             t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt, every=every), reps=2)
             out[f"grad_over_fwd_256_{name}_{tag}"] = round(t_grad / t_fwd, 3)
@@ -858,10 +955,75 @@ def run_ours(args):
     return 0
 
 
+def run_zslab(args):
+    """Weak scaling of one decomposed problem: rank r owns 510 planes of a 512 x 512 x
+    (510 N + 2) grid (its local fields are 512^3 with the two halo planes), steps them
+    with the pre-scaled FP64 kernel, boundary planes first, and exchanges one plane with
+    each neighbour per step over NCCL while its interior steps.  T_eff counts the
+    global grid: 3 * nodes * 8 bytes * nt per step."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2211_15634_gb300 import api, inputs, zslab
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    n, nt, K, W = args.size, args.nt, args.steps, args.warmup
+    nzg = (n - 2) * world + 2
+    slab = zslab.ZSlab((nzg, n, n), rank, world)
+    dev = torch.device(f"cuda:{local}")
+    x = torch.from_numpy(inputs.node_coords(n)).to(dev)
+    z = torch.arange(slab.z0 - 1, slab.z1 + 1, device=dev, dtype=torch.float64) / (nzg - 1)
+    d2 = (x - 0.5) ** 2
+    T0 = 1.7 + torch.exp(-((d2[None, None, :] + d2[None, :, None]) + ((z - 0.5) ** 2)[:, None, None]) / 0.01)
+    idx = torch.arange((slab.z0 - 1) * n * n, (slab.z1 + 1) * n * n, device="cpu", dtype=torch.int64)
+    C = torch.from_numpy((1.0 / inputs.C0) * (1.0 + 0.5 * inputs.uniform(inputs.SEED_CI, idx.numpy().astype(np.uint64)))
+                         .reshape(slab.local_shape)).to(dev)
+    dx = 1.0 / (n - 1)
+    dt = dx * dx / 1.0 / (1.5 / inputs.C0) / 6.1  # the bound max Ci <= 1.5/c0: one dt for all ranks
+    inv = (1.0 / dx,) * 3
+    Cs = api.scale_ci(C, 1.0, dt, inv)
+    T, T2 = T0.clone(), torch.empty_like(T0)
+    ex = zslab.HaloExchange(slab, T, transport="device") if world > 1 else None
+
+    def one():
+        T.copy_(T0)
+        zslab.run_slab(slab, ex, T, T2, Cs, 1.0, dt, inv, nt, ci_scaled=True)
+    for _ in range(W):
+        one()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(K):
+        one()
+    b.record()
+    torch.cuda.synchronize()
+    t = max_over_ranks(a.elapsed_time(b) / 1e3, dev)
+    if rank == 0:
+        gbs = 3 * n * n * nzg * 8 * nt * K / t / 1e9
+        print(json.dumps({
+            "metric": METRIC, "value": round(gbs, 1), "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": round(1e3 * t / K, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"diffusion3d FP64 {n}x{n}x{nzg} z-slabs (one 512^3 slab per rank, "
+                                   f"incl. halos), Gaussian T0, random Ci, nt={nt}",
+                       "nx": n, "ny": n, "nz": nzg, "nt": nt, "parallelism": f"zslab x{world}",
+                       "note": "each timed step includes a reset of T from T0 (one field copy)"}}),
+            flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.kernel_loop:
         return run_kernel_loop(args)
+    if args.zslab:
+        return run_zslab(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

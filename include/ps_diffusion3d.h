@@ -67,7 +67,8 @@ typedef enum {
 
 /* Flags of ps_diffusion3d_run_ex. */
 #define PS_RUN_GRAPH 1u       /* capture the nt launches into a CUDA graph once, replay it */
-#define PS_RUN_COMPENSATED 2u /* PS_F32 only: compensated (Kahan) update, needs `comp` */
+#define PS_RUN_COMPENSATED 2u /* PS_F32 only: compensated step on the two-float state,
+                                 needs `comp` (see ps_diffusion3d_step_comp_f32) */
 #define PS_RUN_NATIVE_F64 4u  /* PS_F64 only: force the plain FP64-instruction kernel */
 #define PS_RUN_CI_SCALED 8u   /* PS_F64, equal spacings: Ci holds dt*lam*_dx^2*Ci (see
                                  ps_diffusion3d_scale_ci); lam, dt are then only checked */
@@ -138,11 +139,19 @@ int ps_diffusion3d_step_ex(void *T2, const void *T, const void *Ci, double lam, 
 int ps_diffusion3d_scale_ci(double *Cs, const double *Ci, double lam, double dt, double _dx,
                             int64_t n, void *stream);
 
-/* Compensated FP32 step: as ps_diffusion3d_step with dtype PS_F32, but the
- * update D2 = D + delta is done with a per-node Kahan compensation term
- * `comp` (float, same layout, read and updated in place; start it at 0).
- * Only interior nodes of comp are touched. */
-int ps_diffusion3d_step_comp_f32(float *T2, const float *T, float *comp, const float *Ci,
+/* Compensated FP32 step (the compensated-update variant of the FP32 form).
+ * The state is a two-float pair: the value of node p is the unevaluated sum
+ * T[p] + E[p] of the FP32 deviation T and a small FP32 correction E (start E
+ * at 0, or at the residual ps_to_deviation_pair leaves).  The step is Fig. 1's
+ * step! on that value: delta = dt*lam*Ci*(lap(T) + lap(E)) in FP32 (lap: the
+ * three second differences times _d^2, Fig. 1's order), then the pair
+ * (T2, E2) holds T + (E + delta) exactly (TwoSum), so rounding the state to
+ * FP32 loses nothing from step to step; only delta's own FP32 roundings
+ * remain.  Reads T, E (with their x/y/z neighbours) and Ci, writes the
+ * interior of T2 and E2 (5 fields per step).  E2's boundary must equal E's
+ * and T2's T's (ps_diffusion3d_run_ex with PS_RUN_COMPENSATED sets both).  E2
+ * must not overlap T, T2, E or Ci; E must not overlap T2. */
+int ps_diffusion3d_step_comp_f32(float *T2, const float *T, float *E2, const float *E, const float *Ci,
                                  double lam, double dt, double _dx, double _dy, double _dz,
                                  int64_t nx, int64_t ny, int64_t nz, void *stream);
 
@@ -170,8 +179,12 @@ int ps_diffusion3d_run(void *T, void *T2, const void *Ci, double lam, double dt,
                        double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int nt,
                        int dtype, void *stream, int *result_in_T2);
 
-/* As ps_diffusion3d_run with flags (PS_RUN_*).  `comp` is the float
- * compensation field for PS_RUN_COMPENSATED (caller zeroes it), else NULL.
+/* As ps_diffusion3d_run with flags (PS_RUN_*).  With PS_RUN_COMPENSATED
+ * `comp` holds TWO float fields of nx*ny*nz values one after the other: the
+ * correction E paired with T at comp[0 .. n) (the caller sets it: zeros, or the
+ * E of ps_to_deviation_pair) and the one paired with T2 at comp[n .. 2n) (its
+ * boundary is set from the first at the start); the final correction is in
+ * the half paired with the buffer that holds the result.  Else `comp` is NULL.
  * With PS_RUN_GRAPH the nt launches are captured into a CUDA graph on the
  * first call for a given argument set and replayed afterwards (the graph
  * is cached inside the library until ps_clear_graph_cache()). */
@@ -196,6 +209,34 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
 
 /* Destroy every cached CUDA graph. */
 int ps_clear_graph_cache(void);
+
+/* ---------------------------------------------------------------------
+ * Launch-shape overrides (no counterpart in the paper): for tests that
+ * compare launch shapes bit for bit and for a tuner that times them.  Each
+ * value is process-wide and read on the host at launch; 0 (the initial
+ * value) leaves the choice to the library's own rule.  Chunk values are
+ * planes (or rows) per CTA, 1 .. 4096; flag values 0 or 1.  None changes a
+ * result: the z-chunk and tile-width choices give bit for bit the same
+ * fields, the plain compensated FP32 step equals the staged one bit for bit
+ * (explicit roundings), and the other plain kernels agree with the staged
+ * ones to rounding.  Setting a value that differs from the current one empties the
+ * CUDA-graph cache (a captured graph keeps the shapes of its capture).
+ * ------------------------------------------------------------------- */
+typedef enum {
+    PS_OVERRIDE_KCHUNK = 0,     /* z-planes per CTA of the one-step z-march kernels */
+    PS_OVERRIDE_KCHUNK2 = 1,    /* z-planes per CTA of the fused-pair kernels */
+    PS_OVERRIDE_ADJ_KCHUNK = 2, /* z-planes per CTA of the staged transposed-step kernels */
+    PS_OVERRIDE_CHUNK2D = 3,    /* rows per warp of the 2-D kernel */
+    PS_OVERRIDE_ADJ_PLAIN = 4,  /* 1: transposed steps take the plain one-thread-per-column kernel */
+    PS_OVERRIDE_F64_PX2 = 5,    /* 1: the pre-scaled FP64 step keeps two nodes per thread */
+    PS_OVERRIDE_STEP_PLAIN = 6, /* 1: single forward steps take the plain one-thread-per-column
+                                   kernel (fused pairs are not affected) */
+    PS_OVERRIDE_COUNT = 7
+} ps_override;
+/* Set override `which` to `value` (PS_ERR_ARG when out of range). */
+int ps_set_launch_override(int which, int value);
+/* Current value of override `which` to *value (host int). */
+int ps_get_launch_override(int which, int *value);
 
 /* ---------------------------------------------------------------------
  * Adjoint of one step (the transpose of step!'s Jacobian; derived from
@@ -242,6 +283,43 @@ int ps_diffusion3d_adjoint2_ex(void *Tbar, void *Cibar, const void *ybar, const 
                                unsigned flags, void *stream);
 
 /* ---------------------------------------------------------------------
+ * Reverse sweep with the adjoint state in fixed point (FP64, pre-scaled
+ * coefficient Cs of ps_diffusion3d_scale_ci, equal spacings; derived from
+ * Fig. 1's step, no paper line).  The transposed step of
+ * ps_diffusion3d_adjoint_ex(PS_RUN_CI_SCALED) with ybar held as an int64 field
+ * Y, ybar = Y * 2^sigma, sigma one scale for the whole grid kept in a small
+ * device state:
+ *   w[q] = Cs[q]*Y[q] rounded toward zero at interior q (0 elsewhere),
+ *   Y'[p] = Y[p] + L(w)[p] at every node (exact integer sums),
+ *   Csbar[q] += (Y[q]*2^sigma) * L(T)[q] at interior q (FP64, as the FP64 call),
+ * with L(A) = (sum of the six neighbours) - 6 A.  The largest |Y| carries 50-60
+ * significant bits: each step records max|Y'| and the next one rescales by a
+ * power of two when it leaves [2^50, 2^60).  Needs |Cs| < 1/4 at every interior
+ * node (a stable step has Cs <= 1/6.1): otherwise, or on a non-finite input,
+ * the sweep is marked bad and ps_adjoint_fx_end returns NaN everywhere.
+ * Use: ps_adjoint_fx_begin (Y from ybar_nt, state initialised), then
+ * ps_diffusion3d_adjoint_fx with step = 0, 1, 2, ... (each reads the Y the
+ * previous one wrote), then ps_adjoint_fx_end with step = the number of
+ * transposed steps taken.  `state` is a caller-owned device buffer of
+ * ps_adjoint_fx_state_bytes(); one sweep at a time per state buffer.  Y fields
+ * are int64, 16-byte aligned, x fastest; all calls asynchronous on `stream`.
+ * ------------------------------------------------------------------- */
+size_t ps_adjoint_fx_state_bytes(void);
+/* Y = ybar * 2^-sigma rounded to nearest with max|Y| in [2^58, 2^59]; starts the
+ * state.  n values; Y must not overlap ybar. */
+int ps_adjoint_fx_begin(long long *Y, const double *ybar, int64_t n, void *state, void *stream);
+/* One transposed step (the step-th of the sweep): Yout from Yin (Yout at every
+ * node), Csbar accumulated at interior nodes; T = the state the forward step
+ * read.  nx*8 a multiple of 16 (else PS_ERR_UNSUPPORTED).  Yout must not
+ * overlap any input; Csbar not Yin, T or Cs. */
+int ps_diffusion3d_adjoint_fx(long long *Yout, double *Csbar, const long long *Yin, const double *T,
+                              const double *Cs, int64_t nx, int64_t ny, int64_t nz, void *state, int step,
+                              void *stream);
+/* ybar = Y * 2^sigma (FP64, one rounding) after `step` transposed steps. */
+int ps_adjoint_fx_end(double *ybar, const long long *Y, int64_t n, const void *state, int step,
+                      void *stream);
+
+/* ---------------------------------------------------------------------
  * Reductions in FP64 (deterministic: a fixed partition and a fixed
  * summation order, independent of timing).  A, B are device arrays of n
  * elements of `dtype`; out_dev is a device double; workspace is a device
@@ -266,13 +344,15 @@ int ps_dot(double *out_dev, const void *A, const void *B, int64_t n, int dtype, 
  * device memory (for example a plugin inside a host application that owns
  * every device allocation, or a loop that must not allocate while it runs):
  * it takes no workspace and allocates nothing.  The paper has no counterpart;
- * this is a library convenience.
+ * this is a library convenience.  A and B need only be aligned to their
+ * element size (8 bytes PS_F64, 4 bytes PS_F32), unlike the other calls.
  *   - Scratch: the per-block partial sums live in a 256 KiB array inside
  *     the library image, resident on every GPU that uses the library until
  *     the process exits.  n may be at most 134217728 (4096 elements per
  *     partial x 32768 partials); larger n returns PS_ERR_UNSUPPORTED and
  *     launches nothing.
- *   - The first call on a device looks up the array's device address once;
+ *   - The first call on a device looks up the array's device address once
+ *     (again after cudaDeviceReset, which gives the device a new context);
  *     make that first call before any stream capture on the device.
  *   - Every call shares the one array (it keeps the last call's partials,
  *     each call overwrites what it reads): calls that can overlap on the GPU,
@@ -293,6 +373,14 @@ int ps_half_sq_dist(double *out_dev, void *R, const void *A, const void *B, int6
 int ps_to_deviation(float *D, const double *T, double t_ref, int64_t n, void *stream);
 /* T[p] = (double)D[p] + t_ref in FP64. */
 int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *stream);
+/* Two-float deviation for the compensated step: v = T[p] - t_ref in FP64,
+ * D[p] = (float)v, E[p] = (float)(v - D[p]) (D + E carries about 48 bits of v).
+ * D, E and T must not overlap. */
+int ps_to_deviation_pair(float *D, float *E, const double *T, double t_ref, int64_t n, void *stream);
+/* T[p] = ((double)D[p] + (double)E[p]) + t_ref in FP64 (the value of a two-float
+ * state). */
+int ps_from_deviation_pair(double *T, const float *D, const float *E, double t_ref, int64_t n,
+                           void *stream);
 
 /* ---------------------------------------------------------------------
  * 2-D form of the step: Fig. 1's step! with the z term dropped (the
@@ -308,6 +396,13 @@ int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *
  * ------------------------------------------------------------------- */
 int ps_diffusion2d_step(void *T2, const void *T, const void *Ci, double lam, double dt, double _dx,
                         double _dy, int64_t nx, int64_t ny, int dtype, unsigned flags, void *stream);
+/* dt for the 2-D form, Fig. 1's rule with the two-axis bound:
+ * dt = min(dx^2, dy^2)/lam/maximum(Ci)/4.1 with dx = lx/(nx-1), dy = ly/(ny-1);
+ * maximum(Ci) over nx*ny values reduced on the device (workspace as for the
+ * reductions below), dt formed on the host in FP64 to *dt_host (synchronizes
+ * `stream`). */
+int ps_diffusion2d_stable_dt(double *dt_host, const void *Ci, int64_t nx, int64_t ny, double lam,
+                             double lx, double ly, int dtype, void *workspace, void *stream);
 /* nt 2-D steps with T and T2 swapped after each (T2's edges first set to T's);
  * *result_in_T2 = nt & 1 (may be NULL).  Flags: PS_RUN_GRAPH (capture once per
  * argument set, replay), PS_RUN_CI_SCALED. */

@@ -29,6 +29,8 @@ PS_BATCH_COLUMN = 1
 PS_BATCH_ZMARCH = 2
 PS_BATCH_CI_SCALED = 4
 PS_BATCH_TEMPORAL2 = 8
+PS_OVERRIDE = {"kchunk": 0, "kchunk2": 1, "adj_kchunk": 2, "chunk2d": 3, "adj_plain": 4, "f64_px2": 5,
+               "step_plain": 6}
 
 STATUS_NAMES = {0: "PS_OK", -1: "PS_ERR_ARG", -2: "PS_ERR_ALIAS", -3: "PS_ERR_ALIGN",
                 -4: "PS_ERR_CUDA", -5: "PS_ERR_UNSUPPORTED"}
@@ -62,7 +64,9 @@ SIGNATURES = {
     "ps_diffusion3d_step_ex": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _U, _P]),
     "ps_diffusion3d_scale_ci": (_I, [_P, _P, _D, _D, _D, _I64, _P]),
     "ps_diffusion3d_step": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
-    "ps_diffusion3d_step_comp_f32": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _P]),
+    "ps_diffusion3d_step_comp_f32": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _P]),
+    "ps_to_deviation_pair": (_I, [_P, _P, _P, _D, _I64, _P]),
+    "ps_from_deviation_pair": (_I, [_P, _P, _P, _D, _I64, _P]),
     "ps_diffusion3d_copy_boundary": (_I, [_P, _P, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_copy_boundary_many": (_I, [_P, _I64, _I64, _P, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_run": (_I, [_P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _I, _P,
@@ -72,9 +76,16 @@ SIGNATURES = {
     "ps_diffusion3d_run_states": (_I, [_P, _P, _I64, _I, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
                                        _I, _U, _P, ctypes.POINTER(_I)]),
     "ps_clear_graph_cache": (_I, []),
+    "ps_set_launch_override": (_I, [_I, _I]),
+    "ps_get_launch_override": (_I, [_I, ctypes.POINTER(_I)]),
+    "ps_diffusion2d_stable_dt": (_I, [ctypes.POINTER(_D), _P, _I64, _I64, _D, _D, _D, _I, _P, _P]),
     "ps_diffusion3d_adjoint": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_adjoint_ex": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
                                        _U, _P]),
+    "ps_adjoint_fx_state_bytes": (_SZ, []),
+    "ps_adjoint_fx_begin": (_I, [_P, _P, _I64, _P, _P]),
+    "ps_diffusion3d_adjoint_fx": (_I, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P, _I, _P]),
+    "ps_adjoint_fx_end": (_I, [_P, _P, _I64, _P, _I, _P]),
     "ps_maximum_async": (_I, [_P, _P, _I64, _I, _P, _P]),
     "ps_maximum": (_I, [ctypes.POINTER(_D), _P, _I64, _I, _P, _P]),
     "ps_diffusion3d_stable_dt": (_I, [ctypes.POINTER(_D), _P, _I64, _I64, _I64, _D, _D, _D, _D, _I,

@@ -102,13 +102,26 @@ def scale_ci(Ci, lam: float, dt: float, inv_spacing, out: Optional[torch.Tensor]
     return out
 
 
-def step_compensated(T2, T, comp, Ci, lam: float, dt: float, inv_spacing) -> None:
-    """FP32 step with the per-node Kahan compensation field ``comp``."""
-    _same(T, T2, comp, Ci)
+def step_compensated(T2, T, E2, E, Ci, lam: float, dt: float, inv_spacing) -> None:
+    """Compensated FP32 step on the two-float state: the value of a node is T + E
+    (FP32 deviation plus FP32 correction); (T2, E2) receives the step of that value
+    with the addition done exactly (``ps_diffusion3d_step_comp_f32``)."""
+    _same(T, T2, E2, E, Ci)
     nx, ny, nz = _grid(T)
     check(_lib.load().ps_diffusion3d_step_comp_f32(
-        _field(T2, "T2", PS_F32), _field(T, "T", PS_F32), _field(comp, "comp", PS_F32),
-        _field(Ci, "Ci", PS_F32), lam, dt, *inv_spacing, nx, ny, nz, _stream(T)))
+        _field(T2, "T2", PS_F32), _field(T, "T", PS_F32), _field(E2, "E2", PS_F32),
+        _field(E, "E", PS_F32), _field(Ci, "Ci", PS_F32), lam, dt, *inv_spacing, nx, ny, nz,
+        _stream(T)))
+
+
+def compensation_fields(D: torch.Tensor, E0: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """The two correction fields :func:`run` takes with ``comp=`` for a two-float state
+    in (D, D2): shape ``(2, nz, ny, nx)`` float32, ``[0]`` paired with D (``E0`` or
+    zeros), ``[1]`` with D2 (its boundary is set by the run)."""
+    comp = torch.zeros((2,) + tuple(D.shape), dtype=torch.float32, device=D.device)
+    if E0 is not None:
+        comp[0].copy_(E0)
+    return comp
 
 
 def copy_boundary(T2, T) -> None:
@@ -176,7 +189,9 @@ def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, gr
     """Fig. 1 time loop on the buffer pair (T, T2); returns the tensor holding T(nt).
 
     ``temporal2=True`` runs the steps in fused pairs (FP32, or FP64 with
-    ``ci_scaled``); the result is bit for bit the same."""
+    ``ci_scaled``); the result is bit for bit the same.  ``comp`` (FP32): the two
+    correction fields of :func:`compensation_fields`; the steps are the compensated
+    two-float steps and the result's correction ends in ``comp[nt % 2]``."""
     code = _code(T)
     _same(T, T2, Ci)
     nx, ny, nz = _grid(T)
@@ -185,7 +200,9 @@ def run(T, T2, Ci, lam: float, dt: float, inv_spacing, nt: int, *, comp=None, gr
         flags |= _lib.PS_RUN_GRAPH
     if comp is not None:
         flags |= _lib.PS_RUN_COMPENSATED
-        _same(T, comp)
+        if tuple(comp.shape) != (2,) + tuple(T.shape) or comp.device != T.device:
+            raise ValueError("comp must hold two correction fields: shape (2,) + T.shape "
+                             "(see compensation_fields)")
     if native_f64:
         flags |= _lib.PS_RUN_NATIVE_F64
     if ci_scaled:
@@ -214,6 +231,53 @@ def adjoint(Tbar, Cibar, ybar, T, Ci, lam: float, dt: float, inv_spacing, *,
         _field(Tbar, "Tbar", code), _field(Cibar, "Cibar", code), _field(ybar, "ybar", code),
         _field(T, "T", code), _field(Ci, "Ci", code), lam, dt, *inv_spacing, nx, ny, nz, code,
         _lib.PS_RUN_CI_SCALED if ci_scaled else 0, _stream(T)))
+
+
+class FixedPointSweep:
+    """Reverse sweep of the pre-scaled FP64 step with dL/dT held as an int64 field
+    (``ps_adjoint_fx_*``): ``Y = ybar * 2^-sigma`` with one scale for the grid, kept in a
+    small device state.  ``start(ybar)`` converts dL/dT(nt); each :meth:`step` applies
+    one transposed step (Csbar accumulates dL/dCs at interior nodes); :meth:`finish`
+    returns dL/dT as an FP64 field.  Two int64 work fields and the state buffer are
+    allocated once per sweep object."""
+
+    def __init__(self, like: torch.Tensor):
+        if like.dtype != torch.float64:
+            raise TypeError("the fixed-point sweep is FP64")
+        self.shape = tuple(like.shape)
+        self.Y = torch.empty(self.shape, dtype=torch.int64, device=like.device)
+        self.Y2 = torch.empty_like(self.Y)
+        self.state = torch.empty(_lib.load().ps_adjoint_fx_state_bytes(), dtype=torch.uint8,
+                                 device=like.device)
+        self.steps = 0
+
+    @staticmethod
+    def supported(T: torch.Tensor) -> bool:
+        """Whether fields shaped like ``T`` can take the sweep (TMA rows: nx*8 a multiple of 16)."""
+        return T.dtype == torch.float64 and T.dim() == 3 and (T.shape[2] * 8) % 16 == 0
+
+    def start(self, ybar: torch.Tensor) -> None:
+        _same(ybar, self.Y)
+        check(_lib.load().ps_adjoint_fx_begin(self.Y.data_ptr(), _field(ybar, "ybar", PS_F64), ybar.numel(),
+                                              self.state.data_ptr(), _stream(ybar)))
+        self.steps = 0
+
+    def step(self, Csbar: torch.Tensor, T: torch.Tensor, Cs: torch.Tensor) -> None:
+        """One transposed step with the state T the forward step read."""
+        nx, ny, nz = _grid(T)
+        check(_lib.load().ps_diffusion3d_adjoint_fx(
+            self.Y2.data_ptr(), _field(Csbar, "Csbar", PS_F64), self.Y.data_ptr(), _field(T, "T", PS_F64),
+            _field(Cs, "Cs", PS_F64), nx, ny, nz, self.state.data_ptr(), self.steps, _stream(T)))
+        self.Y, self.Y2 = self.Y2, self.Y
+        self.steps += 1
+
+    def finish(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """dL/dT after the steps taken, as an FP64 field."""
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.Y.device)
+        check(_lib.load().ps_adjoint_fx_end(_field(out, "ybar", PS_F64), self.Y.data_ptr(), out.numel(),
+                                            self.state.data_ptr(), self.steps, _stream(out)))
+        return out
 
 
 def _grid2d(t: torch.Tensor):
@@ -251,10 +315,14 @@ def run2d(T, T2, Ci, lam: float, dt: float, inv_spacing: Sequence[float], nt: in
 
 def stable_dt2d(Ci, lam: float = 1.0, lengths=(1.0, 1.0)) -> float:
     """dt for the 2-D form: min(dx^2, dy^2)/lam/maximum(Ci)/4.1 (Fig. 1's rule with the
-    2-D bound 4 in place of 6), maximum(Ci) reduced on the GPU."""
-    ny, nx = Ci.shape
-    dx, dy = lengths[0] / (nx - 1), lengths[1] / (ny - 1)
-    return min(dx * dx, dy * dy) / lam / maximum(Ci) / 4.1
+    2-D bound 4 in place of 6; ``ps_diffusion2d_stable_dt``, maximum(Ci) on the GPU)."""
+    code = _code(Ci)
+    nx, ny = _grid2d(Ci)
+    v = ctypes.c_double(0.0)
+    check(_lib.load().ps_diffusion2d_stable_dt(ctypes.byref(v), _field(Ci, "Ci", code), nx, ny, lam,
+                                               lengths[0], lengths[1], code,
+                                               workspace(Ci.device).data_ptr(), _stream(Ci)))
+    return v.value
 
 
 def adjoint2(Tbar, Cibar, ybar, T_first, T_second, Ci, lam: float, dt: float, inv_spacing) -> None:
@@ -320,6 +388,9 @@ class SolvePipeline:
     ``submit`` returns the event recorded after the copy out (``out_host`` is valid
     once it has completed); :meth:`finish` waits for every submitted problem.  The
     host blocks only inside ``submit``, on the maximum(Ci) of its own problem.
+    Call :meth:`finish` before reading results in bulk or dropping the pipeline
+    (the buffers are released safely either way, but host tensors passed to
+    ``submit`` must stay alive until their copies have completed).
     ``graph=True`` replays the nt steps from the library's graph cache, whose key
     holds dt: worth it only for small grids whose problems share dt (each new dt
     captures a graph); by default the steps are launched from the library's loop,
@@ -335,6 +406,13 @@ class SolvePipeline:
         self.s_in = torch.cuda.Stream(self.device)
         self.s_run = torch.cuda.Stream(self.device)
         self.s_out = torch.cuda.Stream(self.device)
+        # the buffers are allocated on the caller's stream but used on the three streams:
+        # tell the caching allocator, so that a pipeline dropped with work still queued
+        # does not hand its blocks to a new allocation before that work completes
+        for bufs in self.sets:
+            for t in bufs:
+                for st in (self.s_in, self.s_run, self.s_out):
+                    t.record_stream(st)
         self.freed = [None, None]  # per set: event after its last result was copied out
         self.count = 0
         self.scaled = dtype == torch.float64 and self.inv[0] == self.inv[1] == self.inv[2]
@@ -427,6 +505,25 @@ def from_deviation(D: torch.Tensor, t_ref: float, out: Optional[torch.Tensor] = 
         out = torch.empty(D.shape, dtype=torch.float64, device=D.device)
     check(_lib.load().ps_from_deviation(_field(out, "T", PS_F64), _field(D, "D", PS_F32), t_ref,
                                         D.numel(), _stream(D)))
+    return out
+
+
+def to_deviation_pair(T: torch.Tensor, t_ref: float):
+    """Two-float deviation (D, E) of an FP64 field: D = (float)(T - t_ref), E the FP32
+    rounding of what D misses (``ps_to_deviation_pair``)."""
+    D = torch.empty(T.shape, dtype=torch.float32, device=T.device)
+    E = torch.empty_like(D)
+    check(_lib.load().ps_to_deviation_pair(_field(D, "D", PS_F32), _field(E, "E", PS_F32),
+                                           _field(T, "T", PS_F64), t_ref, T.numel(), _stream(T)))
+    return D, E
+
+
+def from_deviation_pair(D: torch.Tensor, E: torch.Tensor, t_ref: float) -> torch.Tensor:
+    """FP64 field ``(D + E) + t_ref`` of a two-float state."""
+    _same(D, E)
+    out = torch.empty(D.shape, dtype=torch.float64, device=D.device)
+    check(_lib.load().ps_from_deviation_pair(_field(out, "T", PS_F64), _field(D, "D", PS_F32),
+                                             _field(E, "E", PS_F32), t_ref, D.numel(), _stream(D)))
     return out
 
 
@@ -554,6 +651,38 @@ class Batch:
 
 def clear_graph_cache() -> None:
     check(_lib.load().ps_clear_graph_cache())
+
+
+def set_launch_override(name: str, value: int) -> int:
+    """Set a launch-shape override (``ps_set_launch_override``): ``name`` is one of
+    ``kchunk, kchunk2, adj_kchunk, chunk2d`` (planes or rows per CTA, 0 = the library's
+    rule) or ``adj_plain, f64_px2, step_plain`` (0/1).  Returns the previous value.  No override
+    changes a result; a change empties the graph cache."""
+    lib = _lib.load()
+    which = _lib.PS_OVERRIDE[name]
+    old = ctypes.c_int(0)
+    check(lib.ps_get_launch_override(which, ctypes.byref(old)))
+    check(lib.ps_set_launch_override(which, int(value)))
+    return old.value
+
+
+class launch_override:
+    """Context manager: ``with launch_override(kchunk=7): ...`` sets overrides for the
+    block and restores the previous values after it."""
+
+    def __init__(self, **values):
+        self.values = values
+        self.saved = {}
+
+    def __enter__(self):
+        for name, v in self.values.items():
+            self.saved[name] = set_launch_override(name, v)
+        return self
+
+    def __exit__(self, *exc):
+        for name, v in self.saved.items():
+            set_launch_override(name, v)
+        return False
 
 
 def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing, ci_scaled=False, temporal2=False) -> str:

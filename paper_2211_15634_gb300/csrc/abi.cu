@@ -1,6 +1,7 @@
 // C ABI of the library: host-side argument checks, dispatch to the kernels,
 // the CUDA-graph cache of ps_diffusion3d_run_ex and the batch-table builder.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -10,6 +11,8 @@
 #include <string>
 #include <tuple>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "emu64.cuh"
 #include "internal.h"
@@ -34,12 +37,70 @@ static int cuda_fail(cudaError_t e, const char *where) {
 }
 
 int api_fail(int status, const char *msg) { return fail(status, "%s", msg); }
+
+// Launch-shape overrides (ps_set_launch_override), read by the launchers.
+static std::atomic<int> g_override[PS_OVERRIDE_COUNT];
+
+int launch_override(int which) {
+    return which >= 0 && which < PS_OVERRIDE_COUNT ? g_override[which].load(std::memory_order_relaxed) : 0;
+}
 int api_cuda_fail(cudaError_t e, const char *where) { return cuda_fail(e, where); }
 
 int current_device() {
     int d = 0;
     cudaGetDevice(&d);
     return d;
+}
+
+// Generation of the current device's context: 1 for the first context seen on the
+// device, +1 whenever the current context's unique id differs from the last one seen
+// (cudaDeviceReset makes a new primary context).  State created inside a context -
+// function attributes, the capture stream, cached graphs, a device symbol's address -
+// is keyed on it.
+unsigned context_generation() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_cur = (PFN_cuCtxGetCurrent_v4000)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_cuCtxGetId_v12000)p;
+    });
+    static std::mutex mu;
+    static unsigned long long last_id[64] = {0};
+    static unsigned gen[64] = {0};
+    const int d = current_device();
+    if (d < 0 || d >= 64 || !get_cur || !get_id) return 1;
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) {
+        cudaSetDevice(d);  // makes the device's primary context current on this thread
+        if (get_cur(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    }
+    unsigned long long id = 0;
+    if (!ctx || get_id(ctx, &id) != CUDA_SUCCESS) return gen[d] ? gen[d] : 1;
+    std::lock_guard<std::mutex> lock(mu);
+    if (gen[d] == 0 || id != last_id[d]) {
+        last_id[d] = id;
+        ++gen[d];
+    }
+    return gen[d];
+}
+
+bool set_smem_attr_once(const void *func, int smem, unsigned *done_gen, cudaError_t *err) {
+    const int dev = current_device();
+    const unsigned g = context_generation();
+    *err = cudaSuccess;
+    if (dev < 0 || dev >= 64 || done_gen[dev] == g) return true;
+    *err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (*err != cudaSuccess) return false;
+    done_gen[dev] = g;
+    return true;
 }
 
 int sm_count() {
@@ -116,8 +177,9 @@ static int check_step_args(const void *T2, const void *T, const void *Ci, double
     return PS_OK;
 }
 
-static cudaError_t enqueue_step(void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
-                                Grid3 g, int dtype, unsigned flags, cudaStream_t s) {
+// One step; E2 / E: correction fields of the two-float state (PS_RUN_COMPENSATED).
+static cudaError_t enqueue_step(void *T2, const void *T, void *E2, const void *E, const void *Ci,
+                                StepCoef c, Grid3 g, int dtype, unsigned flags, cudaStream_t s) {
     if (dtype == PS_F64) {
         if (flags & PS_RUN_CI_SCALED)
             return launch_step_f64_scaled((double *)T2, (const double *)T, (const double *)Ci, g, s);
@@ -126,8 +188,8 @@ static cudaError_t enqueue_step(void *T2, const void *T, void *comp, const void 
         return launch_step_f64_fast((double *)T2, (const double *)T, (const double *)Ci, c, g, s);
     }
     if (flags & PS_RUN_COMPENSATED)
-        return launch_step_f32_comp((float *)T2, (const float *)T, (float *)comp, (const float *)Ci,
-                                    c, g, s);
+        return launch_step_f32_comp((float *)T2, (const float *)T, (float *)E2, (const float *)E,
+                                    (const float *)Ci, c, g, s);
     return launch_step_f32((float *)T2, (const float *)T, (const float *)Ci, c, g, s);
 }
 
@@ -148,9 +210,13 @@ static cudaError_t enqueue_step2(void *T2, const void *T, const void *Ci, StepCo
 // PS_RUN_TEMPORAL2 the steps go in fused pairs; when the number of passes would
 // leave the result in the other buffer than nt's parity says, one pair is run
 // as two single steps.
+// `comp` (PS_RUN_COMPENSATED): two correction fields, comp[0, n) paired with T and
+// comp[n, 2n) with T2; their boundaries are copied like T's.
 static cudaError_t enqueue_run(void *T, void *T2, void *comp, const void *Ci, StepCoef c, Grid3 g,
                                int nt, int dtype, unsigned flags, cudaStream_t s) {
     cudaError_t e = launch_copy_boundary(T2, T, g, elem_bytes(dtype), s);
+    float *EA = (float *)comp, *EB = comp ? (float *)comp + g.n() : nullptr;
+    if (comp && e == cudaSuccess) e = launch_copy_boundary(EB, EA, g, 4, s);
     int pairs = 0, singles = nt;
     if ((flags & PS_RUN_TEMPORAL2) && temporal2_ok(g, dtype, T, T2, Ci)) {
         pairs = nt / 2;
@@ -164,7 +230,8 @@ static cudaError_t enqueue_run(void *T, void *T2, void *comp, const void *Ci, St
         void *src = (it & 1) ? T2 : T;
         void *dst = (it & 1) ? T : T2;
         e = it < pairs ? enqueue_step2(dst, src, Ci, c, g, dtype, s)
-                       : enqueue_step(dst, src, comp, Ci, c, g, dtype, flags, s);
+                       : enqueue_step(dst, src, (it & 1) ? EA : EB, (it & 1) ? EB : EA, Ci, c, g, dtype,
+                                      flags, s);
     }
     return e;
 }
@@ -176,13 +243,24 @@ using GraphKey = std::tuple<int, const void *, const void *, const void *, const
 static std::mutex g_graph_mu;
 static std::map<GraphKey, cudaGraphExec_t> g_graphs;
 static cudaStream_t g_capture_stream[64] = {nullptr};
+static unsigned g_capture_gen[64] = {0};
 
+// The device's capture stream, created in its current context.  After the context
+// changed (cudaDeviceReset) the old stream and the graphs cached for the device are
+// handles of a context that no longer exists: they are forgotten, not destroyed.
 static cudaError_t capture_stream(cudaStream_t *out) {
     const int d = current_device();
     if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    const unsigned gen = context_generation();
+    if (g_capture_gen[d] != gen) {
+        for (auto it = g_graphs.begin(); it != g_graphs.end();)
+            it = std::get<0>(it->first) == d ? g_graphs.erase(it) : std::next(it);
+        g_capture_stream[d] = nullptr;
+    }
     if (!g_capture_stream[d]) {
         cudaError_t e = cudaStreamCreateWithFlags(&g_capture_stream[d], cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
+        g_capture_gen[d] = gen;
     }
     *out = g_capture_stream[d];
     return cudaSuccess;
@@ -193,12 +271,12 @@ static cudaError_t capture_stream(cudaStream_t *out) {
 template <typename F>
 static int graph_replay(const GraphKey &key, F &&enqueue, const char *what, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
+    cudaStream_t cs;
+    cudaError_t ce = capture_stream(&cs);  // also drops graphs of a context that is gone
+    if (ce != cudaSuccess) return cuda_fail(ce, "capture stream");
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
-        cudaStream_t cs;
-        cudaError_t e = capture_stream(&cs);
-        if (e != cudaSuccess) return cuda_fail(e, "capture stream");
-        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
         const cudaError_t le = enqueue(cs);
         cudaGraph_t graph = nullptr;
@@ -247,7 +325,7 @@ int ps_device_error(unsigned *out_host, int clear) {
     *out_host = zmarch_device_error(clear != 0) | adjoint_device_error(clear != 0) |
                 adjoint_scaled_device_error(clear != 0) | zmarch2_device_error(clear != 0) |
                 adjoint_f32_device_error(clear != 0) | batch_device_error(clear != 0) |
-                batch_zmarch_device_error(clear != 0);
+                batch_zmarch_device_error(clear != 0) | adjoint_fx_device_error(clear != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ps_device_error");
     return PS_OK;
@@ -290,7 +368,7 @@ int ps_diffusion3d_step(void *T2, const void *T, const void *Ci, double lam, dou
                         double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int dtype,
                         void *stream) {
     PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, dtype));
-    cudaError_t e = enqueue_step(T2, T, nullptr, Ci, make_coef(lam, dt, _dx, _dy, _dz),
+    cudaError_t e = enqueue_step(T2, T, nullptr, nullptr, Ci, make_coef(lam, dt, _dx, _dy, _dz),
                                  Grid3{nx, ny, nz}, dtype, 0u, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_step");
     return PS_OK;
@@ -304,7 +382,7 @@ int ps_diffusion3d_step_ex(void *T2, const void *T, const void *Ci, double lam, 
     PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
     if ((flags & PS_RUN_NATIVE_F64) && dtype != PS_F64)
         return fail(PS_ERR_UNSUPPORTED, "PS_RUN_NATIVE_F64 needs PS_F64");
-    cudaError_t e = enqueue_step(T2, T, nullptr, Ci, make_coef(lam, dt, _dx, _dy, _dz),
+    cudaError_t e = enqueue_step(T2, T, nullptr, nullptr, Ci, make_coef(lam, dt, _dx, _dy, _dz),
                                  Grid3{nx, ny, nz}, dtype, flags, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_step_ex");
     return PS_OK;
@@ -324,15 +402,17 @@ int ps_diffusion3d_scale_ci(double *Cs, const double *Ci, double lam, double dt,
     return PS_OK;
 }
 
-int ps_diffusion3d_step_comp_f32(float *T2, const float *T, float *comp, const float *Ci,
+int ps_diffusion3d_step_comp_f32(float *T2, const float *T, float *E2, const float *E, const float *Ci,
                                  double lam, double dt, double _dx, double _dy, double _dz,
                                  int64_t nx, int64_t ny, int64_t nz, void *stream) {
     PS_TRY(check_step_args(T2, T, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz, PS_F32));
-    PS_TRY(check_ptr(comp, "comp"));
+    PS_TRY(check_ptr(E2, "E2"));
+    PS_TRY(check_ptr(E, "E"));
     const size_t bytes = (size_t)(nx * ny * nz) * 4;
-    if (overlap(comp, T, bytes) || overlap(comp, T2, bytes) || overlap(comp, Ci, bytes))
-        return fail(PS_ERR_ALIAS, "comp overlaps T, T2 or Ci");
-    cudaError_t e = launch_step_f32_comp(T2, T, comp, Ci, make_coef(lam, dt, _dx, _dy, _dz),
+    if (overlap(E2, T, bytes) || overlap(E2, T2, bytes) || overlap(E2, Ci, bytes) || overlap(E2, E, bytes))
+        return fail(PS_ERR_ALIAS, "E2 overlaps T, T2, E or Ci");
+    if (overlap(E, T2, bytes)) return fail(PS_ERR_ALIAS, "E overlaps T2");
+    cudaError_t e = launch_step_f32_comp(T2, T, E2, E, Ci, make_coef(lam, dt, _dx, _dy, _dz),
                                          Grid3{nx, ny, nz}, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_step_comp_f32");
     return PS_OK;
@@ -411,7 +491,7 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
             dst = grid(nslots + work_next);
             work_next ^= 1;
         }
-        cudaError_t e = enqueue_step(dst, cur, nullptr, Ci, c, g, dtype, flags, (cudaStream_t)stream);
+        cudaError_t e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_run_states");
         cur = dst;
         cur_slot = slot;
@@ -437,8 +517,9 @@ int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double 
         if (dtype != PS_F32) return fail(PS_ERR_UNSUPPORTED, "PS_RUN_COMPENSATED needs PS_F32");
         PS_TRY(check_ptr(comp, "comp"));
         const size_t bytes = (size_t)(nx * ny * nz) * 4;
-        if (overlap(comp, T, bytes) || overlap(comp, T2, bytes) || overlap(comp, Ci, bytes))
-            return fail(PS_ERR_ALIAS, "comp overlaps T, T2 or Ci");
+        if (overlap2(comp, 2 * bytes, T, bytes) || overlap2(comp, 2 * bytes, T2, bytes) ||
+            overlap2(comp, 2 * bytes, Ci, bytes))
+            return fail(PS_ERR_ALIAS, "comp (two fields) overlaps T, T2 or Ci");
     } else {
         comp = nullptr;
     }
@@ -466,6 +547,27 @@ int ps_clear_graph_cache(void) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     for (auto &kv : g_graphs) cudaGraphExecDestroy(kv.second);
     g_graphs.clear();
+    return PS_OK;
+}
+
+int ps_set_launch_override(int which, int value) {
+    if (which < 0 || which >= PS_OVERRIDE_COUNT)
+        return fail(PS_ERR_ARG, "override %d is not a PS_OVERRIDE_* value", which);
+    const bool flag = which == PS_OVERRIDE_ADJ_PLAIN || which == PS_OVERRIDE_F64_PX2 ||
+                      which == PS_OVERRIDE_STEP_PLAIN;
+    if (value < 0 || (flag && value > 1) || (!flag && value > 4096))
+        return fail(PS_ERR_ARG, "override %d: value %d out of range (%s)", which, value,
+                    flag ? "0 or 1" : "0 .. 4096");
+    // cached graphs hold the launch shapes chosen at capture: drop them on a change
+    if (g_override[which].exchange(value) != value) return ps_clear_graph_cache();
+    return PS_OK;
+}
+
+int ps_get_launch_override(int which, int *value) {
+    if (!value) return fail(PS_ERR_ARG, "value is NULL");
+    if (which < 0 || which >= PS_OVERRIDE_COUNT)
+        return fail(PS_ERR_ARG, "override %d is not a PS_OVERRIDE_* value", which);
+    *value = g_override[which].load();
     return PS_OK;
 }
 
@@ -514,6 +616,62 @@ int ps_diffusion3d_adjoint_ex(void *Tbar, void *Cibar, const void *ybar, const v
         e = launch_adjoint_f32((float *)Tbar, (float *)Cibar, (const float *)ybar, (const float *)T,
                                (const float *)Ci, c, g, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_adjoint");
+    return PS_OK;
+}
+
+size_t ps_adjoint_fx_state_bytes(void) { return kFxStateBytes; }
+
+int ps_adjoint_fx_begin(long long *Y, const double *ybar, int64_t n, void *state, void *stream) {
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(Y, "Y"));
+    PS_TRY(check_ptr(ybar, "ybar"));
+    PS_TRY(check_ptr(state, "state"));
+    if (overlap(Y, ybar, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "Y overlaps ybar");
+    if (overlap2(state, kFxStateBytes, Y, (size_t)n * 8) || overlap2(state, kFxStateBytes, ybar, (size_t)n * 8))
+        return fail(PS_ERR_ALIAS, "state overlaps Y or ybar");
+    cudaError_t e = launch_adjoint_fx_begin(Y, ybar, n, state, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_adjoint_fx_begin");
+    return PS_OK;
+}
+
+int ps_diffusion3d_adjoint_fx(long long *Yout, double *Csbar, const long long *Yin, const double *T,
+                              const double *Cs, int64_t nx, int64_t ny, int64_t nz, void *state, int step,
+                              void *stream) {
+    PS_TRY(check_grid(nx, ny, nz));
+    PS_TRY(check_ptr(Yout, "Yout"));
+    PS_TRY(check_ptr(Csbar, "Csbar"));
+    PS_TRY(check_ptr(Yin, "Yin"));
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_ptr(Cs, "Cs"));
+    PS_TRY(check_ptr(state, "state"));
+    if (step < 0) return fail(PS_ERR_ARG, "step = %d < 0", step);
+    const size_t bytes = (size_t)(nx * ny * nz) * 8;
+    if (overlap(Yout, Yin, bytes) || overlap(Yout, T, bytes) || overlap(Yout, Cs, bytes) ||
+        overlap(Yout, Csbar, bytes))
+        return fail(PS_ERR_ALIAS, "Yout overlaps an input");
+    if (overlap(Csbar, Yin, bytes) || overlap(Csbar, T, bytes) || overlap(Csbar, Cs, bytes))
+        return fail(PS_ERR_ALIAS, "Csbar overlaps an input");
+    const void *fields[5] = {Yout, Csbar, Yin, T, Cs};
+    for (const void *f : fields)
+        if (overlap2(state, kFxStateBytes, f, bytes)) return fail(PS_ERR_ALIAS, "state overlaps a field");
+    const Grid3 g{nx, ny, nz};
+    if (!adjoint_fx_supported(g, fields, 5))
+        return fail(PS_ERR_UNSUPPORTED, "the fixed-point sweep needs nx*8 a multiple of 16 and a CUDA driver");
+    cudaError_t e = launch_adjoint_fx(Yout, Csbar, Yin, T, Cs, g, state, step, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_adjoint_fx");
+    return PS_OK;
+}
+
+int ps_adjoint_fx_end(double *ybar, const long long *Y, int64_t n, const void *state, int step,
+                      void *stream) {
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(Y, "Y"));
+    PS_TRY(check_ptr(ybar, "ybar"));
+    PS_TRY(check_ptr(state, "state"));
+    if (step < 0) return fail(PS_ERR_ARG, "step = %d < 0", step);
+    if (overlap(Y, ybar, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "ybar overlaps Y");
+    cudaError_t e = launch_adjoint_fx_end(ybar, Y, n, state, step, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_adjoint_fx_end");
     return PS_OK;
 }
 
@@ -676,6 +834,20 @@ int ps_diffusion3d_stable_dt(double *dt_host, const void *Ci, int64_t nx, int64_
     return PS_OK;
 }
 
+int ps_diffusion2d_stable_dt(double *dt_host, const void *Ci, int64_t nx, int64_t ny, double lam,
+                             double lx, double ly, int dtype, void *workspace, void *stream) {
+    if (!dt_host) return fail(PS_ERR_ARG, "dt_host is NULL");
+    if (nx < 3 || ny < 3) return fail(PS_ERR_ARG, "grid %lld x %lld: every size must be >= 3", (long long)nx,
+                                      (long long)ny);
+    PS_TRY(check_finite(lam, "lam"));
+    double mx = 0.0;
+    PS_TRY(ps_maximum(&mx, Ci, nx * ny, dtype, workspace, stream));
+    const double dx = lx / (double)(nx - 1), dy = ly / (double)(ny - 1);
+    const double m = dy * dy < dx * dx ? dy * dy : dx * dx;
+    *dt_host = m / lam / mx / 4.1;
+    return PS_OK;
+}
+
 int ps_dot(double *out_dev, const void *A, const void *B, int64_t n, int dtype, void *workspace,
            void *stream) {
     PS_TRY(check_reduce(A, n, dtype, workspace));
@@ -720,6 +892,34 @@ int ps_from_deviation(double *T, const float *D, double t_ref, int64_t n, void *
     if (overlap2(D, (size_t)n * 4, T, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "T overlaps D");
     cudaError_t e = launch_from_deviation(T, D, t_ref, n, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_from_deviation");
+    return PS_OK;
+}
+
+int ps_to_deviation_pair(float *D, float *E, const double *T, double t_ref, int64_t n, void *stream) {
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(D, "D"));
+    PS_TRY(check_ptr(E, "E"));
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_finite(t_ref, "t_ref"));
+    if (overlap2(D, (size_t)n * 4, T, (size_t)n * 8) || overlap2(E, (size_t)n * 4, T, (size_t)n * 8) ||
+        overlap(D, E, (size_t)n * 4))
+        return fail(PS_ERR_ALIAS, "D, E and T must not overlap");
+    cudaError_t e = launch_to_deviation_pair(D, E, T, t_ref, n, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_to_deviation_pair");
+    return PS_OK;
+}
+
+int ps_from_deviation_pair(double *T, const float *D, const float *E, double t_ref, int64_t n,
+                           void *stream) {
+    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
+    PS_TRY(check_ptr(T, "T"));
+    PS_TRY(check_ptr(D, "D"));
+    PS_TRY(check_ptr(E, "E"));
+    PS_TRY(check_finite(t_ref, "t_ref"));
+    if (overlap2(D, (size_t)n * 4, T, (size_t)n * 8) || overlap2(E, (size_t)n * 4, T, (size_t)n * 8))
+        return fail(PS_ERR_ALIAS, "T overlaps D or E");
+    cudaError_t e = launch_from_deviation_pair(T, D, E, t_ref, n, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ps_from_deviation_pair");
     return PS_OK;
 }
 

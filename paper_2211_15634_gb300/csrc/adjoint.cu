@@ -5,7 +5,6 @@
 //   w[q]      = dt*lam*Ci[q]*ybar[q] at interior q, 0 elsewhere (and outside),
 //   Tbar[p]   = ybar[p] + sum_d (w[p-e_d] - 2 w[p] + w[p+e_d]) * _d^2  (all p),
 //   Cibar[q] += dt*lam*ybar[q]*Lap(T_t)[q]                             (interior q).
-#include <cstdlib>
 
 #include "internal.h"
 #include "stencil_basic.cuh"
@@ -117,8 +116,7 @@ k_adjoint_basic_scaled(double *__restrict__ Tbar, double *__restrict__ Csbar,
 static bool use_tma(Grid3 g, int esz, const void *a, const void *b, const void *c, const void *d,
                     const void *e) {
     const void *ptrs[5] = {c, d, e, a, b};  // the three TMA-read fields first
-    const char *v = getenv("PS_ADJ_PLAIN");
-    if (v && v[0] == '1') return false;
+    if (launch_override(PS_OVERRIDE_ADJ_PLAIN) == 1) return false;
     return adjoint_zmarch_supported(g, esz, ptrs, 5);
 }
 
@@ -149,8 +147,7 @@ cudaError_t launch_adjoint_f64_scaled(double *Tbar, double *Csbar, const double 
 cudaError_t launch_adjoint_f32(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                const float *Ci, StepCoef c, Grid3 g, cudaStream_t s) {
     const void *ptrs[5] = {T, ybar, Ci, Cibar, Tbar};
-    const char *v = getenv("PS_ADJ_PLAIN");
-    if (!(v && v[0] == '1') && adjoint_f32_supported(g, ptrs, 5))
+    if (launch_override(PS_OVERRIDE_ADJ_PLAIN) != 1 && adjoint_f32_supported(g, ptrs, 5))
         return launch_adjoint_f32_tma(Tbar, Cibar, ybar, T, Ci, c, g, s);
     return launch_adjoint_basic<float>(
         Tbar, Cibar, ybar, T, Ci,

@@ -19,7 +19,6 @@
 // plane k + NST: the copies run NST-1 planes ahead of the arithmetic.
 #include <cudaTypedefs.h>
 
-#include <cstdlib>
 
 #include "adj32_node.cuh"
 #include "internal.h"
@@ -536,14 +535,9 @@ static cudaError_t launch_adj2_t(float *Tbar, float *Cibar, const float *ybar, c
     constexpr int BY = 8, BX = 128, W = BX + 8;
     constexpr unsigned YBA = (W * (BY + 4) * 4 + 127) / 128 * 128, SBA = (W * (BY + 2) * 4 + 127) / 128 * 128;
     constexpr size_t smem = NYC * 2 * YBA + NS * (2 * SBA + BX * BY * 4) + 2 * SBA + (NYC + NS) * 8;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_adjoint2_f32<NYC, NS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_adjoint2_f32<NYC, NS>, (int)smem, attr_gen, &ae)) return ae;
     CUtensorMap mY, mC, mS1, mS0, mB;
     if (!make_tensor_map_3d(&mY, ybar, 4, g, W, BY + 4) || !make_tensor_map_3d(&mC, Ci, 4, g, W, BY + 4) ||
         !make_tensor_map_3d(&mS1, S1, 4, g, W, BY + 2) || !make_tensor_map_3d(&mS0, S0, 4, g, W, BY + 2) ||
@@ -569,8 +563,7 @@ cudaError_t launch_adjoint2_f32(float *Tbar, float *Cibar, const float *ybar, co
     p.Kx = (float)(c.dtlam * c.ax);
     p.Ky = (float)(c.dtlam * c.ay);
     p.Kz = (float)(c.dtlam * c.az);
-    const char *v = getenv("PS_ADJ_KCHUNK");
-    const int kchunk = v ? atoi(v) : 0;
+    const int kchunk = launch_override(PS_OVERRIDE_ADJ_KCHUNK);
     return launch_adj2_t<4, 3>(Tbar, Cibar, ybar, S1, S0, Ci, g, p, kchunk, s);
 }
 
@@ -580,14 +573,9 @@ static cudaError_t launch_adj32_t(float *Tbar, float *Cibar, const float *ybar, 
     constexpr int BX = 128, W = BX + 8, H = BY + 2;
     constexpr unsigned HBA = (W * H * 4 + 127) / 128 * 128, CBA = (BX * BY * 4 + 127) / 128 * 128;
     constexpr size_t smem = NST * (3 * HBA + CBA) + NST * 8;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_adjoint_f32<BY, NST, MINB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_adjoint_f32<BY, NST, MINB>, (int)smem, attr_gen, &ae)) return ae;
     CUtensorMap mT, mY, mC, mB;
     if (!make_tensor_map_3d(&mT, T, 4, g, W, H) || !make_tensor_map_3d(&mY, ybar, 4, g, W, H) ||
         !make_tensor_map_3d(&mC, Ci, 4, g, W, H) || !make_tensor_map_3d(&mB, Cibar, 4, g, BX, BY))
@@ -636,8 +624,7 @@ cudaError_t launch_adjoint_f32_tma(float *Tbar, float *Cibar, const float *ybar,
     p.Kx = (float)(c.dtlam * c.ax);
     p.Ky = (float)(c.dtlam * c.ay);
     p.Kz = (float)(c.dtlam * c.az);
-    const char *v = getenv("PS_ADJ_KCHUNK");
-    const int kchunk = v ? atoi(v) : 0;
+    const int kchunk = launch_override(PS_OVERRIDE_ADJ_KCHUNK);
     // 4-row tiles, four stages (three planes of copies ahead), four CTAs per SM
     // (48 KB of shared memory each); measured at 256^3 and 512^3 against 8-row
     // tiles with four or five stages at two CTAs per SM and 4-row tiles with six

@@ -26,7 +26,6 @@
 // latency hides behind the w tile work.
 #include <cudaTypedefs.h>
 
-#include <cstdlib>
 
 #include "emu64.cuh"
 #include "internal.h"
@@ -328,21 +327,15 @@ cudaError_t launch_adjoint_scaled(double *Tbar, double *Csbar, const double *yba
     constexpr int BY = 8, NST = 3, PX = 2, BX = 32 * PX, W = BX + 2 * PX, H = BY + 2;
     constexpr unsigned TBA = (W * H * 8 + 127) / 128 * 128;
     constexpr size_t smem = 3 * NST * TBA + 3 * TBA + NST * 8;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_adjoint_scaled<BY, NST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_adjoint_scaled<BY, NST>, (int)smem, attr_gen, &ae)) return ae;
     CUtensorMap mT, mY, mC;
     if (!make_tensor_map_3d(&mT, T, 8, g, W, H) || !make_tensor_map_3d(&mY, ybar, 8, g, W, H) ||
         !make_tensor_map_3d(&mC, Cs, 8, g, W, H))
         return cudaErrorInvalidValue;
     const int64_t ntx = (g.nx + BX - 1) / BX, nty = (g.ny + BY - 1) / BY, tiles = ntx * nty;
-    const char *v = getenv("PS_ADJ_KCHUNK");
-    int kchunk = v ? atoi(v) : 0;
+    int kchunk = launch_override(PS_OVERRIDE_ADJ_KCHUNK);
     if (kchunk <= 0) {
         // long z-chunks amortise the two prologue planes; keep at least ~3 waves of CTAs
         // (3 per SM).  Where chunks of 16 planes or more keep that many, take the chunk

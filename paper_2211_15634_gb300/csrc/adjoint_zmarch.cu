@@ -21,7 +21,6 @@
 // same-binade fast path.  About four FP64 instructions per node in all.
 #include <cudaTypedefs.h>
 
-#include <cstdlib>
 
 #include "emu64.cuh"
 #include "internal.h"
@@ -378,14 +377,9 @@ static cudaError_t launch_adj_t(E *Tbar, E *Cibar, const E *ybar, const E *T, co
     constexpr int PX = ATraits<E>::PX, BX = 32 * PX, W = BX + 2 * PX, H = BY + 2;
     constexpr unsigned TBA = (W * H * sizeof(E) + 127) / 128 * 128;
     constexpr size_t smem = 3 * NST * TBA + 3 * TBA + NST * 8;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_adjoint_zmarch<E, kIso, BY, NST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_adjoint_zmarch<E, kIso, BY, NST>, (int)smem, attr_gen, &ae)) return ae;
     CUtensorMap mT, mY, mC;
     if (!make_tensor_map_3d(&mT, T, sizeof(E), g, W, H) || !make_tensor_map_3d(&mY, ybar, sizeof(E), g, W, H) ||
         !make_tensor_map_3d(&mC, Ci, sizeof(E), g, W, H))
@@ -425,8 +419,7 @@ cudaError_t launch_adjoint_zmarch(E *Tbar, E *Cibar, const E *ybar, const E *T, 
     p.Kx = c.dtlam * c.ax;
     p.Ky = c.dtlam * c.ay;
     p.Kz = c.dtlam * c.az;
-    const char *v = getenv("PS_ADJ_KCHUNK");
-    const int kchunk = v ? atoi(v) : 0;
+    const int kchunk = launch_override(PS_OVERRIDE_ADJ_KCHUNK);
     const bool iso = c.ax == c.ay && c.ay == c.az;
     if (iso) return launch_adj_t<E, true, 8, 3>(Tbar, Cibar, ybar, T, Ci, g, p, kchunk, s);
     return launch_adj_t<E, false, 8, 3>(Tbar, Cibar, ybar, T, Ci, g, p, kchunk, s);

@@ -166,14 +166,9 @@ static cudaError_t launch_bz_t(const void *dev_table, int64_t nitems, int parity
     constexpr int PX = ZTraits<MODE>::PX;
     constexpr size_t sw = bz_smem<E, PX, 32, kBZ_WIDE_BY>(), sn = bz_smem<E, PX, 16, kBZ_NARROW_BY>();
     constexpr size_t smem = sw > sn ? sw : sn;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_batch_zmarch<MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_batch_zmarch<MODE>, (int)smem, attr_gen, &ae)) return ae;
     if (nitems < 1 || nitems > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     k_batch_zmarch<MODE><<<(unsigned)nitems, 256, smem, s>>>((const char *)dev_table, parity);
     return cudaGetLastError();
@@ -196,14 +191,9 @@ static cudaError_t launch_bz2_t(const void *dev_table, int64_t nitems2, int pari
     constexpr unsigned TBA = (W * (BY + 4) * sizeof(E) + 127) / 128 * 128;
     constexpr unsigned CBA = (W * (BY + 2) * sizeof(E) + 127) / 128 * 128;
     constexpr size_t smem = NT * TBA + (NC + 2) * CBA + (NT + NC) * 8;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_batch_zmarch2<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_batch_zmarch2<E>, (int)smem, attr_gen, &ae)) return ae;
     if (nitems2 < 1 || nitems2 > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     k_batch_zmarch2<E><<<(unsigned)nitems2, 32 * BY, smem, s>>>((const char *)dev_table, parity);
     return cudaGetLastError();

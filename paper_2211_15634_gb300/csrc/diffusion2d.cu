@@ -13,7 +13,6 @@
 // (node.cuh, emu64.cuh) with the z-neighbours set to the centre value: the z
 // difference is then exactly zero.
 #include <algorithm>
-#include <cstdlib>
 
 #include "emu64.cuh"
 #include "internal.h"
@@ -261,8 +260,7 @@ static cudaError_t launch_2d_t(void *T2, const void *T, const void *Ci, P2D p, i
     p.ny = ny;
     p.nstrips = (int)((nx + 32 * PX - 1) / (32 * PX));
     // chunks of 16-256 rows, about eight waves of resident warps (48 per SM)
-    const char *v = getenv("PS_CHUNK2D");
-    int chunk = v ? atoi(v) : 0;
+    int chunk = launch_override(PS_OVERRIDE_CHUNK2D);
     if (chunk <= 0) {
         const int64_t target = 8LL * 48 * sm_count();
         const int64_t c = (ny - 2) * (int64_t)p.nstrips / target;

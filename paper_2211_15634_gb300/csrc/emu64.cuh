@@ -20,10 +20,12 @@
 //    units of the common ulp, so S needs no conversion at all (for negative
 //    values the bit difference is minus the value difference; the sign of
 //    the packed result is flipped instead).
-//  * General path (other nodes, rare for smooth fields): every value is
-//    converted to fixed point at the largest exponent among the seven
-//    (57-bit magnitudes), then summed.  It is a separate, non-inlined
-//    function reached by a branch, so nodes on the fast path never execute it.
+//  * General path (other nodes): every value is converted to fixed point at
+//    the largest exponent among the seven (57-bit magnitudes), then summed.
+//    Per node it is a separate, non-inlined function reached by a branch, so
+//    nodes on the fast path never execute it; the z-march tiles instead take
+//    emu_lane_general (the same arithmetic, inlined) for all nodes of every lane
+//    of a warp at once, so the warp does not diverge.
 //  * Inf/NaN inputs fall back to the plain FP64 expression.
 //
 // Error: S is exact (the general path truncates values more than 57 binades
@@ -288,6 +290,47 @@ __device__ __forceinline__ double emu_step_node_scaled(unsigned long long c, uns
     if (emu_same_binade(c, xm, xp, ym, yp, zm, zp))
         return emu_fast_node_scaled(c, xm, xp, ym, yp, zm, zp, cs);
     return emu_general_node_scaled(c, xm, xp, ym, yp, zm, zp, cs);
+}
+
+// General path for the PX stencils of one thread at once (a warp whose lanes do
+// not all pass the same-binade check takes it for every lane, so the warp does not
+// diverge, and nothing is called).  Node by node it is the arithmetic of
+// emu_general_node(_scaled): the node's seven values in 57-bit fixed point at the
+// largest of their exponents, exact integer sums, one pack - so its results are
+// bit for bit those of the per-node general path that the fused-pair and column
+// kernels take.  Inf/NaN among a node's values: plain FP64, which propagates it.
+//   kScaled: out = fma(cs, S*2^sc, c) with ci = cs (pre-scaled coefficient);
+//   else:    out = fma(ci, L, c), L = emu_L<kIso>(per-axis sums).
+template <int PX, bool kScaled, bool kIso>
+__device__ __forceinline__ void emu_lane_general(const unsigned long long (&c)[PX], unsigned long long xl,
+                                                 unsigned long long xr, const unsigned long long (&ym)[PX],
+                                                 const unsigned long long (&yp)[PX],
+                                                 const unsigned long long (&zm)[PX],
+                                                 const unsigned long long (&zp)[PX], const double (&ci)[PX],
+                                                 const EmuCoef &k, double (&out)[PX]) {
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+        const unsigned long long xm = i == 0 ? xl : c[i - 1], xp = i == PX - 1 ? xr : c[i + 1];
+        long long sx, sy, sz;
+        int sc;
+        if (emu_sums_general(c[i], xm, xp, ym[i], yp[i], zm[i], zp[i], sx, sy, sz, sc)) {
+            if (kScaled)
+                out[i] = fma(ci[i], emu_pack(sx + sy + sz, sc), bitsd(c[i]));
+            else
+                out[i] = fma(ci[i], emu_L<kIso>(sx, sy, sz, sc, 0ull, k), bitsd(c[i]));
+        } else {  // Inf / NaN
+            const double cc = bitsd(c[i]);
+            if (kScaled) {
+                out[i] = cc + ci[i] * ((((bitsd(xm) + bitsd(xp)) + (bitsd(ym[i]) + bitsd(yp[i]))) +
+                                        (bitsd(zm[i]) + bitsd(zp[i]))) - 6.0 * cc);
+            } else {
+                const double d2x = (bitsd(xp) - cc) - (cc - bitsd(xm));
+                const double d2y = (bitsd(yp[i]) - cc) - (cc - bitsd(ym[i]));
+                const double d2z = (bitsd(zp[i]) - cc) - (cc - bitsd(zm[i]));
+                out[i] = cc + k.dtlam * (ci[i] * ((d2x * k.ax + d2y * k.ay) + d2z * k.az));
+            }
+        }
+    }
 }
 
 // One node, either path (per-lane branch).

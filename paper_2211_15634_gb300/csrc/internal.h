@@ -28,6 +28,16 @@ struct Grid3 {
 int sm_count();
 int current_device();
 
+// Generation of the current device's context (grows after cudaDeviceReset), and a
+// once-per-context cudaFuncSetAttribute(MaxDynamicSharedMemorySize) keyed on it:
+// done_gen is a launcher's array of 64 generations; false (with *err) on failure.
+unsigned context_generation();
+bool set_smem_attr_once(const void *func, int smem, unsigned *done_gen, cudaError_t *err);
+
+// Launch-shape override set through ps_set_launch_override (PS_OVERRIDE_*); 0 when
+// unset, which leaves the choice to the library's own rule (abi.cu).
+int launch_override(int which);
+
 // Record a message for ps_last_error() and return the status (abi.cu).
 int api_fail(int status, const char *msg);
 int api_cuda_fail(cudaError_t e, const char *where);
@@ -39,7 +49,8 @@ cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, 
                                  Grid3 g, cudaStream_t s);
 cudaError_t launch_step_f32(float *T2, const float *T, const float *Ci, StepCoef c, Grid3 g,
                             cudaStream_t s);
-cudaError_t launch_step_f32_comp(float *T2, const float *T, float *comp, const float *Ci,
+// compensated FP32 step on the two-float state (T, E) -> (T2, E2)
+cudaError_t launch_step_f32_comp(float *T2, const float *T, float *E2, const float *E, const float *Ci,
                                  StepCoef c, Grid3 g, cudaStream_t s);
 cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
                                    cudaStream_t s);
@@ -80,6 +91,10 @@ cudaError_t launch_copy_boundary_many(void *dst, int64_t count, int64_t gstride,
 cudaError_t launch_to_deviation(float *D, const double *T, double t_ref, int64_t n, cudaStream_t s);
 cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64_t n,
                                   cudaStream_t s);
+cudaError_t launch_to_deviation_pair(float *D, float *E, const double *T, double t_ref, int64_t n,
+                                     cudaStream_t s);
+cudaError_t launch_from_deviation_pair(double *T, const float *D, const float *E, double t_ref, int64_t n,
+                                       cudaStream_t s);
 
 // ---- adjoint (adjoint.cu) ----
 cudaError_t launch_adjoint_f64(double *Tbar, double *Cibar, const double *ybar, const double *T,
@@ -88,6 +103,17 @@ cudaError_t launch_adjoint_f64_scaled(double *Tbar, double *Csbar, const double 
                                       const double *T, const double *Cs, Grid3 g, cudaStream_t s);
 cudaError_t launch_adjoint_f32(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
+
+// ---- reverse sweep with the adjoint state in fixed point (adjoint_fx.cu) ----
+constexpr size_t kFxStateBytes = 48;  // three slots of {max|Y|, sigma, bad}
+bool adjoint_fx_supported(Grid3 g, const void *const *ptrs, int nptr);
+cudaError_t launch_adjoint_fx_begin(long long *Y, const double *ybar, int64_t n, void *state,
+                                    cudaStream_t s);
+cudaError_t launch_adjoint_fx(long long *Yout, double *Csbar, const long long *Yin, const double *T,
+                              const double *Cs, Grid3 g, void *state, int step, cudaStream_t s);
+cudaError_t launch_adjoint_fx_end(double *ybar, const long long *Y, int64_t n, const void *state, int step,
+                                  cudaStream_t s);
+unsigned adjoint_fx_device_error(bool clear);
 
 // ---- reductions (reduce.cu) ----
 constexpr int kReduceBlocks = 1024;           // fixed partition => deterministic sums

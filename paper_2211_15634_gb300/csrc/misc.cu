@@ -75,6 +75,26 @@ __global__ void k_from_deviation(double *__restrict__ T, const float *__restrict
         T[p] = (double)D[p] + t_ref;
 }
 
+// Two-float deviation: v = T - t_ref in FP64, D = v rounded to float, E = v - D
+// rounded to float (D + E carries about 48 bits of v).
+__global__ void k_to_deviation_pair(float *__restrict__ D, float *__restrict__ E,
+                                    const double *__restrict__ T, double t_ref, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const double v = T[p] - t_ref;
+        const float d = __double2float_rn(v);
+        D[p] = d;
+        E[p] = __double2float_rn(v - (double)d);
+    }
+}
+
+__global__ void k_from_deviation_pair(double *__restrict__ T, const float *__restrict__ D,
+                                      const float *__restrict__ E, double t_ref, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        T[p] = ((double)D[p] + (double)E[p]) + t_ref;
+}
+
 __global__ void k_scale_ci(double *__restrict__ Cs, const double *__restrict__ Ci, double K, int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) Cs[p] = K * Ci[p];
@@ -95,6 +115,18 @@ cudaError_t launch_to_deviation(float *D, const double *T, double t_ref, int64_t
 cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64_t n,
                                   cudaStream_t s) {
     k_from_deviation<<<ew_blocks(n), 256, 0, s>>>(T, D, t_ref, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_deviation_pair(float *D, float *E, const double *T, double t_ref, int64_t n,
+                                     cudaStream_t s) {
+    k_to_deviation_pair<<<ew_blocks(n), 256, 0, s>>>(D, E, T, t_ref, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_deviation_pair(double *T, const float *D, const float *E, double t_ref, int64_t n,
+                                       cudaStream_t s) {
+    k_from_deviation_pair<<<ew_blocks(n), 256, 0, s>>>(T, D, E, t_ref, n);
     return cudaGetLastError();
 }
 

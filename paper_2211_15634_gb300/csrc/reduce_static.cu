@@ -22,21 +22,26 @@ constexpr int kStaticFinalThreads = 1024;
 
 static __device__ __align__(256) double g_static_partials[kStaticPartials];
 
-// Host-side copies of the array's device address, one per device.  In host
-// code the name g_static_partials is only a stand-in for the symbol, not a
-// device address, so the address is looked up with cudaGetSymbolAddress.
+// Host-side copies of the array's device address, one per device, each with the
+// generation of the context it was looked up in.  In host code the name
+// g_static_partials is only a stand-in for the symbol, not a device address, so
+// the address is looked up with cudaGetSymbolAddress once per device and context
+// (again after cudaDeviceReset, which loads the library's module anew).
 static double *g_static_ptr[64] = {nullptr};
+static unsigned g_static_gen[64] = {0};
 static std::mutex g_static_mu;
 
 static cudaError_t static_partials(double **out) {
     const int d = current_device();
     if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    const unsigned gen = context_generation();
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[d]) {
+    if (!g_static_ptr[d] || g_static_gen[d] != gen) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
         if (e != cudaSuccess) return e;
         g_static_ptr[d] = (double *)p;
+        g_static_gen[d] = gen;
     }
     *out = g_static_ptr[d];
     return cudaSuccess;
@@ -85,8 +90,9 @@ extern "C" int ps_dot_static(double *out_dev, const void *A, const void *B, int6
                              void *stream) {
     if (!out_dev || !A || !B) return api_fail(PS_ERR_ARG, "ps_dot_static: out_dev, A or B is NULL");
     if (dtype != PS_F32 && dtype != PS_F64) return api_fail(PS_ERR_ARG, "ps_dot_static: bad dtype");
-    if (((uintptr_t)A | (uintptr_t)B) & 15u)
-        return api_fail(PS_ERR_ALIGN, "ps_dot_static: A and B must be 16-byte aligned");
+    const uintptr_t esz = dtype == PS_F64 ? 8u : 4u;  // the kernel reads one element at a time
+    if (((uintptr_t)A | (uintptr_t)B) & (esz - 1u))
+        return api_fail(PS_ERR_ALIGN, "ps_dot_static: A and B must be aligned to their element size");
     if (n < 1) return api_fail(PS_ERR_ARG, "ps_dot_static: n < 1");
     const int64_t nmax = kStaticChunk * kStaticPartials;
     if (n > nmax) {

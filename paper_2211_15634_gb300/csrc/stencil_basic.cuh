@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "emu64.cuh"
+#include "node.cuh"
 
 namespace psd {
 
@@ -67,11 +68,14 @@ inline cudaError_t launch_step_basic_emu(double *T2, const double *T, const doub
 }
 
 // Fig. 1 step!: T2 = T + dt*lam*Ci*((d2x*_dx^2 + d2y*_dy^2) + d2z*_dz^2) at
-// interior nodes; the z-range of this block is [k0, k1).
+// interior nodes; the z-range of this block is [k0, k1).  kComp (FP32): the state
+// is the two-float pair (T, E) and (T2, E2) receives the compensated step
+// (comp32_node, node.cuh).
 template <typename F, bool kComp>
 __global__ void __launch_bounds__(256)
-k_step_basic(F *__restrict__ T2, const F *__restrict__ T, F *__restrict__ comp,
-             const F *__restrict__ Ci, CoefT<F> c, int64_t nx, int64_t ny, int64_t nz, int kchunk) {
+k_step_basic(F *__restrict__ T2, const F *__restrict__ T, F *__restrict__ E2,
+             const F *__restrict__ E, const F *__restrict__ Ci, CoefT<F> c, int64_t nx, int64_t ny,
+             int64_t nz, int kchunk) {
     const int64_t i = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = 1 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (i > nx - 2 || j > ny - 2) return;
@@ -83,18 +87,17 @@ k_step_basic(F *__restrict__ T2, const F *__restrict__ T, F *__restrict__ comp,
     F tm = T[p - sz], tc = T[p];
     for (int64_t k = k0; k < k1; ++k, p += sz) {
         const F tp = T[p + sz];
-        const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
-        const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
-        const F d2z = (tp - tc) - (tc - tm);
-        const F lap = (d2x * c.ax + d2y * c.ay) + d2z * c.az;
-        if (kComp) {
-            // compensated update: y = delta - c; t = D + y; c = (t - D) - y; D = t
-            const F delta = c.dtlam * (Ci[p] * lap);
-            const F y = delta - comp[p];
-            const F t = tc + y;
-            comp[p] = (t - tc) - y;
-            T2[p] = t;
+        if constexpr (kComp) {
+            float e2;
+            T2[p] = comp32_node(tc, T[p - 1], T[p + 1], T[p - sy], T[p + sy], tm, tp, E[p], E[p - 1],
+                                E[p + 1], E[p - sy], E[p + sy], E[p - sz], E[p + sz], Ci[p], c.dtlam,
+                                c.ax, c.ay, c.az, &e2);
+            E2[p] = e2;
         } else {
+            const F d2x = (T[p + 1] - tc) - (tc - T[p - 1]);
+            const F d2y = (T[p + sy] - tc) - (tc - T[p - sy]);
+            const F d2z = (tp - tc) - (tc - tm);
+            const F lap = (d2x * c.ax + d2y * c.ay) + d2z * c.az;
             T2[p] = tc + c.dtlam * (Ci[p] * lap);
         }
         tm = tc;
@@ -103,7 +106,7 @@ k_step_basic(F *__restrict__ T2, const F *__restrict__ T, F *__restrict__ comp,
 }
 
 template <typename F, bool kComp>
-cudaError_t launch_step_basic(F *T2, const F *T, F *comp, const F *Ci, CoefT<F> c, int64_t nx,
+cudaError_t launch_step_basic(F *T2, const F *T, F *E2, const F *E, const F *Ci, CoefT<F> c, int64_t nx,
                               int64_t ny, int64_t nz, int nsm, cudaStream_t s) {
     const dim3 block(32, 8, 1);
     const int64_t gx = (nx - 2 + block.x - 1) / block.x, gy = (ny - 2 + block.y - 1) / block.y;
@@ -114,7 +117,7 @@ cudaError_t launch_step_basic(F *T2, const F *T, F *comp, const F *Ci, CoefT<F> 
     const int64_t gz = (nz - 2 + kchunk - 1) / kchunk;
     if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return cudaErrorInvalidConfiguration;
     k_step_basic<F, kComp><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), block, 0, s>>>(
-        T2, T, comp, Ci, c, nx, ny, nz, (int)kchunk);
+        T2, T, E2, E, Ci, c, nx, ny, nz, (int)kchunk);
     return cudaGetLastError();
 }
 

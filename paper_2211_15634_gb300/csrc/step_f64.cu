@@ -12,7 +12,7 @@ static CoefT<double> coef_f64(StepCoef c) { return CoefT<double>{c.dtlam, c.ax, 
 
 cudaError_t launch_step_f64_native(double *T2, const double *T, const double *Ci, StepCoef c,
                                    Grid3 g, cudaStream_t s) {
-    return launch_step_basic<double, false>(T2, T, nullptr, Ci, coef_f64(c), g.nx, g.ny, g.nz,
+    return launch_step_basic<double, false>(T2, T, nullptr, nullptr, Ci, coef_f64(c), g.nx, g.ny, g.nz,
                                             sm_count(), s);
 }
 
@@ -27,8 +27,8 @@ cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, 
                                  Grid3 g, cudaStream_t s) {
     if (!emu_ok(c)) return launch_step_f64_native(T2, T, Ci, c, g, s);
     const bool iso = c.ax == c.ay && c.ay == c.az;
-    if (zmarch_supported(g, 8, T2, T, Ci))
-        return launch_zmarch(iso ? Z_F64_EMU_ISO : Z_F64_EMU_ANISO, T2, T, nullptr, Ci, c, g, s);
+    if (step_tma_ok(g, 8, T2, T, Ci))
+        return launch_zmarch(iso ? Z_F64_EMU_ISO : Z_F64_EMU_ANISO, T2, T, nullptr, nullptr, Ci, c, g, s);
     const EmuCoef ek{emu_const(c.dtlam * c.ax), emu_const(c.dtlam * c.ay), emu_const(c.dtlam * c.az),
                      c.dtlam, c.ax, c.ay, c.az, c.dtlam * c.ax};
     return launch_step_basic_emu(T2, T, Ci, ek, iso, g.nx, g.ny, g.nz, sm_count(), s);
@@ -38,7 +38,7 @@ cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, 
 cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
                                    cudaStream_t s) {
     const StepCoef dummy{1.0, 1.0, 1.0, 1.0};
-    if (zmarch_supported(g, 8, T2, T, Cs)) return launch_zmarch(Z_F64_SCALED, T2, T, nullptr, Cs, dummy, g, s);
+    if (step_tma_ok(g, 8, T2, T, Cs)) return launch_zmarch(Z_F64_SCALED, T2, T, nullptr, nullptr, Cs, dummy, g, s);
     const EmuCoef ek{};
     return launch_step_basic_emu(T2, T, Cs, ek, true, g.nx, g.ny, g.nz, sm_count(), s, true);
 }
@@ -46,12 +46,12 @@ cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs
 const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c,
                                  bool scaled) {
     if (scaled) {
-        if (!zmarch_supported(g, 8, T2, T, Ci)) return "k_step_basic_emu";
+        if (!step_tma_ok(g, 8, T2, T, Ci)) return "k_step_basic_emu";
         return f64_scaled_wide(g, T2, T, Ci) ? "k_zmarch<F64_SCALED4>" : "k_zmarch<F64_SCALED>";
     }
     if (!emu_ok(c)) return "k_step_basic<double>";
     const bool iso = c.ax == c.ay && c.ay == c.az;
-    if (zmarch_supported(g, 8, T2, T, Ci)) return iso ? "k_zmarch<F64_EMU_ISO>" : "k_zmarch<F64_EMU_ANISO>";
+    if (step_tma_ok(g, 8, T2, T, Ci)) return iso ? "k_zmarch<F64_EMU_ISO>" : "k_zmarch<F64_EMU_ANISO>";
     return "k_step_basic_emu";
 }
 

@@ -6,8 +6,6 @@
 // are 16-byte aligned.
 #include <cudaTypedefs.h>
 
-#include <cstdlib>
-#include <cstring>
 
 #include <map>
 #include <mutex>
@@ -27,12 +25,13 @@ __device__ unsigned g_zmarch_error;  // set when an mbarrier wait times out
 template <int MODE, int BY, int NST>
 __global__ void __launch_bounds__(32 * BY, 1)
 k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmC,
-         void *__restrict__ T2v, void *__restrict__ compv, const ZParams p) {
+         const __grid_constant__ CUtensorMap tmE, void *__restrict__ T2v, void *__restrict__ E2v,
+         const ZParams p) {
     const int X0 = (int)(blockIdx.x % p.ntx) * (32 * ZTraits<MODE>::PX);
     const int Y0 = (int)(blockIdx.x / p.ntx) * BY;
     const int k0 = 1 + (int)blockIdx.y * p.kchunk;
     const int k1 = (int)min((int64_t)k0 + p.kchunk, p.nz - 1);  // output planes [k0, k1)
-    zmarch_tile<MODE, BY, NST>(&tmT, &tmC, T2v, compv, p, X0, Y0, k0, k1, &g_zmarch_error);
+    zmarch_tile<MODE, BY, NST>(&tmT, &tmC, T2v, E2v, p, X0, Y0, k0, k1, &g_zmarch_error, &tmE);
 }
 
 // Failure-path self-test: one CTA waits on an mbarrier that nothing ever arrives on.
@@ -96,26 +95,31 @@ bool zmarch_supported(Grid3 g, int esz, const void *a, const void *b, const void
     return encode_fn() != nullptr;
 }
 
+bool step_tma_ok(Grid3 g, int esz, const void *a, const void *b, const void *c) {
+    return launch_override(PS_OVERRIDE_STEP_PLAIN) != 1 && zmarch_supported(g, esz, a, b, c);
+}
+
 template <int MODE, int BY, int NST>
-static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const void *Ci, Grid3 g,
-                                   ZParams p, int kchunk, cudaStream_t s) {
+static cudaError_t launch_zmarch_t(void *T2, const void *T, void *E2, const void *Ein, const void *Ci,
+                                   Grid3 g, ZParams p, int kchunk, cudaStream_t s) {
     using E = typename ZTraits<MODE>::E;
     constexpr int PX = ZTraits<MODE>::PX, BX = 32 * PX, W = BX + 2 * PX, H = BY + 2;
     constexpr unsigned TBA = (W * H * sizeof(E) + 127) / 128 * 128;
     constexpr unsigned CBA = (BX * BY * sizeof(E) + 127) / 128 * 128;
-    constexpr size_t smem = NST * (TBA + CBA) + NST * 8;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_zmarch<MODE, BY, NST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
-    CUtensorMap mT, mC;
+    constexpr unsigned EBA = MODE == Z_F32_COMP ? TBA : 0u;
+    constexpr size_t smem = NST * (TBA + CBA + EBA) + NST * 8;
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_zmarch<MODE, BY, NST>, (int)smem, attr_gen, &ae)) return ae;
+    CUtensorMap mT, mC, mE;
     if (!make_tensor_map_3d(&mT, T, sizeof(E), g, W, H) ||
         !make_tensor_map_3d(&mC, Ci, sizeof(E), g, BX, BY))
         return cudaErrorInvalidValue;
+    if (MODE == Z_F32_COMP) {
+        if (!make_tensor_map_3d(&mE, Ein, sizeof(E), g, W, H)) return cudaErrorInvalidValue;
+    } else {
+        mE = mT;  // not read
+    }
     const int64_t ntx = (g.nx + BX - 1) / BX, nty = (g.ny + BY - 1) / BY;
     const int64_t tiles = ntx * nty;
     if (kchunk <= 0) {
@@ -138,7 +142,7 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *comp, const vo
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
     k_zmarch<MODE, BY, NST><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
-        mT, mC, T2, comp, p);
+        mT, mC, mE, T2, E2, p);
     return cudaGetLastError();
 }
 
@@ -156,8 +160,7 @@ static ZParams make_params(StepCoef c) {
 bool tma_encoder_available() { return encode_fn() != nullptr; }
 
 bool f64_scaled_wide(Grid3 g, const void *T2, const void *T, const void *Ci) {
-    const char *var = getenv("PS_F64_VARIANT");
-    if (var && strcmp(var, "px2") == 0) return false;
+    if (launch_override(PS_OVERRIDE_F64_PX2) == 1) return false;
     return g.nx % 4 == 0 && ((((uintptr_t)T2 | (uintptr_t)T | (uintptr_t)Ci) & 31u) == 0);
 }
 
@@ -170,50 +173,33 @@ ZParams zparams_for(StepCoef c, Grid3 g, int64_t pitch) {
     return p;
 }
 
-
-static int env_int(const char *name, int dflt) {
-    const char *v = getenv(name);
-    return v ? atoi(v) : dflt;
-}
-
-cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
-                          Grid3 g, cudaStream_t s) {
+cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *E2, const void *Ein, const void *Ci,
+                          StepCoef c, Grid3 g, cudaStream_t s) {
     const ZParams p = make_params(c);
-    const int kchunk = env_int("PS_KCHUNK", 0);
+    const int kchunk = launch_override(PS_OVERRIDE_KCHUNK);
     const bool positive = c.dtlam * c.ax > 0 && c.dtlam * c.ay > 0 && c.dtlam * c.az > 0;
-    // Isotropic FP64 grids default to fma(Ci*K, S, T) (two FP64 ops, fewest
-    // integer ops: measured fastest).  PS_F64_VARIANT selects an alternative
-    // for measurements: "umul" = one DFMA plus a 64-bit high multiply,
-    // "by16" = the umul form in 64 x 16 tiles; "px2" keeps the pre-scaled step at two
-    // nodes per thread.
-    const char *var = getenv("PS_F64_VARIANT");
-    const bool dmul = !(var && (strcmp(var, "umul") == 0 || strcmp(var, "by16") == 0));
-    const bool by16 = var && strcmp(var, "by16") == 0;
     switch (mode) {
         case Z_F64_EMU_ISO:
         case Z_F64_EMU_ANISO:
-            if (!positive) return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
-            if (mode == Z_F64_EMU_ISO) {
-                if (dmul)
-                    return launch_zmarch_t<Z_F64_EMU_ISO_DMUL, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
-                if (by16)
-                    return launch_zmarch_t<Z_F64_EMU_ISO, 16, 4>(T2, T, comp, Ci, g, p, kchunk, s);
-                return launch_zmarch_t<Z_F64_EMU_ISO, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
-            }
-            return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
+            if (!positive) return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+            // isotropic grids: fma(Ci*K, S, T), two FP64 ops and the fewest integer ops
+            // (measured faster than one DFMA after a 64 x 64-bit high multiply by K)
+            if (mode == Z_F64_EMU_ISO)
+                return launch_zmarch_t<Z_F64_EMU_ISO_DMUL, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
         case Z_F64_NATIVE:
-            return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
         case Z_F64_SCALED:
             // four nodes per thread (4-row tiles, 128 threads) where rows allow 32-byte
             // accesses: measured 2-3% faster at 512^3 and 768^3 than two per thread
             // (8-row tiles of four per thread, at two CTAs per SM, were 15% slower)
             if (f64_scaled_wide(g, T2, T, Ci))
-                return launch_zmarch_t<Z_F64_SCALED4, 4, 4>(T2, T, comp, Ci, g, p, kchunk, s);
-            return launch_zmarch_t<Z_F64_SCALED, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
+                return launch_zmarch_t<Z_F64_SCALED4, 4, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F64_SCALED, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
         case Z_F32:
-            return launch_zmarch_t<Z_F32, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F32, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
         case Z_F32_COMP:
-            return launch_zmarch_t<Z_F32_COMP, 8, 4>(T2, T, comp, Ci, g, p, kchunk, s);
+            return launch_zmarch_t<Z_F32_COMP, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -29,6 +29,8 @@ struct ZParams {
 
 // True when the TMA path can serve this grid and these pointers.
 bool zmarch_supported(Grid3 g, int esz, const void *a, const void *b, const void *c);
+// The same for one forward step, unless PS_OVERRIDE_STEP_PLAIN asks for the plain kernel.
+bool step_tma_ok(Grid3 g, int esz, const void *a, const void *b, const void *c);
 // 3-D tiled tensor map over a (nz, ny, nx) field with a bx x by x 1 box.
 bool make_tensor_map_3d(CUtensorMap *m, const void *ptr, int esz, Grid3 g, unsigned bx, unsigned by);
 // The same over a grid whose rows are `pitch` elements apart (pitch*esz a multiple of 16).
@@ -51,8 +53,10 @@ unsigned adjoint_device_error(bool clear);
 // TMA-fed transposed step on the pre-scaled coefficient (adjoint_scaled.cu).
 cudaError_t launch_adjoint_scaled(double *Tbar, double *Csbar, const double *ybar, const double *T,
                                   const double *Cs, Grid3 g, cudaStream_t s);
-cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *comp, const void *Ci, StepCoef c,
-                          Grid3 g, cudaStream_t s);
+// One step of the TMA z-march in `mode`; E2 / Ein: the correction fields of the
+// two-float state (Z_F32_COMP only, else unused).
+cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *E2, const void *Ein, const void *Ci,
+                          StepCoef c, Grid3 g, cudaStream_t s);
 unsigned zmarch_device_error(bool clear);
 
 }  // namespace psd

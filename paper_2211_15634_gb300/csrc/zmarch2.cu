@@ -2,7 +2,6 @@
 // (tile, chunk) runs the fused-pair tile body of zmarch2_tile.cuh.
 #include <cudaTypedefs.h>
 
-#include <cstdlib>
 
 #include "internal.h"
 #include "node.cuh"
@@ -35,21 +34,15 @@ static cudaError_t launch_z2(E *T2, const E *T, const E *Ci, Z2Params p, Grid3 g
     constexpr unsigned TBA = (W * (BY + 4) * sizeof(E) + 127) / 128 * 128;
     constexpr unsigned CBA = (W * (BY + 2) * sizeof(E) + 127) / 128 * 128;
     constexpr size_t smem = NT * TBA + (NC + 2) * CBA + (NT + NC) * 8;
-    static bool attr_done[64] = {false};
-    const int dev = current_device();
-    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_zmarch2<E, BY, NT, NC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
+    static unsigned attr_gen[64] = {0};
+    cudaError_t ae;
+    if (!set_smem_attr_once((const void *)k_zmarch2<E, BY, NT, NC>, (int)smem, attr_gen, &ae)) return ae;
     CUtensorMap mT, mC;
     if (!make_tensor_map_3d(&mT, T, sizeof(E), g, W, BY + 4) ||
         !make_tensor_map_3d(&mC, Ci, sizeof(E), g, W, BY + 2))
         return cudaErrorInvalidValue;
     const int64_t ntx = (g.nx + BX - 1) / BX, nty = (g.ny + BY - 1) / BY, tiles = ntx * nty;
-    const char *v = getenv("PS_KCHUNK2");
-    int kchunk = v ? atoi(v) : 0;
+    int kchunk = launch_override(PS_OVERRIDE_KCHUNK2);
     if (kchunk <= 0) {
         // the prologue costs two extra T1 planes: long chunks, but about three waves
         const int64_t waves = 3LL * 3 * sm_count();

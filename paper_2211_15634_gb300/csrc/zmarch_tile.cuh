@@ -14,6 +14,8 @@
 // z-neighbours) and reads x/y neighbours of plane k from shared memory, so
 // every T value is read from HBM once (plus halos that mostly hit in L2).
 // T2 is written with 16-byte stores.  Boundary nodes are never written.
+// The compensated FP32 mode stages the correction field E of its two-float
+// state like T (same box, same stage) and writes E2 beside T2.
 #pragma once
 
 #include <cuda.h>
@@ -65,12 +67,14 @@ __device__ __forceinline__ E vget(const V &v, int i) {
 // tile's node coordinates, boundary included; only interior nodes are written).
 // tmT / tmC: tensor maps of T (box W x H) and Ci (box BX x BY), in parameter or
 // global memory.  Rows are p.pitch elements apart, planes p.pitch * p.ny.
+// Z_F32_COMP (two-float state D + E): tmE maps E (box W x H, staged with T in the same
+// stage) and E2v receives the new correction field; other modes ignore both.
 // A timed-out wait sets bit 0 of *err and the CTA leaves after draining its copies.
 template <int MODE, int BY, int NST, int LPR = 32>
 __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtensorMap *tmC,
-                                            void *__restrict__ T2v, void *__restrict__ compv,
+                                            void *__restrict__ T2v, void *__restrict__ E2v,
                                             const ZParams &p, int X0, int Y0, int k0, int k1,
-                                            unsigned *err) {
+                                            unsigned *err, const CUtensorMap *tmE = nullptr) {
     using Tr = ZTraits<MODE>;
     using E = typename Tr::E;
     using V = typename Tr::V;
@@ -78,10 +82,13 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
     constexpr int PX = Tr::PX, HX = PX, BX = LPR * PX, W = BX + 2 * HX, H = BY + 2;
     constexpr unsigned TB = W * H * sizeof(E), CB = BX * BY * sizeof(E);
     constexpr unsigned TBA = (TB + 127) / 128 * 128, CBA = (CB + 127) / 128 * 128;
+    constexpr bool kComp = MODE == Z_F32_COMP;
+    constexpr unsigned EBA = kComp ? TBA : 0u;  // E boxes (two-float state) after the Ci boxes
     extern __shared__ __align__(128) unsigned char smem[];
     E *sT = (E *)smem;
     E *sC = (E *)(smem + NST * TBA);
-    uint64_t *bar = (uint64_t *)(smem + NST * (TBA + CBA));
+    E *sE = (E *)(smem + NST * (TBA + CBA));
+    uint64_t *bar = (uint64_t *)(smem + NST * (TBA + CBA + EBA));
     __shared__ int s_abort;
 
     const int lane = threadIdx.x % LPR, ty = threadIdx.x / LPR;  // column group, tile row
@@ -97,9 +104,10 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
     constexpr unsigned TSTRIDE = TBA / sizeof(E), CSTRIDE = CBA / sizeof(E);
     auto issue = [&](int s, int q) {
         const bool ci = q >= k0 && q < k1;
-        mbar_expect_tx(&bar[s], TB + (ci ? CB : 0u));
+        mbar_expect_tx(&bar[s], TB + (ci ? CB : 0u) + (kComp ? TB : 0u));
         tma_load_3d(sT + s * TSTRIDE, tmT, &bar[s], X0 - HX, Y0 - 1, q);
         if (ci) tma_load_3d(sC + s * CSTRIDE, tmC, &bar[s], X0, Y0, q);
+        if constexpr (kComp) tma_load_3d(sE + s * TSTRIDE, tmE, &bar[s], X0 - HX, Y0 - 1, q);
     };
     if (threadIdx.x == 0)
         for (int s = 0; s < NST; ++s)
@@ -124,8 +132,11 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
     const int row = ty + 1, col = HX + lane * PX;
     bool ok = acquire(0);
     V qm = *(const V *)(sT + row * W + col);
+    V eqm{}, eqc{};  // E of planes k-1 and k at the own nodes (two-float state)
+    if constexpr (kComp) eqm = *(const V *)(sE + row * W + col);
     ok = acquire(1 % NST) && ok;
     V qc = *(const V *)(sT + (1 % NST) * TSTRIDE + row * W + col);
+    if constexpr (kComp) eqc = *(const V *)(sE + (1 % NST) * TSTRIDE + row * W + col);
     if (!ok) {
         s_abort = 1;
         atomicOr(err, 1u);
@@ -145,7 +156,7 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
     const unsigned rmask = LPR == 32 ? 0xffffffffu : __ballot_sync(0xffffffffu, row_ok);
     bool all_x = gx0 >= 1 && gx0 + PX - 1 <= p.nx - 2;
     E *__restrict__ T2 = (E *)T2v;
-    E *__restrict__ comp = (E *)compv;
+    E *__restrict__ E2 = (E *)E2v;
     int sk = 1 % NST;  // stage of plane k
     const int64_t plane = p.pitch * p.ny;
     int64_t base = (int64_t)gx0 + p.pitch * ((int64_t)gy + p.ny * (int64_t)k0);  // own nodes, plane k
@@ -159,18 +170,19 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
         const V up = *(const V *)(Tk + (row - 1) * W + col);
         const V dn = *(const V *)(Tk + (row + 1) * W + col);
         const V civ = *(const V *)(sC + sk * CSTRIDE + ty * BX + lane * PX);
+        V eqn{}, eup{}, edn{};  // E of plane k+1 and the y-neighbours of plane k
+        E eleft{}, eright{};
+        if constexpr (kComp) {
+            const E *Ek = sE + sk * TSTRIDE;
+            eqn = *(const V *)(sE + sk1 * TSTRIDE + row * W + col);
+            eleft = Ek[row * W + col - 1];
+            eright = Ek[row * W + col + PX];
+            eup = *(const V *)(Ek + (row - 1) * W + col);
+            edn = *(const V *)(Ek + (row + 1) * W + col);
+        }
 
         if (row_ok) {
-            V cv{};
-            if constexpr (MODE == Z_F32_COMP) {
-                if (all_x) cv = *(const V *)(comp + base);
-                else
-#pragma unroll
-                    for (int i = 0; i < PX; ++i) {
-                        const int gx = gx0 + i;
-                        reinterpret_cast<E *>(&cv)[i] = (gx >= 1 && gx <= p.nx - 2) ? comp[base + i] : E(0);
-                    }
-            }
+            V cv{};  // E2 at the own nodes (two-float state)
             V out;
             if constexpr (MODE == Z_F64_EMU_ISO || MODE == Z_F64_EMU_ANISO ||
                           MODE == Z_F64_EMU_ISO_DMUL || MODE == Z_F64_SCALED || MODE == Z_F64_SCALED4) {
@@ -240,17 +252,13 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                             reinterpret_cast<E *>(&out)[i] = emu_fast_node<kIso, kDmul>(
                                 c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci, p.ek);
                     }
-                } else {
+                } else {  // one general path for the whole warp (emu64.cuh)
+                    double ci[PX], o[PX];
 #pragma unroll
-                    for (int i = 0; i < PX; ++i) {
-                        const double ci = (double)vget<V, E>(civ, i);
-                        if constexpr (kScaled)
-                            reinterpret_cast<E *>(&out)[i] =
-                                emu_step_node_scaled(c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci);
-                        else
-                            reinterpret_cast<E *>(&out)[i] = emu_step_node<kIso, kDmul>(
-                                c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci, p.ek);
-                    }
+                    for (int i = 0; i < PX; ++i) ci[i] = (double)vget<V, E>(civ, i);
+                    emu_lane_general<PX, kScaled, kIso>(c, xm[0], xp[PX - 1], ym, yp, zm, zp, ci, p.ek, o);
+#pragma unroll
+                    for (int i = 0; i < PX; ++i) reinterpret_cast<E *>(&out)[i] = o[i];
                 }
             } else
 #pragma unroll
@@ -268,30 +276,27 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                     r = c + p.ek.dtlam * (ci * ((d2x * p.ek.ax + d2y * p.ek.ay) + d2z * p.ek.az));
                 } else if constexpr (MODE == Z_F32) {
                     r = f32_node(c, xm, xp, ym, yp, zm, zp, ci, p.fdtlam, p.fax, p.fay, p.faz);
-                } else {
-                    const float d2x = (xp - c) - (c - xm), d2y = (yp - c) - (c - ym);
-                    const float d2z = (zp - c) - (c - zm);
-                    const float lap = (d2x * p.fax + d2y * p.fay) + d2z * p.faz;
-                    {
-                        const float delta = p.fdtlam * (ci * lap);
-                        const float yv = delta - vget<V, E>(cv, i);
-                        const float t = c + yv;
-                        reinterpret_cast<E *>(&cv)[i] = (t - c) - yv;
-                        r = t;
-                    }
+                } else {  // Z_F32_COMP
+                    const E el = i == 0 ? eleft : vget<V, E>(eqc, i - 1);
+                    const E er = i == PX - 1 ? eright : vget<V, E>(eqc, i + 1);
+                    float e2;
+                    r = comp32_node(c, xm, xp, ym, yp, zm, zp, vget<V, E>(eqc, i), el, er,
+                                    vget<V, E>(eup, i), vget<V, E>(edn, i), vget<V, E>(eqm, i),
+                                    vget<V, E>(eqn, i), ci, p.fdtlam, p.fax, p.fay, p.faz, &e2);
+                    reinterpret_cast<E *>(&cv)[i] = e2;
                 }
                 reinterpret_cast<E *>(&out)[i] = r;
             }
             if (all_x) {
                 *(V *)(T2 + base) = out;
-                if constexpr (MODE == Z_F32_COMP) *(V *)(comp + base) = cv;
+                if constexpr (kComp) *(V *)(E2 + base) = cv;
             } else {
 #pragma unroll
                 for (int i = 0; i < PX; ++i) {
                     const int gx = gx0 + i;
                     if (gx >= 1 && gx <= p.nx - 2) {
                         T2[base + i] = vget<V, E>(out, i);
-                        if constexpr (MODE == Z_F32_COMP) comp[base + i] = vget<V, E>(cv, i);
+                        if constexpr (kComp) E2[base + i] = vget<V, E>(cv, i);
                     }
                 }
             }
@@ -309,6 +314,10 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
         sk = sk1;
         qm = qc;
         qc = qn;
+        if constexpr (kComp) {
+            eqm = eqc;
+            eqc = eqn;
+        }
     }
 }
 

@@ -342,3 +342,40 @@ def test_diffusion2d_rejects_bad_arguments(lib):
                                   ctypes.byref(odd)) == _lib.PS_ERR_ARG
     assert lib.ps_diffusion2d_run(A, B, C, 1.0, 1e-3, 7.0, 7.0, 8, 8, 3, f64, 0x40, None,
                                   ctypes.byref(odd)) == _lib.PS_ERR_ARG
+    dt = ctypes.c_double(0.0)
+    assert lib.ps_diffusion2d_stable_dt(None, C, 8, 8, 1.0, 1.0, 1.0, f64, A, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion2d_stable_dt(ctypes.byref(dt), C, 2, 8, 1.0, 1.0, 1.0, f64, A, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion2d_stable_dt(ctypes.byref(dt), None, 8, 8, 1.0, 1.0, 1.0, f64, A, None) == _lib.PS_ERR_ARG
+    assert lib.ps_diffusion2d_stable_dt(ctypes.byref(dt), C, 8, 8, float("nan"), 1.0, 1.0, f64, A,
+                                        None) == _lib.PS_ERR_ARG
+
+
+def test_launch_overrides_set_get_and_range(lib):
+    """The launch-shape overrides: every PS_OVERRIDE_* value reads back, out-of-range
+    keys and values are rejected, 0 restores the library's own choice."""
+    v = ctypes.c_int(-1)
+    for name, which in _lib.PS_OVERRIDE.items():
+        assert lib.ps_get_launch_override(which, ctypes.byref(v)) == _lib.PS_OK and v.value == 0
+        value = 1 if name in ("adj_plain", "f64_px2", "step_plain") else 17
+        assert lib.ps_set_launch_override(which, value) == _lib.PS_OK
+        assert lib.ps_get_launch_override(which, ctypes.byref(v)) == _lib.PS_OK and v.value == value
+        assert lib.ps_set_launch_override(which, 0) == _lib.PS_OK
+    assert lib.ps_set_launch_override(len(_lib.PS_OVERRIDE), 1) == _lib.PS_ERR_ARG
+    assert lib.ps_set_launch_override(-1, 1) == _lib.PS_ERR_ARG
+    assert lib.ps_set_launch_override(_lib.PS_OVERRIDE["adj_plain"], 2) == _lib.PS_ERR_ARG
+    assert lib.ps_set_launch_override(_lib.PS_OVERRIDE["kchunk"], 4097) == _lib.PS_ERR_ARG
+    assert lib.ps_set_launch_override(_lib.PS_OVERRIDE["kchunk"], -3) == _lib.PS_ERR_ARG
+    assert lib.ps_get_launch_override(0, None) == _lib.PS_ERR_ARG
+
+
+def test_dot_static_rejects_bad_arguments(lib):
+    """The no-allocation dot product: null pointers, element misalignment, n < 1 and
+    n beyond the static capacity are refused before any launch or device call."""
+    f64, f32 = _lib.PS_F64, _lib.PS_F32
+    assert lib.ps_dot_static(None, A, B, 8, f64, None) == _lib.PS_ERR_ARG
+    assert lib.ps_dot_static(C, None, B, 8, f64, None) == _lib.PS_ERR_ARG
+    assert lib.ps_dot_static(C, A, B, 8, 7, None) == _lib.PS_ERR_ARG
+    assert lib.ps_dot_static(C, A + 4, B, 8, f64, None) == _lib.PS_ERR_ALIGN
+    assert lib.ps_dot_static(C, A, B + 2, 8, f32, None) == _lib.PS_ERR_ALIGN
+    assert lib.ps_dot_static(C, A, B, 0, f64, None) == _lib.PS_ERR_ARG
+    assert lib.ps_dot_static(C, A, B, 4096 * 32768 + 1, f64, None) == _lib.PS_ERR_UNSUPPORTED

@@ -59,8 +59,8 @@ def test_adjoint_f32_grid_edges(shape):
 
 
 @pytest.mark.parametrize("kchunk", ["1", "2", "3", "7", "64"])
-def test_adjoint_f32_z_chunks(monkeypatch, kchunk):
-    monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
+def test_adjoint_f32_z_chunks(launch_override, kchunk):
+    launch_override(adj_kchunk=kchunk)
     run_case((132, 19, 29))
 
 
@@ -68,7 +68,7 @@ def test_adjoint_f32_unequal_spacings():
     run_case((136, 21, 18), inv_override=(7.0, 11.0, 5.0))
 
 
-def test_adjoint_f32_matches_plain_kernel(monkeypatch):
+def test_adjoint_f32_matches_plain_kernel(launch_override):
     """The staged kernel and the plain one-thread-per-column kernel agree to FP32
     rounding on a workload-shaped grid (Gaussian state, random Ci)."""
     nx, ny, nz = 200, 40, 33
@@ -77,7 +77,7 @@ def test_adjoint_f32_matches_plain_kernel(monkeypatch):
     args = [to_dev(f32(a), torch.float32) for a in (ybar, T, Ci)]
     out = []
     for plain in ("0", "1"):
-        monkeypatch.setenv("PS_ADJ_PLAIN", plain)
+        launch_override(adj_plain=plain)
         Tbar = torch.empty(T.shape, dtype=torch.float32, device="cuda")
         Cib = torch.zeros(T.shape, dtype=torch.float32, device="cuda")
         api.adjoint(Tbar, Cib, *args, lam, dt, inv)
@@ -104,10 +104,10 @@ def pair_fields(shape, seed=21, inv_override=None):
 
 @pytest.mark.parametrize("kchunk", ["0", "1", "2", "5"])
 @pytest.mark.parametrize("shape", SHAPES + [(136, 21, 18)])
-def test_adjoint2_is_two_single_steps(monkeypatch, kchunk, shape):
+def test_adjoint2_is_two_single_steps(launch_override, kchunk, shape):
     """ps_diffusion3d_adjoint2_ex gives bit for bit two one-step launches (states
     T_first then T_second), Tbar and Cibar, on every grid edge case and z-chunk."""
-    monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
+    launch_override(adj_kchunk=kchunk)
     inv_override = (7.0, 11.0, 5.0) if shape == (136, 21, 18) else None
     (yb, S1, S0, C, cib0), lam, dt, inv = pair_fields(shape, inv_override=inv_override)
     y1 = torch.empty_like(yb)

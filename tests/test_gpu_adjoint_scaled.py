@@ -70,11 +70,11 @@ def test_scaled_adjoint_accumulates_into_csbar():
 
 
 @pytest.mark.parametrize("kchunk", ["0", "1", "3", "40"])
-def test_scaled_adjoint_scale_growth(monkeypatch, kchunk):
+def test_scaled_adjoint_scale_growth(launch_override, kchunk):
     """ybar growing by 10^4 along z (with sign changes and exact zeros): the CTA's
     fixed-point scale grows in mid-march, so tiles and registers already held are
     shifted; every plane still matches the oracle at its own magnitude."""
-    monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
+    launch_override(adj_kchunk=kchunk)
     nx, ny, nz = 68, 21, 40
     T, Ci, lam, dt, inv = iso_fields(nx, ny, nz)
     ybar = inputs.random_field(T.shape, 5) * (10.0 ** (np.arange(nz) / 10.0))[:, None, None]

@@ -85,10 +85,10 @@ def test_fp32_deviation_matches_oracle(shape):
 
 @pytest.mark.parametrize("chunk", ["1", "3", "16", "300"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_row_chunks_do_not_change_results(monkeypatch, chunk, dtype):
+def test_row_chunks_do_not_change_results(launch_override, chunk, dtype):
     T0, Ci, dt, inv = fields2d(130, 77, gaussian=False)
     base = gpu_run2d(T0, Ci, dt, inv, 4, dtype=dtype)
-    monkeypatch.setenv("PS_CHUNK2D", chunk)
+    launch_override(chunk2d=chunk)
     assert np.array_equal(gpu_run2d(T0, Ci, dt, inv, 4, dtype=dtype), base)
 
 
@@ -115,3 +115,19 @@ def test_step_writes_interior_only():
     ref = np.full_like(T0, -5.0)
     oracle.step2d(ref, T0, Ci, 1.0, dt, *inv)
     assert rel_linf(out[inner], ref[inner]) <= 1e-15
+
+
+@pytest.mark.parametrize("shape,lengths,dtype", [((130, 70), (1.0, 1.0), torch.float64),
+                                                 ((33, 170), (2.0, 0.5), torch.float64),
+                                                 ((64, 64), (1.0, 1.0), torch.float32)])
+def test_stable_dt2d_matches_oracle(shape, lengths, dtype):
+    """ps_diffusion2d_stable_dt (maximum on the GPU, dt formed in the library) equals
+    the oracle's 2-D dt bit for bit; FP32 fields reduce their FP32 values."""
+    nx, ny = shape
+    Ci = inputs.ci_random(nx, ny, 1, seed=3)[0]
+    if dtype == torch.float32:
+        Ci = Ci.astype(np.float32).astype(np.float64)
+    lam = 0.9
+    dx, dy = lengths[0] / (nx - 1), lengths[1] / (ny - 1)
+    ref = oracle.stable_dt2d(dx, dy, lam, oracle.maximum(Ci))
+    assert api.stable_dt2d(to_dev(Ci, dtype), lam, lengths) == ref

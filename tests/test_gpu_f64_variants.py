@@ -1,16 +1,12 @@
-"""The FP64 step's alternative forms selected by PS_F64_VARIANT (measurement
-knob): "px2" (pre-scaled step at two nodes per thread instead of four) reorganises
-the default kernel's per-node arithmetic and must give its result bit for bit;
-"umul" (the step on Ci as given with the coefficient product by a 64 x 64-bit high
-multiply and one DFMA) is another rounding of the same step and must meet the FP64
-tolerance against the oracle; "by16" is the umul form in 64 x 16 tiles and must
-equal umul bit for bit."""
+"""The pre-scaled FP64 step at two nodes per thread (launch override ``f64_px2``,
+the kernel the library takes when rows do not allow 32-byte accesses) reorganises
+the default four-per-thread kernel's per-node arithmetic and must give its result
+bit for bit."""
 import numpy as np
 import pytest
 import torch
 
-import oracle
-from gpu_helpers import problem, rel_linf, to_dev, to_host
+from gpu_helpers import problem, to_dev, to_host
 from paper_2211_15634_gb300 import api
 
 pytestmark = [pytest.mark.gpu,
@@ -19,12 +15,10 @@ pytestmark = [pytest.mark.gpu,
 SHAPES = [(64, 9, 7), (132, 21, 17), (68, 40, 11), (256, 35, 19)]
 
 
-def run(T0, Ci, lam, dt, inv, nt, scaled):
+def run(T0, Ci, lam, dt, inv, nt, graph=False):
     T = to_dev(T0)
-    C = to_dev(Ci)
-    if scaled:
-        C = api.scale_ci(C, lam, dt, inv)
-    return to_host(api.run(T, torch.empty_like(T), C, lam, dt, inv, nt, ci_scaled=scaled))
+    C = api.scale_ci(to_dev(Ci), lam, dt, inv)
+    return to_host(api.run(T, torch.empty_like(T), C, lam, dt, inv, nt, ci_scaled=True, graph=graph))
 
 
 def iso(shape):
@@ -35,31 +29,36 @@ def iso(shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("base_variant,variant,scaled", [(None, "px2", True), ("umul", "by16", False)])
-def test_reorganised_variants_are_bitwise_equal(monkeypatch, shape, base_variant, variant, scaled):
+def test_two_per_thread_is_bitwise_equal(launch_override, shape):
     T0, Ci, lam, dt, inv = iso(shape)
-    if base_variant:
-        monkeypatch.setenv("PS_F64_VARIANT", base_variant)
-    base = run(T0, Ci, lam, dt, inv, 6, scaled)
-    monkeypatch.setenv("PS_F64_VARIANT", variant)
-    assert np.array_equal(run(T0, Ci, lam, dt, inv, 6, scaled), base)
+    base = run(T0, Ci, lam, dt, inv, 6)
+    launch_override(f64_px2=1)
+    assert np.array_equal(run(T0, Ci, lam, dt, inv, 6), base)
     assert api.device_error() == 0
 
 
-@pytest.mark.parametrize("shape", SHAPES)
-def test_umul_variant_meets_fp64_tolerance(monkeypatch, shape):
-    T0, Ci, lam, dt, inv = iso(shape)
-    monkeypatch.setenv("PS_F64_VARIANT", "umul")
-    got = run(T0, Ci, lam, dt, inv, 6, False)
-    assert rel_linf(got, oracle.run(T0, Ci, lam, dt, *inv, 6)) <= 1e-12
-    assert api.device_error() == 0
-
-
-def test_px2_variant_names_its_kernel(monkeypatch):
+def test_px2_override_names_its_kernel(launch_override):
     T = torch.zeros((8, 8, 64), dtype=torch.float64, device="cuda")
     inv = (63.0,) * 3
     assert api.step_kernel_name(T, T.clone(), T.clone(), 1.0, 1e-5, inv, ci_scaled=True) == \
         "k_zmarch<F64_SCALED4>"
-    monkeypatch.setenv("PS_F64_VARIANT", "px2")
+    launch_override(f64_px2=1)
     assert api.step_kernel_name(T, T.clone(), T.clone(), 1.0, 1e-5, inv, ci_scaled=True) == \
         "k_zmarch<F64_SCALED>"
+
+
+def test_graph_replay_across_an_override_change(launch_override):
+    """The same buffers run as a cached graph before and after the override changes
+    (the change empties the graph cache, so the second run captures the other kernel):
+    both equal the plain-stream run bit for bit."""
+    T0, Ci, lam, dt, inv = iso((132, 21, 17))
+    T, C = to_dev(T0), api.scale_ci(to_dev(Ci), lam, dt, inv)
+    T2 = torch.empty_like(T)
+    ref = run(T0, Ci, lam, dt, inv, 5)
+    outs = []
+    for px2 in (0, 1):
+        launch_override(f64_px2=px2)
+        T.copy_(to_dev(T0))
+        outs.append(to_host(api.run(T, T2, C, lam, dt, inv, 5, ci_scaled=True, graph=True)))
+    assert np.array_equal(outs[0], ref) and np.array_equal(outs[1], ref)
+    api.clear_graph_cache()

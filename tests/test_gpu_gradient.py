@@ -66,6 +66,31 @@ def test_autograd_function_matches_loss_and_grad():
     assert rel_linf(to_host(gCi), to_host(dCi)) <= 1e-13
 
 
+@pytest.mark.parametrize("every", [1, 4])
+def test_kept_output_does_not_hold_the_state_block(every):
+    """T(nt) from Diffusion3DFn owns its storage: after backward, keeping the output
+    holds one field, not the block of checkpoints it was stepped in."""
+    nx, ny, nz, nt = 40, 32, 36, 16
+    T0, Ci, Tobs, lam, dt, inv = inverse_problem(nx, ny, nz, nt)
+    T0d = to_dev(T0).requires_grad_(True)
+    Cid = to_dev(Ci).requires_grad_(True)
+    Tobsd = to_dev(Tobs)
+    field = T0.nbytes
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    out = ag.Diffusion3DFn.apply(T0d, Cid, lam, dt, inv, nt, every)
+    L = 0.5 * ((out - Tobsd) ** 2).sum()
+    gT0, gCi = torch.autograd.grad(L, (T0d, Cid))
+    del L, gT0, gCi
+    torch.cuda.synchronize()
+    held = torch.cuda.memory_allocated() - before
+    assert out.untyped_storage().nbytes() == field
+    assert held <= field + 4096, f"{held} bytes held with the output, one field is {field}"
+    del out
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() - before <= 4096
+
+
 @pytest.mark.parametrize("every", [1, 2, 5, 13])
 def test_checkpoint_interval_does_not_change_gradient(every):
     """Recomputed states are bit-identical to the forward ones, so any interval
@@ -104,11 +129,11 @@ def test_gradient_central_differences_16():
 
 
 @pytest.mark.parametrize("kchunk", ["0", "3", "40"])
-def test_adjoint_fixed_point_scale_growth(monkeypatch, kchunk):
+def test_adjoint_fixed_point_scale_growth(launch_override, kchunk):
     """ybar growing by 10^4 along z (with sign changes and exact zeros) makes the
     FP64 adjoint's per-CTA fixed-point scale grow in the middle of its z-march,
     so tiles already stored must be rescaled; results still match the oracle."""
-    monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
+    launch_override(adj_kchunk=kchunk)
     nx, ny, nz = 68, 21, 40
     T = 1.7 + inputs.random_field((nz, ny, nx), 3, 0.0, 1.0)
     Ci = inputs.ci_random(nx, ny, nz)
@@ -131,8 +156,8 @@ def test_adjoint_fixed_point_scale_growth(monkeypatch, kchunk):
 
 
 @pytest.mark.parametrize("kchunk", ["1", "2", "5"])
-def test_adjoint_short_z_chunks(monkeypatch, kchunk):
-    monkeypatch.setenv("PS_ADJ_KCHUNK", kchunk)
+def test_adjoint_short_z_chunks(launch_override, kchunk):
+    launch_override(adj_kchunk=kchunk)
     nx, ny, nz = 132, 19, 13
     T = 1.7 + inputs.random_field((nz, ny, nx), 3, 0.0, 1.0)
     Ci = inputs.ci_random(nx, ny, nz)

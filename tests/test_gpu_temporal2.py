@@ -66,8 +66,8 @@ def test_fp32_pairs_equal_single_steps(shape, nt):
 
 
 @pytest.mark.parametrize("kchunk", ["1", "2", "5", "40"])
-def test_pairs_short_and_long_z_chunks(monkeypatch, kchunk):
-    monkeypatch.setenv("PS_KCHUNK2", kchunk)
+def test_pairs_short_and_long_z_chunks(launch_override, kchunk):
+    launch_override(kchunk2=kchunk)
     T0, Ci, lam, dt, inv = iso_problem(136, 27, 22, gaussian=True)
     one = run64(T0, Ci, lam, dt, inv, 6)
     assert np.array_equal(one, run64(T0, Ci, lam, dt, inv, 6, temporal2=True))
@@ -104,4 +104,4 @@ def test_pairs_fall_back_on_odd_nx_and_reject_other_modes():
     D = to_dev(T0 - 1.7, torch.float32)
     with pytest.raises(_lib.PsError, match="TEMPORAL2"):
         api.run(D, torch.empty_like(D), to_dev(Ci, torch.float32), lam, dt, inv, 4,
-                comp=torch.zeros_like(D), temporal2=True)
+                comp=api.compensation_fields(D), temporal2=True)

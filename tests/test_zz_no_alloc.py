@@ -35,6 +35,24 @@ def test_dot_static_matches_dot(dtype, n):
     A, B = seeded(n, dtype, 11), seeded(n, dtype, 12)
     ref = float(api.dot(A, B))
     scale = float(api.dot(A.abs(), B.abs()))
+    check_twice(lib, A, B, n, code, ref, scale)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_dot_static_takes_element_aligned_views(dtype):
+    """Views that start one element into a buffer (8 or 4 bytes past a 16-byte
+    boundary) are accepted: the kernel reads one element at a time."""
+    lib = _lib.load()
+    code = _lib.PS_F64 if dtype == torch.float64 else _lib.PS_F32
+    n = 70001
+    A, B = seeded(n + 1, dtype, 21)[1:], seeded(n + 3, dtype, 22)[3:]
+    assert A.data_ptr() % 16 != 0 and B.data_ptr() % 16 != 0
+    ref = float(api.dot(A.clone(), B.clone()))
+    scale = float(api.dot(A.abs(), B.abs()))
+    check_twice(lib, A, B, n, code, ref, scale)
+
+
+def check_twice(lib, A, B, n, code, ref, scale):
     stream = torch.cuda.current_stream().cuda_stream
     out = torch.empty((), dtype=torch.float64, device="cuda")
     for _ in range(2):
