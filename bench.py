@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--no-secondary", action="store_true", help="skip FP32 / gradient / batch lines")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
-    p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint_fx", "adjoint2", "batch", "step2d"],
+    p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint2", "batch", "step2d"],
                    default=None,
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON); "
                         "step2d on a --size^2 grid")
@@ -99,15 +99,6 @@ def run_kernel_loop(args):
                 api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
         name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled,
                                     temporal2=args.temporal2)
-    elif args.kernel_loop == "adjoint_fx":
-        # FP64: the fixed-point reverse sweep's transposed step on the pre-scaled coefficient
-        Cs = api.scale_ci(C, 1.0, dt, inv)
-        sw = api.FixedPointSweep(T)
-        sw.start(T2 - T.mean())
-        Cib = torch.zeros_like(T)
-        for _ in range(args.reps):
-            sw.step(Cib, T, Cs)
-        name = "adjoint_fx (fixed-point sweep)"
     elif args.kernel_loop == "adjoint2":
         # FP32: two transposed steps per pass (states T and T2)
         if args.dtype != "f32":
@@ -701,17 +692,6 @@ def secondary_metrics(torch, api, ag, inputs, log):
         t_adj = timed(adj10, reps=3) / 10
         out[f"adjoint_256_{name}_ms"] = round(1e3 * t_adj, 4)
         out[f"adjoint_256_{name}_gbs"] = round(6 * n ** 3 * Td.element_size() / t_adj / 1e9, 1)
-        if scaled:  # the fixed-point sweep's transposed step (the gradient's default on FP64)
-            sw = api.FixedPointSweep(Td)
-            sw.start(ybar)
-
-            def fx10():
-                for _ in range(10):
-                    sw.step(Cib, Td, Cf)
-            t_fx = timed(fx10, reps=3) / 10
-            out[f"adjoint_fx_256_{name}_ms"] = round(1e3 * t_fx, 4)
-            out[f"adjoint_fx_256_{name}_gbs"] = round(6 * n ** 3 * 8 / t_fx / 1e9, 1)
-            del sw
         for tag, every in (("sqrt_nt", ag.default_every(nt)), ("all_states", 1)):
             t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt, every=every), reps=2)
             out[f"grad_over_fwd_256_{name}_{tag}"] = round(t_grad / t_fwd, 3)

@@ -283,43 +283,6 @@ int ps_diffusion3d_adjoint2_ex(void *Tbar, void *Cibar, const void *ybar, const 
                                unsigned flags, void *stream);
 
 /* ---------------------------------------------------------------------
- * Reverse sweep with the adjoint state in fixed point (FP64, pre-scaled
- * coefficient Cs of ps_diffusion3d_scale_ci, equal spacings; derived from
- * Fig. 1's step, no paper line).  The transposed step of
- * ps_diffusion3d_adjoint_ex(PS_RUN_CI_SCALED) with ybar held as an int64 field
- * Y, ybar = Y * 2^sigma, sigma one scale for the whole grid kept in a small
- * device state:
- *   w[q] = Cs[q]*Y[q] rounded toward zero at interior q (0 elsewhere),
- *   Y'[p] = Y[p] + L(w)[p] at every node (exact integer sums),
- *   Csbar[q] += (Y[q]*2^sigma) * L(T)[q] at interior q (FP64, as the FP64 call),
- * with L(A) = (sum of the six neighbours) - 6 A.  The largest |Y| carries 50-60
- * significant bits: each step records max|Y'| and the next one rescales by a
- * power of two when it leaves [2^50, 2^60).  Needs |Cs| < 1/4 at every interior
- * node (a stable step has Cs <= 1/6.1): otherwise, or on a non-finite input,
- * the sweep is marked bad and ps_adjoint_fx_end returns NaN everywhere.
- * Use: ps_adjoint_fx_begin (Y from ybar_nt, state initialised), then
- * ps_diffusion3d_adjoint_fx with step = 0, 1, 2, ... (each reads the Y the
- * previous one wrote), then ps_adjoint_fx_end with step = the number of
- * transposed steps taken.  `state` is a caller-owned device buffer of
- * ps_adjoint_fx_state_bytes(); one sweep at a time per state buffer.  Y fields
- * are int64, 16-byte aligned, x fastest; all calls asynchronous on `stream`.
- * ------------------------------------------------------------------- */
-size_t ps_adjoint_fx_state_bytes(void);
-/* Y = ybar * 2^-sigma rounded to nearest with max|Y| in [2^58, 2^59]; starts the
- * state.  n values; Y must not overlap ybar. */
-int ps_adjoint_fx_begin(long long *Y, const double *ybar, int64_t n, void *state, void *stream);
-/* One transposed step (the step-th of the sweep): Yout from Yin (Yout at every
- * node), Csbar accumulated at interior nodes; T = the state the forward step
- * read.  nx*8 a multiple of 16 (else PS_ERR_UNSUPPORTED).  Yout must not
- * overlap any input; Csbar not Yin, T or Cs. */
-int ps_diffusion3d_adjoint_fx(long long *Yout, double *Csbar, const long long *Yin, const double *T,
-                              const double *Cs, int64_t nx, int64_t ny, int64_t nz, void *state, int step,
-                              void *stream);
-/* ybar = Y * 2^sigma (FP64, one rounding) after `step` transposed steps. */
-int ps_adjoint_fx_end(double *ybar, const long long *Y, int64_t n, const void *state, int step,
-                      void *stream);
-
-/* ---------------------------------------------------------------------
  * Reductions in FP64 (deterministic: a fixed partition and a fixed
  * summation order, independent of timing).  A, B are device arrays of n
  * elements of `dtype`; out_dev is a device double; workspace is a device

@@ -82,10 +82,6 @@ SIGNATURES = {
     "ps_diffusion3d_adjoint": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I, _P]),
     "ps_diffusion3d_adjoint_ex": (_I, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
                                        _U, _P]),
-    "ps_adjoint_fx_state_bytes": (_SZ, []),
-    "ps_adjoint_fx_begin": (_I, [_P, _P, _I64, _P, _P]),
-    "ps_diffusion3d_adjoint_fx": (_I, [_P, _P, _P, _P, _P, _I64, _I64, _I64, _P, _I, _P]),
-    "ps_adjoint_fx_end": (_I, [_P, _P, _I64, _P, _I, _P]),
     "ps_maximum_async": (_I, [_P, _P, _I64, _I, _P, _P]),
     "ps_maximum": (_I, [ctypes.POINTER(_D), _P, _I64, _I, _P, _P]),
     "ps_diffusion3d_stable_dt": (_I, [ctypes.POINTER(_D), _P, _I64, _I64, _I64, _D, _D, _D, _D, _I,

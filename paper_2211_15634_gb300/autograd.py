@@ -13,9 +13,7 @@ maximum(Ci)).  Memory: about ``nt/every + every + 2`` fields.
 
 On FP64 grids with equal spacings every kernel runs on the pre-scaled
 coefficient Cs = dt*lam*_dx^2*Ci (one FP64 multiply-add per node forward);
-the sweep then accumulates dL/dCs and returns dL/dCi = dt*lam*_dx^2 * dL/dCs,
-and carries dL/dT between its steps as an int64 field at one scale
-(``api.FixedPointSweep``: two FP64 instructions per node instead of 3.3).
+the sweep then accumulates dL/dCs and returns dL/dCi = dt*lam*_dx^2 * dL/dCs.
 With ``pairs=True`` (FP32 grids) the reverse sweep takes the transposed steps
 two at a time (``api.adjoint2``: one pass over HBM per pair, bit for bit two
 single steps; measured no faster than single steps on GB300, so off by default).
@@ -81,26 +79,14 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
     return cur, ckpts
 
 
-def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None,
-                          fixed_point=None):
+def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None):
     """Reverse sweep; returns (dL/dT0, dL/dCi).  ``pairs``: take the transposed
-    steps two per launch where ``api.adjoint2`` applies (default off).
-    ``fixed_point`` (FP64 on the pre-scaled coefficient; default on where the grid
-    allows it): dL/dT travels between the steps as an int64 field at one scale
-    (``api.FixedPointSweep``), which needs fewer FP64 instructions per node."""
+    steps two per launch where ``api.adjoint2`` applies (default off)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     pairs = bool(pairs) and not scaled and api.adjoint2_supported(ybar_nt)
-    if fixed_point is None:
-        fixed_point = True
-    fx = api.FixedPointSweep(ybar_nt) if (scaled and fixed_point and
-                                          api.FixedPointSweep.supported(ybar_nt)) else None
+    ybar = ybar_nt.contiguous().clone()
+    tbar = torch.empty_like(ybar)
     cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
-    if fx is not None:
-        fx.start(ybar_nt.contiguous())
-        ybar = tbar = None
-    else:
-        ybar = ybar_nt.contiguous().clone()
-        tbar = torch.empty_like(ybar)
     # grids for the recomputed states of one segment, with the boundary of T0
     seg = api.StateBlock(ckpts[0], max(0, min(every, nt) - 1))
     nseg = len(ckpts)
@@ -112,10 +98,6 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
         states = [ckpts[s]] + seg.grids[:t1 - t0 - 1]
         t = t1 - 1
         while t >= t0:
-            if fx is not None:
-                fx.step(cibar, states[t - t0], C)
-                t -= 1
-                continue
             if pairs and t - 1 >= t0:  # steps t and t-1 in one pass
                 api.adjoint2(tbar, cibar, ybar, states[t - t0], states[t - 1 - t0], C, lam, dt, inv)
                 t -= 2
@@ -123,8 +105,6 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
                 api.adjoint(tbar, cibar, ybar, states[t - t0], C, lam, dt, inv, ci_scaled=scaled)
                 t -= 1
             ybar, tbar = tbar, ybar
-    if fx is not None:
-        ybar = fx.finish()
     if scaled:  # dL/dCi = dt*lam*_dx^2 * dL/dCs
         api.scale_ci(cibar, lam, dt, inv, out=cibar)
     return ybar, cibar
@@ -160,15 +140,15 @@ class Diffusion3DFn(torch.autograd.Function):
         return dT0, dCi, None, None, None, None, None
 
 
-def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None, fixed_point=None):
+def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None):
     """L = 1/2||T(nt) - Tobs||^2 (FP64 on the GPU) and (dL/dT0, dL/dCi); ``every``
-    as for :class:`Diffusion3DFn` (None: every state kept when it fits); ``pairs``,
-    ``fixed_point`` as for :func:`backward_checkpointed`."""
+    as for :class:`Diffusion3DFn` (None: every state kept when it fits); ``pairs``
+    as for :func:`backward_checkpointed`."""
     every = auto_every(T0, int(nt)) if every is None else int(every)
     inv = tuple(inv_spacing)
     coef = coefficient(Ci.contiguous(), lam, dt, inv)
     out, ckpts = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef)
     resid = torch.empty_like(out)
     L = api.half_sq_dist(out, Tobs, residual=resid)
-    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs, fixed_point)
+    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs)
     return L, dT0, dCi

@@ -325,7 +325,7 @@ int ps_device_error(unsigned *out_host, int clear) {
     *out_host = zmarch_device_error(clear != 0) | adjoint_device_error(clear != 0) |
                 adjoint_scaled_device_error(clear != 0) | zmarch2_device_error(clear != 0) |
                 adjoint_f32_device_error(clear != 0) | batch_device_error(clear != 0) |
-                batch_zmarch_device_error(clear != 0) | adjoint_fx_device_error(clear != 0);
+                batch_zmarch_device_error(clear != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ps_device_error");
     return PS_OK;
@@ -616,62 +616,6 @@ int ps_diffusion3d_adjoint_ex(void *Tbar, void *Cibar, const void *ybar, const v
         e = launch_adjoint_f32((float *)Tbar, (float *)Cibar, (const float *)ybar, (const float *)T,
                                (const float *)Ci, c, g, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_adjoint");
-    return PS_OK;
-}
-
-size_t ps_adjoint_fx_state_bytes(void) { return kFxStateBytes; }
-
-int ps_adjoint_fx_begin(long long *Y, const double *ybar, int64_t n, void *state, void *stream) {
-    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
-    PS_TRY(check_ptr(Y, "Y"));
-    PS_TRY(check_ptr(ybar, "ybar"));
-    PS_TRY(check_ptr(state, "state"));
-    if (overlap(Y, ybar, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "Y overlaps ybar");
-    if (overlap2(state, kFxStateBytes, Y, (size_t)n * 8) || overlap2(state, kFxStateBytes, ybar, (size_t)n * 8))
-        return fail(PS_ERR_ALIAS, "state overlaps Y or ybar");
-    cudaError_t e = launch_adjoint_fx_begin(Y, ybar, n, state, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "ps_adjoint_fx_begin");
-    return PS_OK;
-}
-
-int ps_diffusion3d_adjoint_fx(long long *Yout, double *Csbar, const long long *Yin, const double *T,
-                              const double *Cs, int64_t nx, int64_t ny, int64_t nz, void *state, int step,
-                              void *stream) {
-    PS_TRY(check_grid(nx, ny, nz));
-    PS_TRY(check_ptr(Yout, "Yout"));
-    PS_TRY(check_ptr(Csbar, "Csbar"));
-    PS_TRY(check_ptr(Yin, "Yin"));
-    PS_TRY(check_ptr(T, "T"));
-    PS_TRY(check_ptr(Cs, "Cs"));
-    PS_TRY(check_ptr(state, "state"));
-    if (step < 0) return fail(PS_ERR_ARG, "step = %d < 0", step);
-    const size_t bytes = (size_t)(nx * ny * nz) * 8;
-    if (overlap(Yout, Yin, bytes) || overlap(Yout, T, bytes) || overlap(Yout, Cs, bytes) ||
-        overlap(Yout, Csbar, bytes))
-        return fail(PS_ERR_ALIAS, "Yout overlaps an input");
-    if (overlap(Csbar, Yin, bytes) || overlap(Csbar, T, bytes) || overlap(Csbar, Cs, bytes))
-        return fail(PS_ERR_ALIAS, "Csbar overlaps an input");
-    const void *fields[5] = {Yout, Csbar, Yin, T, Cs};
-    for (const void *f : fields)
-        if (overlap2(state, kFxStateBytes, f, bytes)) return fail(PS_ERR_ALIAS, "state overlaps a field");
-    const Grid3 g{nx, ny, nz};
-    if (!adjoint_fx_supported(g, fields, 5))
-        return fail(PS_ERR_UNSUPPORTED, "the fixed-point sweep needs nx*8 a multiple of 16 and a CUDA driver");
-    cudaError_t e = launch_adjoint_fx(Yout, Csbar, Yin, T, Cs, g, state, step, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_adjoint_fx");
-    return PS_OK;
-}
-
-int ps_adjoint_fx_end(double *ybar, const long long *Y, int64_t n, const void *state, int step,
-                      void *stream) {
-    if (n < 1) return fail(PS_ERR_ARG, "n = %lld < 1", (long long)n);
-    PS_TRY(check_ptr(Y, "Y"));
-    PS_TRY(check_ptr(ybar, "ybar"));
-    PS_TRY(check_ptr(state, "state"));
-    if (step < 0) return fail(PS_ERR_ARG, "step = %d < 0", step);
-    if (overlap(Y, ybar, (size_t)n * 8)) return fail(PS_ERR_ALIAS, "ybar overlaps Y");
-    cudaError_t e = launch_adjoint_fx_end(ybar, Y, n, state, step, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "ps_adjoint_fx_end");
     return PS_OK;
 }
 

@@ -104,17 +104,6 @@ cudaError_t launch_adjoint_f64_scaled(double *Tbar, double *Csbar, const double 
 cudaError_t launch_adjoint_f32(float *Tbar, float *Cibar, const float *ybar, const float *T,
                                const float *Ci, StepCoef c, Grid3 g, cudaStream_t s);
 
-// ---- reverse sweep with the adjoint state in fixed point (adjoint_fx.cu) ----
-constexpr size_t kFxStateBytes = 48;  // three slots of {max|Y|, sigma, bad}
-bool adjoint_fx_supported(Grid3 g, const void *const *ptrs, int nptr);
-cudaError_t launch_adjoint_fx_begin(long long *Y, const double *ybar, int64_t n, void *state,
-                                    cudaStream_t s);
-cudaError_t launch_adjoint_fx(long long *Yout, double *Csbar, const long long *Yin, const double *T,
-                              const double *Cs, Grid3 g, void *state, int step, cudaStream_t s);
-cudaError_t launch_adjoint_fx_end(double *ybar, const long long *Y, int64_t n, const void *state, int step,
-                                  cudaStream_t s);
-unsigned adjoint_fx_device_error(bool clear);
-
 // ---- reductions (reduce.cu) ----
 constexpr int kReduceBlocks = 1024;           // fixed partition => deterministic sums
 constexpr size_t kWorkspaceBytes = 16384;     // >= kReduceBlocks doubles + one key
