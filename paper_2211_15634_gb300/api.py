@@ -233,53 +233,6 @@ def adjoint(Tbar, Cibar, ybar, T, Ci, lam: float, dt: float, inv_spacing, *,
         _lib.PS_RUN_CI_SCALED if ci_scaled else 0, _stream(T)))
 
 
-class FixedPointSweep:
-    """Reverse sweep of the pre-scaled FP64 step with dL/dT held as an int64 field
-    (``ps_adjoint_fx_*``): ``Y = ybar * 2^-sigma`` with one scale for the grid, kept in a
-    small device state.  ``start(ybar)`` converts dL/dT(nt); each :meth:`step` applies
-    one transposed step (Csbar accumulates dL/dCs at interior nodes); :meth:`finish`
-    returns dL/dT as an FP64 field.  Two int64 work fields and the state buffer are
-    allocated once per sweep object."""
-
-    def __init__(self, like: torch.Tensor):
-        if like.dtype != torch.float64:
-            raise TypeError("the fixed-point sweep is FP64")
-        self.shape = tuple(like.shape)
-        self.Y = torch.empty(self.shape, dtype=torch.int64, device=like.device)
-        self.Y2 = torch.empty_like(self.Y)
-        self.state = torch.empty(_lib.load().ps_adjoint_fx_state_bytes(), dtype=torch.uint8,
-                                 device=like.device)
-        self.steps = 0
-
-    @staticmethod
-    def supported(T: torch.Tensor) -> bool:
-        """Whether fields shaped like ``T`` can take the sweep (TMA rows: nx*8 a multiple of 16)."""
-        return T.dtype == torch.float64 and T.dim() == 3 and (T.shape[2] * 8) % 16 == 0
-
-    def start(self, ybar: torch.Tensor) -> None:
-        _same(ybar, self.Y)
-        check(_lib.load().ps_adjoint_fx_begin(self.Y.data_ptr(), _field(ybar, "ybar", PS_F64), ybar.numel(),
-                                              self.state.data_ptr(), _stream(ybar)))
-        self.steps = 0
-
-    def step(self, Csbar: torch.Tensor, T: torch.Tensor, Cs: torch.Tensor) -> None:
-        """One transposed step with the state T the forward step read."""
-        nx, ny, nz = _grid(T)
-        check(_lib.load().ps_diffusion3d_adjoint_fx(
-            self.Y2.data_ptr(), _field(Csbar, "Csbar", PS_F64), self.Y.data_ptr(), _field(T, "T", PS_F64),
-            _field(Cs, "Cs", PS_F64), nx, ny, nz, self.state.data_ptr(), self.steps, _stream(T)))
-        self.Y, self.Y2 = self.Y2, self.Y
-        self.steps += 1
-
-    def finish(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """dL/dT after the steps taken, as an FP64 field."""
-        if out is None:
-            out = torch.empty(self.shape, dtype=torch.float64, device=self.Y.device)
-        check(_lib.load().ps_adjoint_fx_end(_field(out, "ybar", PS_F64), self.Y.data_ptr(), out.numel(),
-                                            self.state.data_ptr(), self.steps, _stream(out)))
-        return out
-
-
 def _grid2d(t: torch.Tensor):
     if t.dim() != 2:
         raise ValueError("2-D fields must have shape (ny, nx)")
@@ -579,13 +532,45 @@ class Batch:
     whose ``Ci`` holds the pre-scaled ``dt*lam*_dx^2*Ci`` of :func:`scale_ci`
     (equal spacings; z-march).  ``temporal2``: :meth:`run` steps in fused pairs
     (temporal blocking of depth 2; z-march, FP32 or FP64 with ``ci_scaled``).
-    The chosen kernel is ``self.kernel``.
+    ``prescale`` (default on): FP64 problems given with Ci as it is are stepped on
+    the pre-scaled coefficient when every problem can take it (the z-march, equal
+    spacings, dt*lam*_dx^2 > 0): the batch keeps its own copy Cs = dt*lam*_dx^2*Ci
+    per problem, made at construction (``ps_diffusion3d_scale_ci``; a later change
+    of Ci needs a new Batch), and each step costs one FP64 multiply-add per node,
+    the arithmetic of :func:`solve` - a problem then equals its single run on that
+    Cs bit for bit.  ``prescale=False`` keeps the kernel on Ci as given (two FP64
+    products per node).  The chosen kernel is ``self.kernel``; ``self.prescaled``
+    tells whether the batch steps on its own Cs.
     """
 
     KERNELS = {"auto": 0, "column": _lib.PS_BATCH_COLUMN, "zmarch": _lib.PS_BATCH_ZMARCH}
 
+    @staticmethod
+    def _prescalable(problems, kernel: str) -> bool:
+        """FP64 problems that can all take the pre-scaled z-march."""
+        if kernel == "column":
+            return False
+        for p in problems:
+            T, inv = p["T"], p["inv_spacing"]
+            if T.dtype != torch.float64 or not (inv[0] == inv[1] == inv[2]):
+                return False
+            if (_pitch(T, "T") * 8) % 16 != 0 or not (p["dt"] * p["lam"] * inv[0] * inv[0] > 0.0):
+                return False
+        return True
+
+    @staticmethod
+    def _scaled_copy(p) -> torch.Tensor:
+        """Cs = dt*lam*_dx^2*Ci in a field of Ci's layout (the pitched block scaled whole)."""
+        Ci = p["Ci"]
+        nz, ny, nx = Ci.shape
+        pitch = _pitch(Ci, "Ci")
+        Cs = torch.empty((nz, ny, pitch), dtype=Ci.dtype, device=Ci.device)
+        block = Ci.as_strided((nz, ny, pitch), (ny * pitch, pitch, 1)) if pitch != nx else Ci
+        scale_ci(block, p["lam"], p["dt"], p["inv_spacing"], out=Cs)
+        return Cs[:, :, :nx] if pitch != nx else Cs
+
     def __init__(self, problems, tile=(0, 0, 0), kernel: str = "auto", ci_scaled: bool = False,
-                 temporal2: bool = False):
+                 temporal2: bool = False, prescale: bool = True):
         if not problems:
             raise ValueError("empty batch")
         if kernel not in self.KERNELS:
@@ -593,6 +578,10 @@ class Batch:
         lib = _lib.load()
         self.code = _code(problems[0]["T"])
         self.device = problems[0]["T"].device
+        self.prescaled = bool(prescale and not ci_scaled and self._prescalable(problems, kernel))
+        if self.prescaled:
+            problems = [dict(p, Ci=self._scaled_copy(p)) for p in problems]
+            ci_scaled = True
         self.problems = problems
         arr = (_lib.PsProblem * len(problems))()
         for q, p in enumerate(problems):

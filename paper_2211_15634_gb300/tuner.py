@@ -93,7 +93,16 @@ def _key(device, dtype, cls, kernel="column", ci_scaled=False) -> str:
 
 def batch_kernel(problems, kernel: str = "auto", ci_scaled: bool = False) -> str:
     """The kernel ("column" or "zmarch") a Batch of these problems would run."""
-    return api.Batch(problems, kernel=kernel, ci_scaled=ci_scaled).kernel
+    return api.Batch(problems, kernel=kernel, ci_scaled=ci_scaled, prescale=False).kernel
+
+
+def prescaled(problems, kernel: str = "auto", ci_scaled: bool = False):
+    """(problems, ci_scaled) as an api.Batch would step them: FP64 problems on Ci as
+    given get their pre-scaled copy once here (see api.Batch's ``prescale``), so that
+    the candidates timed below do not each make their own."""
+    if not ci_scaled and api.Batch._prescalable(problems, kernel):
+        return [dict(p, Ci=api.Batch._scaled_copy(p)) for p in problems], True
+    return problems, ci_scaled
 
 
 def time_batch_step(problems, cand: Tile, reps: int = 5, warmup: int = 2, kernel: str = "auto",
@@ -141,6 +150,7 @@ def tune(problems, candidates: Optional[Sequence[Tile]] = None, reps: int = 5,
     """
     if not problems:
         return {}
+    problems, ci_scaled = prescaled(problems, kernel, ci_scaled)
     dev = problems[0]["T"].device
     dtype = problems[0]["T"].dtype
     kern = batch_kernel(problems, kernel, ci_scaled)
@@ -201,7 +211,10 @@ def tune_depth(problems, reps: int = 5, use_cache: bool = True, kernel: str = "a
                ci_scaled: bool = False, **kw) -> int:
     """Temporal-block depth (1 or 2 steps per pass) for the whole batch, timed with
     each class's tuned z-chunk (cached)."""
-    if not problems or not pairs_possible(problems, kernel, ci_scaled):
+    if not problems:
+        return 1
+    problems, ci_scaled = prescaled(problems, kernel, ci_scaled)
+    if not pairs_possible(problems, kernel, ci_scaled):
         return 1
     dev = problems[0]["T"].device
     dtype = problems[0]["T"].dtype
@@ -223,6 +236,7 @@ def tune_depth(problems, reps: int = 5, use_cache: bool = True, kernel: str = "a
 def tuned_batch(problems, kernel: str = "auto", ci_scaled: bool = False, depth=None, **kw) -> api.Batch:
     """A Batch whose problems carry the tuned tile of their size class, stepping at the
     tuned temporal-block depth (``depth`` = 1 or 2 overrides it)."""
+    problems, ci_scaled = prescaled(problems, kernel, ci_scaled)
     best = tune(problems, kernel=kernel, ci_scaled=ci_scaled, **kw)
     if depth is None:
         depth = tune_depth(problems, kernel=kernel, ci_scaled=ci_scaled, **kw)

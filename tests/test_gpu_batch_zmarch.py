@@ -66,17 +66,36 @@ EVEN64 = [(32, 32, 32), (34, 21, 9), (64, 64, 64), (66, 17, 30), (130, 40, 12), 
 EVEN32 = [(32, 32, 32), (36, 21, 9), (128, 16, 12), (132, 40, 12), (4, 3, 3), (260, 9, 5)]
 
 
-@pytest.mark.parametrize("dtype,shapes", [(torch.float64, EVEN64), (torch.float32, EVEN32)])
+@pytest.mark.parametrize("dtype,shapes,prescale", [(torch.float64, EVEN64, True), (torch.float64, EVEN64, False),
+                                                    (torch.float32, EVEN32, True)])
 @pytest.mark.parametrize("nt", [1, 6])
-def test_zmarch_batch_equals_single_runs(dtype, shapes, nt):
+def test_zmarch_batch_equals_single_runs(dtype, shapes, prescale, nt):
+    """FP64 problems on Ci as given are stepped on the batch's own pre-scaled copy by
+    default (equal to the pre-scaled single run), else on Ci as given (equal to that
+    single run); FP32 is never pre-scaled."""
     probs, host = make_batch_problems(shapes, dtype, pitched=False)
-    b = api.Batch(probs, kernel="zmarch")
+    b = api.Batch(probs, kernel="zmarch", prescale=prescale)
     assert b.kernel == "zmarch"
+    assert b.prescaled == (prescale and dtype == torch.float64)
     b.run(nt, graph=False)
     for q, h in enumerate(host):
-        ref = single_run(*h, nt, dtype)
+        ref = single_run(*h, nt, dtype, ci_scaled=b.prescaled)
         assert torch.equal(b.result(q, nt), ref), q
     assert api.device_error() == 0
+
+
+def test_prescaled_batch_keeps_the_given_ci_and_pitch():
+    """The batch's own Cs copies leave the caller's Ci untouched; padded rows work."""
+    probs, host = make_batch_problems([(33, 33, 33), (47, 31, 20)], torch.float64, pitched=True)
+    before = [p["Ci"].clone() for p in probs]
+    b = api.Batch(probs)
+    assert b.prescaled and b.kernel == "zmarch"
+    b.run(3, graph=False)
+    for p, c in zip(probs, before):
+        assert torch.equal(p["Ci"], c)
+    for q, h in enumerate(host):
+        ref = single_run(*h, 3, torch.float64, ci_scaled=True)
+        assert torch.equal(b.result(q, 3).contiguous(), ref), q
 
 
 ODD = [(3, 3, 3), (5, 7, 6), (17, 17, 17), (33, 33, 33), (47, 31, 20), (61, 9, 70), (97, 40, 13),
@@ -195,7 +214,7 @@ def test_tuned_zmarch_batch(tmp_path, monkeypatch):
     probs, host = make_batch_problems(shapes, torch.float64, pitched=True)
     best = tuner.tune(probs, reps=2)
     cache = json.load(open(tmp_path / "tuner.json"))
-    assert all("|zmarch|" in k for k in cache)
+    assert all("|zmarch" in k for k in cache)  # "zmarch-scaled": FP64 is stepped on its own Cs
     assert all(tuple(v) in tuner.ZMARCH_CANDIDATES for v in cache.values())
     for p, (T0, *_rest) in zip(probs, host):
         p["T"].copy_(to_dev(T0))
@@ -303,8 +322,9 @@ def test_batch_step2_is_two_steps(dtype):
 
 def test_batch_pairs_refusals():
     p64, _ = make_batch_problems([(32, 32, 32)], torch.float64, pitched=True)
-    with pytest.raises(_lib.PsError):
-        api.Batch(p64, temporal2=True)  # FP64 pairs run on the pre-scaled coefficient only
+    with pytest.raises(_lib.PsError):  # FP64 pairs run on the pre-scaled coefficient only
+        api.Batch(p64, temporal2=True, prescale=False)
+    assert api.Batch(p64, temporal2=True).prescaled  # the batch's own Cs serves them
     p32, _ = make_batch_problems([(32, 32, 32)], torch.float32, pitched=True)
     with pytest.raises(_lib.PsError):
         api.Batch(p32, kernel="column", temporal2=True)
