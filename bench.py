@@ -54,6 +54,9 @@ def parse_args():
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON); "
                         "step2d on a --size^2 grid")
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    p.add_argument("--field", choices=["gauss", "sine", "gauss_dev"], default="gauss",
+                   help="kernel loop step (FP64): the workload's Gaussian on 1.7, or a field that leaves "
+                        "one binade (see general_path_fields)")
     p.add_argument("--reps", type=int, default=4)
     p.add_argument("--batch-count", type=int, default=256,
                    help="kernel loop batch: the first this many problems of the 256-problem workload")
@@ -82,6 +85,8 @@ def run_kernel_loop(args):
     dev = torch.device("cuda")
     T = torch.from_numpy(T0).to(dev)
     C = torch.from_numpy(Ci).to(dev)
+    if args.field != "gauss":
+        T = dict(general_path_fields(torch, n, dev))[args.field]
     if args.dtype == "f32":
         T, C = api.to_deviation(T, 1.7), api.to_f32(C)
     T2 = T.clone()

@@ -333,11 +333,12 @@ __device__ __forceinline__ void emu_lane_general(const unsigned long long (&c)[P
     }
 }
 
-// True when every high word in h and hc has the sign of hc and a biased exponent
-// of e or e+1 for one e >= 1 (no zero, subnormal, Inf or NaN): the values lie in two
-// adjacent binades of one sign.  *emin = e.
+// True when every high word in h and hc has the sign of hc and a biased exponent in
+// [e, e + 4] for one e >= 1 (no zero, subnormal, Inf or NaN): the values lie, with
+// one sign, in a window of five adjacent binades - where the general path's 57-bit
+// fixed point is exact too, so both give the same sums.  *emin = e.
 template <int N>
-__device__ __forceinline__ bool emu_two_binades_hi(const unsigned (&h)[N], unsigned hc, int *emin) {
+__device__ __forceinline__ bool emu_window_hi(const unsigned (&h)[N], unsigned hc, int *emin) {
     unsigned lo = hc & 0x7ff00000u, hi = lo, sg = 0u;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -347,45 +348,44 @@ __device__ __forceinline__ bool emu_two_binades_hi(const unsigned (&h)[N], unsig
         sg |= h[i] ^ hc;
     }
     *emin = (int)(lo >> 20);
-    return (sg & 0x80000000u) == 0u && hi - lo <= 0x00100000u && lo != 0u && hi != 0x7ff00000u;
+    return (sg & 0x80000000u) == 0u && hi - lo <= 0x00400000u && lo != 0u && hi != 0x7ff00000u;
 }
 
-// |v| in units of the ulp of binade e0, for v of biased exponent e0 or e0 + 1
-// (base_hi = (e0 - 1) << 20): the bit pattern less (e0 - 1) * 2^52 is 2^52 + m in
-// binade e0 and 2^53 + m in binade e0 + 1, whose value is 2 * (2^52 + m).  Exact.
-__device__ __forceinline__ long long emu_near_units(unsigned long long v, unsigned base_hi) {
-    const unsigned hi = ((unsigned)(v >> 32) & 0x7fffffffu) - base_hi;
-    const unsigned long long u = ((unsigned long long)hi << 32) | (unsigned)v;
-    return (long long)(hi < 0x200000u ? u : u + u - (1ull << 53));
+// |v| in units of the ulp of binade emin, for v of biased exponent e in [emin, emin + 4]:
+// the 53-bit significand shifted left by e - emin (< 2^57).  Exact.
+__device__ __forceinline__ long long emu_window_units(unsigned long long v, int emin) {
+    const unsigned hi = (unsigned)(v >> 32);
+    const int d = (int)((hi >> 20) & 0x7ffu) - emin;
+    const unsigned long long m = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | (unsigned)v;
+    return (long long)(m << d);
 }
 
-// The PX stencils of one thread when all their values lie in two adjacent binades
-// of one sign (emu_two_binades_hi, emin = the lower binade): the values' bit
-// patterns become exact integers in units of the lower binade's ulp with a few
-// integer instructions each, the sums are exact, and the node finishes as on the
-// general path (same real sum, same rounding: bit for bit emu_lane_general's
-// result) at about half its cost.  flip: the sign of the values.
+// The PX stencils of one thread when all their values lie, with one sign, in a
+// window of five binades (emu_window_hi, emin = the lowest): each value becomes an
+// exact integer in units of the lowest binade's ulp with a few integer instructions
+// (|value| < 2^57 units, so the sums of seven stay below 2^61), the sums are exact,
+// and the node finishes as on the general path (same real sum, same rounding: bit for
+// bit emu_lane_general's result) at about half its cost.  flip: the values' sign.
 template <int PX, bool kScaled, bool kIso>
-__device__ __forceinline__ void emu_lane_near(const unsigned long long (&c)[PX], unsigned long long xl,
-                                              unsigned long long xr, const unsigned long long (&ym)[PX],
-                                              const unsigned long long (&yp)[PX],
-                                              const unsigned long long (&zm)[PX],
-                                              const unsigned long long (&zp)[PX], const double (&ci)[PX],
-                                              const EmuCoef &k, int emin, double (&out)[PX]) {
-    const unsigned base = (unsigned)(emin - 1) << 20;
+__device__ __forceinline__ void emu_lane_window(const unsigned long long (&c)[PX], unsigned long long xl,
+                                                unsigned long long xr, const unsigned long long (&ym)[PX],
+                                                const unsigned long long (&yp)[PX],
+                                                const unsigned long long (&zm)[PX],
+                                                const unsigned long long (&zp)[PX], const double (&ci)[PX],
+                                                const EmuCoef &k, int emin, double (&out)[PX]) {
     const unsigned long long flip = c[0] & 0x8000000000000000ull;
     const int sc = emin - 1075;
     long long uc[PX];
 #pragma unroll
-    for (int i = 0; i < PX; ++i) uc[i] = emu_near_units(c[i], base);
-    const long long ul = emu_near_units(xl, base), ur = emu_near_units(xr, base);
+    for (int i = 0; i < PX; ++i) uc[i] = emu_window_units(c[i], emin);
+    const long long ul = emu_window_units(xl, emin), ur = emu_window_units(xr, emin);
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
         const long long uxm = i == 0 ? ul : uc[i - 1], uxp = i == PX - 1 ? ur : uc[i + 1];
         const long long c2 = 2 * uc[i];
         const long long sx = uxm + uxp - c2;
-        const long long sy = emu_near_units(ym[i], base) + emu_near_units(yp[i], base) - c2;
-        const long long sz = emu_near_units(zm[i], base) + emu_near_units(zp[i], base) - c2;
+        const long long sy = emu_window_units(ym[i], emin) + emu_window_units(yp[i], emin) - c2;
+        const long long sz = emu_window_units(zm[i], emin) + emu_window_units(zp[i], emin) - c2;
         if (kScaled) {
             unsigned long long sg;
             const unsigned long long a = emu_abs(sx + sy + sz, &sg);

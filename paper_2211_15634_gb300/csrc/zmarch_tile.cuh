@@ -253,16 +253,17 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                                 c[i], xm[i], xp[i], ym[i], yp[i], zm[i], zp[i], ci, p.ek);
                     }
                 } else {
-                    // one path for the whole warp (emu64.cuh): two adjacent binades of one
-                    // sign take the cheap exact conversion, anything else the general one
+                    // one path for the whole warp (emu64.cuh): values of one sign within
+                    // five binades take the cheap exact conversion, anything else the
+                    // general one
                     double ci[PX], o[PX];
 #pragma unroll
                     for (int i = 0; i < PX; ++i) ci[i] = (double)vget<V, E>(civ, i);
                     int emin;
-                    const bool near = emu_two_binades_hi(hw, hc, &emin);
+                    const bool near = emu_window_hi(hw, hc, &emin);
                     if (__all_sync(rmask, near))
-                        emu_lane_near<PX, kScaled, kIso>(c, xm[0], xp[PX - 1], ym, yp, zm, zp, ci, p.ek,
-                                                         emin, o);
+                        emu_lane_window<PX, kScaled, kIso>(c, xm[0], xp[PX - 1], ym, yp, zm, zp, ci, p.ek,
+                                                           emin, o);
                     else
                         emu_lane_general<PX, kScaled, kIso>(c, xm[0], xp[PX - 1], ym, yp, zm, zp, ci,
                                                             p.ek, o);

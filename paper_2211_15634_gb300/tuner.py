@@ -235,7 +235,9 @@ def tune_depth(problems, reps: int = 5, use_cache: bool = True, kernel: str = "a
 
 def tuned_batch(problems, kernel: str = "auto", ci_scaled: bool = False, depth=None, **kw) -> api.Batch:
     """A Batch whose problems carry the tuned tile of their size class, stepping at the
-    tuned temporal-block depth (``depth`` = 1 or 2 overrides it)."""
+    tuned temporal-block depth (``depth`` = 1 or 2 overrides it).  Tuning times real
+    steps on the problems' own fields (unless every choice is cached): set their
+    states after this call."""
     problems, ci_scaled = prescaled(problems, kernel, ci_scaled)
     best = tune(problems, kernel=kernel, ci_scaled=ci_scaled, **kw)
     if depth is None:

@@ -1,5 +1,5 @@
-"""The FP64 step's paths for warps whose values leave one binade: the two-binade
-path (values of one sign in two adjacent binades: cheap exact integer sums) and the
+"""The FP64 step's paths for warps whose values leave one binade: the window path
+(values of one sign within five adjacent binades: cheap exact integer sums) and the
 general fixed-point path.  Both are exact in their sums, so the z-march step must give
 bit for bit the per-node general arithmetic of the kernels that step node by node:
 the fused-pair kernel (pre-scaled coefficient) and the column kernel (Ci as given,
@@ -26,6 +26,10 @@ def field(kind, shape=SHAPE, seed=11):
         return 1.0 + 0.05 * np.where((i + j + k) % 2 == 0, 1.0, -1.0) * (1.0 + 0.1 * r)
     if kind == "two_binades_negative":
         return -field("two_binades", shape, seed)
+    if kind == "window":  # one sign, seven binades: lanes in five take the window path, others not
+        return np.exp2(6.0 * r) * (1.0 + 0.5 * np.where((i + j + k) % 2 == 0, 1.0, -1.0) * r)
+    if kind == "window_negative":
+        return -field("window", shape, seed)
     if kind == "many_binades":  # signs, zeros and tiny values: the general path
         T = 2.0 * r - 1.0
         T[::3, :, ::5] = 0.0
@@ -43,7 +47,10 @@ def setup(kind):
     return T0, Ci, dt, (1.0 / d,) * 3
 
 
-@pytest.mark.parametrize("kind", ["two_binades", "two_binades_negative", "many_binades"])
+KINDS = ["two_binades", "two_binades_negative", "window", "window_negative", "many_binades"]
+
+
+@pytest.mark.parametrize("kind", KINDS)
 def test_prescaled_step_equals_per_node_pairs(kind):
     """Pre-scaled coefficient: nt single z-march steps = nt/2 fused pairs (the pair
     kernel steps node by node) bit for bit, and the oracle within 1e-12."""
@@ -60,7 +67,7 @@ def test_prescaled_step_equals_per_node_pairs(kind):
     assert api.device_error() == 0
 
 
-@pytest.mark.parametrize("kind", ["two_binades", "two_binades_negative", "many_binades"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_ci_as_given_step_equals_column_kernel(launch_override, kind):
     """Ci as given: on fields where every warp leaves one binade, the z-march step
     equals the column kernel's per-node arithmetic bit for bit (a warp whose values
