@@ -60,6 +60,8 @@ def parse_args():
     p.add_argument("--reps", type=int, default=4)
     p.add_argument("--batch-count", type=int, default=256,
                    help="kernel loop batch: the first this many problems of the 256-problem workload")
+    p.add_argument("--comp", action="store_true",
+                   help="kernel loop step (FP32): the compensated step on the two-float state")
     p.add_argument("--temporal2", action="store_true",
                    help="kernel loop step: fused step pairs (each rep is two two-step passes)")
     p.add_argument("--plain-ci", action="store_true",
@@ -95,15 +97,19 @@ def run_kernel_loop(args):
         # FP64: the pre-scaled coefficient of the headline step (--plain-ci: Ci as given)
         scaled = args.dtype == "f64" and not args.plain_ci
         Cs = api.scale_ci(C, 1.0, dt, inv) if scaled else C
+        comp = api.compensation_fields(T) if (args.comp and args.dtype == "f32") else None
         for i in range(args.reps):
             src, dst = (T, T2) if i % 2 == 0 else (T2, T)
+            if comp is not None:
+                api.step_compensated(dst, src, comp[(i + 1) % 2], comp[i % 2], Cs, 1.0, dt, inv)
+                continue
             if args.temporal2:  # two fused two-step passes (plus the boundary copy); nt = 4
                 # keeps the result in `src`, as an even step count must
                 api.run(src, dst, Cs, 1.0, dt, inv, 4, ci_scaled=scaled, temporal2=True)
             else:
                 api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
-        name = api.step_kernel_name(T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled,
-                                    temporal2=args.temporal2)
+        name = "compensated FP32 step" if comp is not None else api.step_kernel_name(
+            T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled, temporal2=args.temporal2)
     elif args.kernel_loop == "adjoint2":
         # FP32: two transposed steps per pass (states T and T2)
         if args.dtype != "f32":

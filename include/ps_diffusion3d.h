@@ -207,8 +207,13 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
                               double _dz, int64_t nx, int64_t ny, int64_t nz, int nt, int dtype,
                               unsigned flags, void *stream, int *final_slot);
 
-/* Destroy every cached CUDA graph. */
+/* Destroy every cached CUDA graph.  The cache (PS_RUN_GRAPH of the 3-D and 2-D time
+ * loops and the batch run) holds at most 256 graphs, keyed by the call's device,
+ * pointers, coefficients, sizes and flags; beyond that the least recently replayed
+ * one is destroyed (a graph still running is freed when it completes). */
 int ps_clear_graph_cache(void);
+/* Number of graphs in the cache. */
+size_t ps_graph_cache_size(void);
 
 /* ---------------------------------------------------------------------
  * Launch-shape overrides (no counterpart in the paper): for tests that

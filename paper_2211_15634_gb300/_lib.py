@@ -76,6 +76,7 @@ SIGNATURES = {
     "ps_diffusion3d_run_states": (_I, [_P, _P, _I64, _I, _P, _D, _D, _D, _D, _D, _I64, _I64, _I64, _I,
                                        _I, _U, _P, ctypes.POINTER(_I)]),
     "ps_clear_graph_cache": (_I, []),
+    "ps_graph_cache_size": (_SZ, []),
     "ps_set_launch_override": (_I, [_I, _I]),
     "ps_get_launch_override": (_I, [_I, ctypes.POINTER(_I)]),
     "ps_diffusion2d_stable_dt": (_I, [ctypes.POINTER(_D), _P, _I64, _I64, _D, _D, _D, _I, _P, _P]),

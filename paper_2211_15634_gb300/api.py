@@ -642,6 +642,11 @@ def clear_graph_cache() -> None:
     check(_lib.load().ps_clear_graph_cache())
 
 
+def graph_cache_size() -> int:
+    """Graphs held by the library's cache (at most 256, least recently used evicted)."""
+    return int(_lib.load().ps_graph_cache_size())
+
+
 def set_launch_override(name: str, value: int) -> int:
     """Set a launch-shape override (``ps_set_launch_override``): ``name`` is one of
     ``kchunk, kchunk2, adj_kchunk, chunk2d`` (planes or rows per CTA, 0 = the library's

@@ -240,8 +240,14 @@ static cudaError_t enqueue_run(void *T, void *T2, void *comp, const void *Ci, St
 using GraphKey = std::tuple<int, const void *, const void *, const void *, const void *, double,
                             double, double, double, double, int64_t, int64_t, int64_t, int, int,
                             unsigned>;
+struct CachedGraph {
+    cudaGraphExec_t exec;
+    uint64_t last_use;  // value of g_graph_clock at the last replay
+};
 static std::mutex g_graph_mu;
-static std::map<GraphKey, cudaGraphExec_t> g_graphs;
+static std::map<GraphKey, CachedGraph> g_graphs;
+static uint64_t g_graph_clock = 0;
+constexpr size_t kGraphCacheMax = 256;  // least recently used graphs beyond this are destroyed
 static cudaStream_t g_capture_stream[64] = {nullptr};
 static unsigned g_capture_gen[64] = {0};
 
@@ -290,9 +296,18 @@ static int graph_replay(const GraphKey &key, F &&enqueue, const char *what, cuda
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        it = g_graphs.emplace(key, exec).first;
+        if (g_graphs.size() >= kGraphCacheMax) {
+            // a graph still running when destroyed is freed by the driver once it completes
+            auto lru = g_graphs.begin();
+            for (auto jt = g_graphs.begin(); jt != g_graphs.end(); ++jt)
+                if (jt->second.last_use < lru->second.last_use) lru = jt;
+            cudaGraphExecDestroy(lru->second.exec);
+            g_graphs.erase(lru);
+        }
+        it = g_graphs.emplace(key, CachedGraph{exec, 0}).first;
     }
-    cudaError_t e = cudaGraphLaunch(it->second, s);
+    it->second.last_use = ++g_graph_clock;
+    cudaError_t e = cudaGraphLaunch(it->second.exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return PS_OK;
 }
@@ -543,9 +558,14 @@ int ps_diffusion3d_run(void *T, void *T2, const void *Ci, double lam, double dt,
                                  0u, stream, result_in_T2);
 }
 
+size_t ps_graph_cache_size(void) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    return g_graphs.size();
+}
+
 int ps_clear_graph_cache(void) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
-    for (auto &kv : g_graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : g_graphs) cudaGraphExecDestroy(kv.second.exec);
     g_graphs.clear();
     return PS_OK;
 }

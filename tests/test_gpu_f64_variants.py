@@ -62,3 +62,21 @@ def test_graph_replay_across_an_override_change(launch_override):
         outs.append(to_host(api.run(T, T2, C, lam, dt, inv, 5, ci_scaled=True, graph=True)))
     assert np.array_equal(outs[0], ref) and np.array_equal(outs[1], ref)
     api.clear_graph_cache()
+
+
+def test_graph_cache_is_bounded_and_override_changes_empty_it(launch_override):
+    """The graph cache keeps at most 256 graphs (the least recently replayed go first);
+    a launch-override change empties it."""
+    api.clear_graph_cache()
+    T0, Ci, lam, dt, inv = iso((64, 9, 7))
+    T, C = to_dev(T0), api.scale_ci(to_dev(Ci), lam, dt, inv)
+    T2 = torch.empty_like(T)
+    for i in range(300):  # each dt is a new key
+        api.run(T, T2, C, lam, dt * (1.0 + 1e-6 * i), inv, 2, ci_scaled=True, graph=True)
+    assert api.graph_cache_size() == 256
+    torch.cuda.synchronize()
+    launch_override(f64_px2=1)
+    assert api.graph_cache_size() == 0
+    api.run(T, T2, C, lam, dt, inv, 2, ci_scaled=True, graph=True)
+    assert api.graph_cache_size() == 1
+    api.clear_graph_cache()

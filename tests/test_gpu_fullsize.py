@@ -4,7 +4,8 @@ for the batch, on whole problems.
 
 * FP64 512^3, nt = 100: dt from maximum(Ci) on the GPU, the pre-scaled
   coefficient, the graph-captured loop of the TMA step (the headline path).
-* FP32 1024^3, nt = 100, deviation storage (the bench's FP32 1024^3 row).
+* FP32 1024^3, nt = 100, deviation storage (the bench's FP32 1024^3 row), and the
+  compensated two-float step at 512^3 (the bench's compensated row).
 * The 256-problem batch, nt = 500, padded rows, the TMA z-march with tuned
   z-chunks (FP64 on the pre-scaled coefficient, and FP32): the smallest
   problems and the largest one against the oracle's own runs.
@@ -58,6 +59,32 @@ def test_fp64_512_bench_path():
         oracle.set_threads(1)
     assert np.max(np.abs(got - ref)) <= FP64_TOL * np.max(np.abs(T0))
     assert float(res.min()) >= T0.min() - 1e-12 and float(res.max()) <= T0.max() + 1e-12
+    assert api.device_error() == 0
+    api.clear_graph_cache()
+
+
+def test_fp32_compensated_512_bench_path():
+    """The bench's compensated FP32 row (512^3, nt = 100, graph) from the two-float
+    deviation of T0: sampled nodes against the oracle on the same starting state and
+    the FP32 Ci: within 2e-8 of max|D0|, ten times the compensated arithmetic error the
+    bench measures at 256^3 and far inside the plain FP32 bound (7.7e-5 here)."""
+    n, nt = 512, 100
+    T0, Ci, inv = bench.fields(n)
+    dev = torch.device("cuda")
+    D, E0 = api.to_deviation_pair(torch.from_numpy(T0).to(dev), 1.7)
+    C32 = api.to_f32(torch.from_numpy(Ci).to(dev))
+    dt = api.stable_dt(C32, 1.0)
+    comp = api.compensation_fields(D, E0)
+    start = api.from_deviation_pair(D, E0, 0.0).cpu().numpy()
+    res = api.run(D, torch.empty_like(D), C32, 1.0, dt, inv, nt, comp=comp, graph=True)
+    got = sample(api.from_deviation_pair(res, comp[nt % 2], 0.0), PTS512)
+    C0 = Ci.astype(np.float32).astype(np.float64)
+    oracle.set_threads(max(1, oracle.max_threads()))
+    try:
+        ref = light_cone_reference(oracle, start, C0, 1.0, dt, inv, nt, PTS512)
+    finally:
+        oracle.set_threads(1)
+    assert np.max(np.abs(got - ref)) <= 2e-8 * np.max(np.abs(start))
     assert api.device_error() == 0
     api.clear_graph_cache()
 
