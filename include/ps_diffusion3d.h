@@ -30,9 +30,13 @@
  *          constant is zero and the boundary is fixed); ps_to_deviation /
  *          ps_from_deviation convert.
  * Memory   All field pointers are DEVICE pointers allocated and owned by
- *          the caller.  The library allocates nothing on these calls.
- *          Entry points that need scratch take a caller-owned device
- *          workspace of at least ps_workspace_bytes() bytes.
+ *          the caller.  The library allocates no device memory on these
+ *          calls.  Entry points that need scratch take a caller-owned
+ *          device workspace of at least ps_workspace_bytes() bytes.  The
+ *          two calls that return a host result (ps_maximum,
+ *          ps_diffusion3d_stable_dt) keep a 64-byte pinned host slot per
+ *          concurrent caller, allocated on first use and reused for the
+ *          life of the context.
  * Streams  `stream` is a cudaStream_t (NULL = legacy default stream).
  *          Every call only enqueues work on it and returns; none
  *          synchronizes, except where a host result is returned
@@ -296,7 +300,12 @@ int ps_diffusion3d_adjoint2_ex(void *Tbar, void *Cibar, const void *ybar, const 
 /* maximum(A) (Fig. 1's maximum(Ci)); result to a device double. */
 int ps_maximum_async(double *out_dev, const void *A, int64_t n, int dtype, void *workspace,
                      void *stream);
-/* maximum(A) returned to the host (synchronizes `stream`). */
+/* maximum(A) returned to the host (synchronizes `stream`).  The finishing
+ * kernel stores the result into a pinned, mapped host slot taken from a
+ * pool for the duration of the call (allocating one when every slot is in
+ * use; a failed allocation returns PS_ERR_CUDA), so the read-back uses no
+ * copy engine and does not wait behind copies that other streams have in
+ * flight. */
 int ps_maximum(double *out_host, const void *A, int64_t n, int dtype, void *workspace,
                void *stream);
 /* Fig. 1: dt = min(dx^2,dy^2,dz^2)/lam/maximum(Ci)/6.1 with dd = ld/(nd-1);

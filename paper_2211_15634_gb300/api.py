@@ -389,15 +389,19 @@ class SolvePipeline:
         with torch.cuda.stream(self.s_in):
             if self.freed[k] is not None:
                 self.s_in.wait_event(self.freed[k])
-            T.copy_(T0_host, non_blocking=True)
+            # Ci first: dt and the scaled coefficient are formed while T arrives
             Ci.copy_(Ci_host, non_blocking=True)
+            ci_arrived = torch.cuda.Event()
+            ci_arrived.record(self.s_in)
+            T.copy_(T0_host, non_blocking=True)
             arrived = torch.cuda.Event()
             arrived.record(self.s_in)
         with torch.cuda.stream(self.s_run):
-            self.s_run.wait_event(arrived)
+            self.s_run.wait_event(ci_arrived)
             dt = stable_dt(Ci, self.lam, self.lengths)  # waits for this stream only
             if self.scaled:
                 scale_ci(Ci, self.lam, dt, self.inv, out=Ci)
+            self.s_run.wait_event(arrived)
             res = run(T, T2, Ci, self.lam, dt, self.inv, self.nt, graph=self.graph, ci_scaled=self.scaled)
             done = torch.cuda.Event()
             done.record(self.s_run)

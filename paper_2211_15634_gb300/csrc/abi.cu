@@ -769,15 +769,55 @@ int ps_maximum_async(double *out_dev, const void *A, int64_t n, int dtype, void 
     return PS_OK;
 }
 
+// Result slots of the blocking reductions: pinned, mapped host memory that the
+// finishing kernel stores to directly.  A device-to-host memcpy of the 8-byte result
+// would wait behind large copies that other streams have in flight on the copy
+// engine (a 1 GiB copy out of an earlier result holds it for milliseconds); a kernel
+// store does not use the copy engine.  One slot per concurrent call, kept for the
+// life of the context (device, context generation) that allocated it.
+class HostSlots {
+public:
+    double *acquire(cudaError_t *err) {
+        const uint64_t key = ((uint64_t)(unsigned)current_device() << 32) | context_generation();
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            auto &v = free_[key];
+            if (!v.empty()) {
+                double *p = v.back();
+                v.pop_back();
+                *err = cudaSuccess;
+                return p;
+            }
+        }
+        void *p = nullptr;
+        *err = cudaHostAlloc(&p, 64, cudaHostAllocMapped);
+        return *err == cudaSuccess ? (double *)p : nullptr;
+    }
+    void release(double *p) {
+        const uint64_t key = ((uint64_t)(unsigned)current_device() << 32) | context_generation();
+        std::lock_guard<std::mutex> lock(mu_);
+        free_[key].push_back(p);
+    }
+
+private:
+    std::mutex mu_;
+    std::map<uint64_t, std::vector<double *>> free_;
+};
+static HostSlots g_host_slots;
+
 int ps_maximum(double *out_host, const void *A, int64_t n, int dtype, void *workspace,
                void *stream) {
     if (!out_host) return fail(PS_ERR_ARG, "out_host is NULL");
     PS_TRY(check_reduce(A, n, dtype, workspace));
-    double *slot = (double *)((char *)workspace + 8);  // scratch slot inside the workspace
-    cudaError_t e = launch_maximum(slot, A, n, dtype, workspace, (cudaStream_t)stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out_host, slot, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    cudaError_t e = cudaSuccess;
+    double *slot = g_host_slots.acquire(&e);
+    if (!slot) return cuda_fail(e, "ps_maximum: allocating its host result slot");
+    double *slot_dev = nullptr;
+    e = cudaHostGetDevicePointer((void **)&slot_dev, slot, 0);
+    if (e == cudaSuccess) e = launch_maximum(slot_dev, A, n, dtype, workspace, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) *out_host = *(volatile double *)slot;
+    g_host_slots.release(slot);
     if (e != cudaSuccess) return cuda_fail(e, "ps_maximum");
     return PS_OK;
 }
