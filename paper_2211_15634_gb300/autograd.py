@@ -8,8 +8,9 @@ reads each state once), else every ``ceil(sqrt(nt))`` steps.  ``backward`` walks
 segments in reverse: it recomputes the states of one segment from its
 checkpoint with the forward kernel, then applies the transposed step
 (``ps_diffusion3d_adjoint``) from the segment's last step to its first,
-accumulating dL/dCi.  dt is held constant (not differentiated through
-maximum(Ci)).  Memory: about ``nt/every + every + 2`` fields.
+accumulating dL/dCi; the next segment's recompute runs on a side stream meanwhile.
+dt is held constant (not differentiated through maximum(Ci)).  Memory: about
+``nt/every + 2*every + 2`` fields.
 
 On FP64 grids with equal spacings every kernel runs on the pre-scaled
 coefficient Cs = dt*lam*_dx^2*Ci (one FP64 multiply-add per node forward);
@@ -79,32 +80,77 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
     return cur, ckpts
 
 
-def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None):
+def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None,
+                          overlap=None):
     """Reverse sweep; returns (dL/dT0, dL/dCi).  ``pairs``: take the transposed
-    steps two per launch where ``api.adjoint2`` applies (default off)."""
+    steps two per launch where ``api.adjoint2`` applies (default off).  ``overlap``
+    (default on for CUDA tensors with more than one segment to recompute): recompute
+    segment s-1's states on a side stream while segment s's transposed steps run,
+    into the second of two segment buffers (one more segment of memory); the kernels
+    and their order on every buffer are unchanged, so the gradient is bit for bit
+    the one-stream sweep's."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     pairs = bool(pairs) and not scaled and api.adjoint2_supported(ybar_nt)
     ybar = ybar_nt.contiguous().clone()
     tbar = torch.empty_like(ybar)
     cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
-    # grids for the recomputed states of one segment, with the boundary of T0
-    seg = api.StateBlock(ckpts[0], max(0, min(every, nt) - 1))
     nseg = len(ckpts)
-    for s in range(nseg - 1, -1, -1):
+    seg_len = max(0, min(every, nt) - 1)  # recomputed states per segment
+    if overlap is None:
+        overlap = ybar.is_cuda and nseg > 1 and seg_len > 0
+    # grids for the recomputed states of a segment, with the boundary of T0
+    segs = [api.StateBlock(ckpts[0], seg_len) for _ in range(2 if overlap else 1)]
+    main = torch.cuda.current_stream(ybar.device) if overlap else None
+    side = torch.cuda.Stream(ybar.device) if overlap else None
+    ready, used = {}, [None, None]  # recompute of segment s done; sweep done with buffer b
+
+    def recompute(s):
         t0 = s * every
         t1 = min(t0 + every, nt)
-        if t1 - t0 > 1:  # states t0+1 .. t1-1 from the checkpoint, every one kept
-            api.run_states(ckpts[s], seg, 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
-        states = [ckpts[s]] + seg.grids[:t1 - t0 - 1]
-        t = t1 - 1
-        while t >= t0:
-            if pairs and t - 1 >= t0:  # steps t and t-1 in one pass
-                api.adjoint2(tbar, cibar, ybar, states[t - t0], states[t - 1 - t0], C, lam, dt, inv)
-                t -= 2
+        if t1 - t0 <= 1:
+            return
+        b = s % len(segs)
+        if not overlap:
+            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
+            return
+        with torch.cuda.stream(side):
+            side.wait_stream(main)  # the checkpoints, Cs and the buffers' boundaries
+            if used[b] is not None:
+                side.wait_event(used[b])  # the sweep no longer reads this buffer
+            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
+            ready[s] = torch.cuda.Event()
+            ready[s].record(side)
+
+    try:
+        if overlap:
+            recompute(nseg - 1)
+        for s in range(nseg - 1, -1, -1):
+            if overlap:
+                if s >= 1:
+                    recompute(s - 1)
+                if s in ready:
+                    main.wait_event(ready[s])
             else:
-                api.adjoint(tbar, cibar, ybar, states[t - t0], C, lam, dt, inv, ci_scaled=scaled)
-                t -= 1
-            ybar, tbar = tbar, ybar
+                recompute(s)
+            t0 = s * every
+            t1 = min(t0 + every, nt)
+            b = s % len(segs)
+            states = [ckpts[s]] + segs[b].grids[:t1 - t0 - 1]
+            t = t1 - 1
+            while t >= t0:
+                if pairs and t - 1 >= t0:  # steps t and t-1 in one pass
+                    api.adjoint2(tbar, cibar, ybar, states[t - t0], states[t - 1 - t0], C, lam, dt, inv)
+                    t -= 2
+                else:
+                    api.adjoint(tbar, cibar, ybar, states[t - t0], C, lam, dt, inv, ci_scaled=scaled)
+                    t -= 1
+                ybar, tbar = tbar, ybar
+            if overlap:
+                used[b] = torch.cuda.Event()
+                used[b].record(main)
+    finally:
+        if overlap:  # later work on the caller's stream (and frees of these buffers) after the side stream's
+            main.wait_stream(side)
     if scaled:  # dL/dCi = dt*lam*_dx^2 * dL/dCs
         api.scale_ci(cibar, lam, dt, inv, out=cibar)
     return ybar, cibar

@@ -22,6 +22,7 @@
 
 #include "adj32_node.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 #include "tma.cuh"
 #include "zmarch.h"
 
@@ -47,6 +48,8 @@ k_adjoint_f32(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ C
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = (uint64_t *)(smem + NST * SB);
     __shared__ int s_abort;
+    grid_dep_wait();  // the previous launch's writes (and its reads of Tbar) are complete
+    grid_dep_launch();
 
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int X0 = (int)(blockIdx.x % p.ntx) * BX, Y0 = (int)(blockIdx.x / p.ntx) * BY;
@@ -250,6 +253,8 @@ k_adjoint2_f32(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ 
     unsigned char *ringY = smem, *ringS = smem + NYC * YCS, *tiles = ringS + NS * SS;
     uint64_t *barY = (uint64_t *)(tiles + 2 * SBA), *barS = barY + NYC;
     __shared__ int s_abort;
+    grid_dep_wait();
+    grid_dep_launch();
 
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int X0 = (int)(blockIdx.x % p.ntx) * BX, Y0 = (int)(blockIdx.x / p.ntx) * BY;
@@ -552,9 +557,8 @@ static cudaError_t launch_adj2_t(float *Tbar, float *Cibar, const float *ybar, c
     p.nz = (int)g.nz;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    k_adjoint2_f32<NYC, NS><<<dim3((unsigned)tiles, (unsigned)gz, 1), 256, smem, s>>>(
-        mY, mC, mS1, mS0, mB, Tbar, Cibar, p);
-    return cudaGetLastError();
+    return launch_pdl(k_adjoint2_f32<NYC, NS>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(256), smem, s, mY, mC,
+                      mS1, mS0, mB, Tbar, Cibar, p);
 }
 
 cudaError_t launch_adjoint2_f32(float *Tbar, float *Cibar, const float *ybar, const float *S1,
@@ -603,9 +607,8 @@ static cudaError_t launch_adj32_t(float *Tbar, float *Cibar, const float *ybar, 
     p.nz = (int)g.nz;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    k_adjoint_f32<BY, NST, MINB><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
-        mT, mY, mC, mB, Tbar, Cibar, p);
-    return cudaGetLastError();
+    return launch_pdl(k_adjoint_f32<BY, NST, MINB>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem,
+                      s, mT, mY, mC, mB, Tbar, Cibar, p);
 }
 
 bool adjoint_f32_supported(Grid3 g, const void *const *ptrs, int nptr) {

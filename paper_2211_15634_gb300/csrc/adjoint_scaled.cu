@@ -29,6 +29,7 @@
 
 #include "emu64.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 #include "tma.cuh"
 #include "zmarch.h"
 
@@ -75,6 +76,8 @@ k_adjoint_scaled(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
     long long *wtile = (long long *)(smem + 3 * NST * TBA);  // 3 rotating w tiles
     uint64_t *bar = (uint64_t *)(smem + 3 * NST * TBA + 3 * TBA);
     __shared__ int s_abort, s_E;
+    grid_dep_wait();  // the previous launch's writes (and its reads of Tbar) are complete
+    grid_dep_launch();
 
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int X0 = (int)(blockIdx.x % p.ntx) * BX, Y0 = (int)(blockIdx.x / p.ntx) * BY;
@@ -362,9 +365,8 @@ cudaError_t launch_adjoint_scaled(double *Tbar, double *Csbar, const double *yba
     const int64_t gz = (g.nz + kchunk - 1) / kchunk;
     if (tiles > 0x7fffffffLL || gz > 65535) return cudaErrorInvalidConfiguration;
     AdjSParams p{g.nx, g.ny, g.nz, kchunk, (int)ntx};
-    k_adjoint_scaled<BY, NST><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
-        mT, mY, mC, Tbar, Csbar, p);
-    return cudaGetLastError();
+    return launch_pdl(k_adjoint_scaled<BY, NST>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem, s,
+                      mT, mY, mC, Tbar, Csbar, p);
 }
 
 unsigned adjoint_scaled_device_error(bool clear) {

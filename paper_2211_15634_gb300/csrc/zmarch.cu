@@ -14,6 +14,7 @@
 #include "emu64.cuh"
 #include "internal.h"
 #include "node.cuh"
+#include "pdl.cuh"
 #include "tma.cuh"
 #include "zmarch.h"
 #include "zmarch_tile.cuh"
@@ -27,6 +28,8 @@ __global__ void __launch_bounds__(32 * BY, 1)
 k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmC,
          const __grid_constant__ CUtensorMap tmE, void *__restrict__ T2v, void *__restrict__ E2v,
          const ZParams p) {
+    grid_dep_wait();  // the previous step's writes (and its reads of T2) are complete
+    grid_dep_launch();
     const int X0 = (int)(blockIdx.x % p.ntx) * (32 * ZTraits<MODE>::PX);
     const int Y0 = (int)(blockIdx.x / p.ntx) * BY;
     const int k0 = 1 + (int)blockIdx.y * p.kchunk;
@@ -141,9 +144,8 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *E2, const void
     p.pitch = g.nx;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    k_zmarch<MODE, BY, NST><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
-        mT, mC, mE, T2, E2, p);
-    return cudaGetLastError();
+    return launch_pdl(k_zmarch<MODE, BY, NST>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem, s,
+                      mT, mC, mE, T2, E2, p);
 }
 
 static ZParams make_params(StepCoef c) {

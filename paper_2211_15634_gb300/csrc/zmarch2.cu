@@ -5,6 +5,7 @@
 
 #include "internal.h"
 #include "node.cuh"
+#include "pdl.cuh"
 #include "tma.cuh"
 #include "zmarch.h"
 #include "zmarch2_tile.cuh"
@@ -17,6 +18,8 @@ template <typename E, int BY, int NT, int NC>
 __global__ void __launch_bounds__(32 * BY, Z2Ring<E>::MINB)
 k_zmarch2(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmC,
           E *__restrict__ T2, const Z2Params p) {
+    grid_dep_wait();  // the previous launch's writes (and its reads of T2) are complete
+    grid_dep_launch();
     const int X0 = (int)(blockIdx.x % p.ntx) * (32 * Z2Traits<E>::PX), Y0 = (int)(blockIdx.x / p.ntx) * BY;
     const int k0 = 1 + (int)blockIdx.y * p.kchunk;
     const int k1 = (int)min((int64_t)k0 + p.kchunk, p.nz - 1);  // output planes [k0, k1)
@@ -57,8 +60,8 @@ static cudaError_t launch_z2(E *T2, const E *T, const E *Ci, Z2Params p, Grid3 g
     p.pitch = g.nx;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    k_zmarch2<E, BY, NT, NC><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(mT, mC, T2, p);
-    return cudaGetLastError();
+    return launch_pdl(k_zmarch2<E, BY, NT, NC>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem, s, mT,
+                      mC, T2, p);
 }
 
 cudaError_t launch_step2_f32(float *T2, const float *T, const float *Ci, StepCoef c, Grid3 g,
