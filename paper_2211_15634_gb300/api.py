@@ -697,10 +697,12 @@ def step_kernel_name(T2, T, Ci, lam, dt, inv_spacing, ci_scaled=False, temporal2
 KERNEL_SOURCES = {
     "k_zmarch": ["paper_2211_15634_gb300/csrc/zmarch.cu", "paper_2211_15634_gb300/csrc/zmarch_tile.cuh",
                  "paper_2211_15634_gb300/csrc/zmarch.h", "paper_2211_15634_gb300/csrc/emu64.cuh",
-                 "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],
+                 "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh",
+                 "paper_2211_15634_gb300/csrc/pdl.cuh"],
     "k_zmarch2": ["paper_2211_15634_gb300/csrc/zmarch2.cu", "paper_2211_15634_gb300/csrc/zmarch2_tile.cuh",
                   "paper_2211_15634_gb300/csrc/emu64.cuh",
-                  "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh"],
+                  "paper_2211_15634_gb300/csrc/node.cuh", "paper_2211_15634_gb300/csrc/tma.cuh",
+                  "paper_2211_15634_gb300/csrc/pdl.cuh"],
     "k_step_basic_emu": ["paper_2211_15634_gb300/csrc/stencil_basic.cuh",
                          "paper_2211_15634_gb300/csrc/emu64.cuh"],
     "k_step_basic": ["paper_2211_15634_gb300/csrc/stencil_basic.cuh"],

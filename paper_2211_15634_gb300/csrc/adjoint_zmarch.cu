@@ -24,6 +24,7 @@
 
 #include "emu64.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 #include "tma.cuh"
 #include "zmarch.h"
 
@@ -70,6 +71,8 @@ k_adjoint_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
     uint64_t *bar = (uint64_t *)(smem + 3 * NST * TBA + 3 * TBA);
     __shared__ int s_abort;
     __shared__ int s_emax[BY];
+    grid_dep_wait();  // the previous launch's writes (and its reads of Tbar) are complete
+    grid_dep_launch();
     // FP64: biased exponent of the fixed-point scale (value = X * 2^(Esc-1079)); it only grows,
     // and every stored value is at most 2^57 in magnitude.  0x7ff marks a non-finite w.
     int Esc = 1;
@@ -398,9 +401,8 @@ static cudaError_t launch_adj_t(E *Tbar, E *Cibar, const E *ybar, const E *T, co
     p.nz = g.nz;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    k_adjoint_zmarch<E, kIso, BY, NST><<<dim3((unsigned)tiles, (unsigned)gz, 1), 32 * BY, smem, s>>>(
-        mT, mY, mC, Tbar, Cibar, p);
-    return cudaGetLastError();
+    return launch_pdl(k_adjoint_zmarch<E, kIso, BY, NST>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem,
+                      s, mT, mY, mC, Tbar, Cibar, p);
 }
 
 bool adjoint_zmarch_supported(Grid3 g, int esz, const void *const *ptrs, int nptr) {

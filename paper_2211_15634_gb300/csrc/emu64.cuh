@@ -28,10 +28,13 @@
 //    of a warp at once, so the warp does not diverge.
 //  * Inf/NaN inputs fall back to the plain FP64 expression.
 //
-// Error: S is exact (the general path truncates values more than 57 binades
-// below the largest of the seven); K*S keeps >= 60 bits before one
-// round-to-nearest into 53 bits; the DFMA rounds once more.  Per step this
-// stays within a few units in the last place of T.
+// Error: the fast path forms S exactly.  The general path keeps each value's
+// bits down to 2^-56 of the largest of the seven (a value more than four binades
+// below it loses low-order bits, one 57 or more binades below loses all of them),
+// so S is exact when the seven span at most five binades and otherwise within
+// 7 * 2^-56 of the largest value.  K*S keeps >= 60 bits before one
+// round-to-nearest into 53 bits; the DFMA rounds once more.  Per step this stays
+// within a few units in the last place of the stencil's largest value.
 #pragma once
 
 #include <cstdint>

@@ -1,7 +1,9 @@
 """The FP64 step's paths for warps whose values leave one binade: the window path
 (values of one sign within five adjacent binades: cheap exact integer sums) and the
-general fixed-point path.  Both are exact in their sums, so the z-march step must give
-bit for bit the per-node general arithmetic of the kernels that step node by node:
+general fixed-point path (each node's values at 57 bits below its largest exponent:
+exact within five binades, low-order bits of smaller values dropped beyond).  Both
+are deterministic node by node, so the z-march step must give bit for bit the
+per-node general arithmetic of the kernels that step node by node:
 the fused-pair kernel (pre-scaled coefficient) and the column kernel (Ci as given,
 forced by the step_plain launch override), and the FP64 oracle within 1e-12."""
 import numpy as np
