@@ -41,7 +41,11 @@
  *          Every call only enqueues work on it and returns; none
  *          synchronizes, except where a host result is returned
  *          (ps_maximum, ps_diffusion3d_stable_dt), which synchronize
- *          `stream` before returning.
+ *          `stream` before returning.  The step and transposed-step
+ *          kernels use programmatic dependent launch: one may be
+ *          scheduled while the launch before it on the stream still
+ *          runs, but it touches no memory until that launch has
+ *          completed, so stream order holds as for any other launch.
  * Errors   Every entry point returns a ps_status.  Arguments are checked
  *          on the host before anything is launched; a failed check
  *          launches nothing.  PS_ERR_CUDA reports a CUDA error seen at
