@@ -64,6 +64,8 @@ def _load():
             lib.or_stable_dt2d.restype = d
             lib.or_step.argtypes = [p, p, p, d, d, d, d, d, i64, i64, i64]
             lib.or_run.argtypes = [p, p, p, d, d, d, d, d, i64, i64, i64, i32]
+            lib.or_step_explicit.argtypes = [p, p, p, d, d, d, d, d, i64, i64, i64]
+            lib.or_run_explicit.argtypes = [p, p, p, d, d, d, d, d, i64, i64, i64, i32]
             lib.or_run.restype = i32
             lib.or_adjoint_step.argtypes = [p, p, p, p, p, d, d, d, d, d, i64, i64, i64]
             lib.or_gradient.argtypes = [p, p, p, p, p, d, d, d, d, d, i64, i64, i64, i32]
@@ -110,22 +112,27 @@ def stable_dt(dx: float, dy: float, dz: float, lam: float, maxCi: float) -> floa
 
 
 def step(T2: np.ndarray, T: np.ndarray, Ci: np.ndarray, lam: float, dt: float,
-         _dx: float, _dy: float, _dz: float) -> None:
-    """``step!(T2, T, Ci, lam, dt, _dx, _dy, _dz)`` of Fig. 1, in place on T2's interior."""
+         _dx: float, _dy: float, _dz: float, *, explicit: bool = False) -> None:
+    """``step!(T2, T, Ci, lam, dt, _dx, _dy, _dz)`` of Fig. 1, in place on T2's interior
+    (``explicit``: in the explicit notation, see :func:`run`)."""
     for a, nm in ((T2, "T2"), (T, "T"), (Ci, "Ci")):
         _f64(a, nm)
     nz, ny, nx = T.shape
-    _load().or_step(_ptr(T2), _ptr(T), _ptr(Ci), lam, dt, _dx, _dy, _dz, nx, ny, nz)
+    fn = _load().or_step_explicit if explicit else _load().or_step
+    fn(_ptr(T2), _ptr(T), _ptr(Ci), lam, dt, _dx, _dy, _dz, nx, ny, nz)
 
 
 def run(T0: np.ndarray, Ci: np.ndarray, lam: float, dt: float, _dx: float, _dy: float,
-        _dz: float, nt: int) -> np.ndarray:
-    """Fig. 1 time loop from T0 for nt steps; returns the final state (a new array)."""
+        _dz: float, nt: int, *, explicit: bool = False) -> np.ndarray:
+    """Fig. 1 time loop from T0 for nt steps; returns the final state (a new array).
+    ``explicit``: the step in the explicit notation of the paper's Results (second
+    differences A[i+1] - 2*A[i] + A[i-1]) instead of Fig. 1's @d2_xi form."""
     T = np.array(_f64(T0, "T0"), copy=True)
     T2 = np.empty_like(T)
     _f64(Ci, "Ci")
     nz, ny, nx = T.shape
-    odd = _load().or_run(_ptr(T), _ptr(T2), _ptr(Ci), lam, dt, _dx, _dy, _dz, nx, ny, nz, int(nt))
+    fn = _load().or_run_explicit if explicit else _load().or_run
+    odd = fn(_ptr(T), _ptr(T2), _ptr(Ci), lam, dt, _dx, _dy, _dz, nx, ny, nz, int(nt))
     return T2 if odd else T
 
 

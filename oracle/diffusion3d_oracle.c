@@ -25,7 +25,8 @@
  *
  * Parity pins (tests/test_oracle_pins.py): constant field, discrete sine
  * eigenmode decay, dense matrix form on tiny grids, adjoint dot-product test,
- * complex-step and finite-difference gradients.
+ * complex-step and finite-difference gradients; the explicit-notation step
+ * (or_step_explicit) has its own pins in tests/test_oracle_explicit_pins.py.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -90,6 +91,46 @@ void or_step(double *T2, const double *T, const double *Ci, double lam, double d
                 double lap = laplacian_at(T, p, sx, sy, sz, _dx2, _dy2, _dz2);
                 T2[p] = T[p] + dt * ((lam * Ci[p]) * lap);
             }
+}
+
+/* The explicit-notation solver the paper's Results set beside Fig. 1's (the same
+ * step with the stencil written out on indices instead of @d2_xi): each second
+ * difference as A[i+1] - 2*A[i] + A[i-1], evaluated left to right.  The same
+ * operator as laplacian_at in exact arithmetic; the roundings differ. */
+static double laplacian_explicit_at(const double *T, int64_t p, int64_t sx, int64_t sy, int64_t sz,
+                                    double _dx2, double _dy2, double _dz2) {
+    double c = T[p];
+    double d2x = (T[p + sx] - 2.0 * c) + T[p - sx];
+    double d2y = (T[p + sy] - 2.0 * c) + T[p - sy];
+    double d2z = (T[p + sz] - 2.0 * c) + T[p - sz];
+    return (d2x * _dx2 + d2y * _dy2) + d2z * _dz2;
+}
+
+/* step! in the explicit notation (interior nodes of T2 only, as or_step). */
+void or_step_explicit(double *T2, const double *T, const double *Ci, double lam, double dt,
+                      double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz) {
+    const double _dx2 = _dx * _dx, _dy2 = _dy * _dy, _dz2 = _dz * _dz;
+    const int64_t sx = 1, sy = nx, sz = nx * ny;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int64_t k = 1; k < nz - 1; ++k)
+        for (int64_t j = 1; j < ny - 1; ++j)
+            for (int64_t i = 1; i < nx - 1; ++i) {
+                int64_t p = i + nx * (j + ny * k);
+                double lap = laplacian_explicit_at(T, p, sx, sy, sz, _dx2, _dy2, _dz2);
+                T2[p] = T[p] + dt * ((lam * Ci[p]) * lap);
+            }
+}
+
+/* Fig. 1 time loop with the explicit-notation step (see or_run). */
+int or_run_explicit(double *T, double *T2, const double *Ci, double lam, double dt,
+                    double _dx, double _dy, double _dz, int64_t nx, int64_t ny, int64_t nz, int nt) {
+    memcpy(T2, T, sizeof(double) * (size_t)(nx * ny * nz));
+    double *cur = T, *nxt = T2;
+    for (int it = 0; it < nt; ++it) {
+        or_step_explicit(nxt, cur, Ci, lam, dt, _dx, _dy, _dz, nx, ny, nz);
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    return cur == T2;
 }
 
 /* Fig. 1 time loop: T2 = copy(T), then nt times { step!(T2, T, ...); swap }.

@@ -147,6 +147,24 @@ def test_fp64_prescaled_ci_matches_oracle(shape, nt):
     assert api.device_error() == 0
 
 
+@pytest.mark.parametrize("shape", [(37, 29, 23), (130, 67, 33)])
+def test_fp64_matches_both_notations(shape):
+    """The paper's Results run Fig. 1's solver and an explicit-notation one (second
+    differences written A[i+1] - 2*A[i] + A[i-1]): one operator, different roundings.
+    The FP64 step forms the neighbour sum exactly, so it is within 1e-12 of the
+    oracle in either notation (pre-scaled and on Ci as given)."""
+    nt = 9
+    T0, Ci, lam, dt, inv = iso_problem(*shape)
+    got_s = prescaled_run(T0, Ci, lam, dt, inv, nt)
+    T = to_dev(T0)
+    got_c = to_host(api.run(T, torch.empty_like(T), to_dev(Ci), lam, dt, inv, nt))
+    for explicit in (False, True):
+        ref = oracle.run(T0, Ci, lam, dt, *inv, nt, explicit=explicit)
+        assert rel_linf(got_s, ref) <= FP64_TOL
+        assert rel_linf(got_c, ref) <= FP64_TOL
+    assert api.device_error() == 0
+
+
 def test_fp64_prescaled_general_path_and_graph():
     """Signs, zeros and binade changes (fixed-point path) with the pre-scaled
     coefficient, run plainly and as a CUDA graph (bitwise equal)."""
