@@ -65,6 +65,46 @@ def uniform(seed: int, idx: np.ndarray) -> np.ndarray:
     return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
+def _as_int64(v: int) -> int:
+    """The signed 64-bit integer with the bits of the unsigned 64-bit ``v``."""
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _shr(z, s: int):
+    """Logical right shift by ``s`` of uint64 bit patterns held in an int64 tensor."""
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def uniform_torch(seed: int, idx):
+    """:func:`uniform` for an int64 torch tensor of counters, on any device, bit for bit:
+    the same SplitMix64 draw in wrapping int64 arithmetic with logical right shifts
+    (for inputs too large to generate on the host)."""
+    import torch
+    g = _as_int64(int(GOLDEN_GAMMA))
+    z = idx.to(torch.int64) * g
+    z = z ^ _as_int64(int(seed) & ((1 << 64) - 1))
+    z = z + g
+    z = z ^ _shr(z, 30)
+    z = z * _as_int64(int(_M1))
+    z = z ^ _shr(z, 27)
+    z = z * _as_int64(int(_M2))
+    z = z ^ _shr(z, 31)
+    return _shr(z, 11).to(torch.float64) * (2.0 ** -53)
+
+
+def uniform_field_torch(seed: int, nx: int, ny: int, nz: int, device, planes: int = 32):
+    """:func:`uniform_field` generated on ``device`` (float64, shape ``(nz, ny, nx)``),
+    ``planes`` z-planes of counters at a time."""
+    import torch
+    out = torch.empty((nz, ny, nx), dtype=torch.float64, device=device)
+    plane = nx * ny
+    for k0 in range(0, nz, planes):
+        k1 = min(nz, k0 + planes)
+        idx = torch.arange(k0 * plane, k1 * plane, dtype=torch.int64, device=device)
+        out[k0:k1] = uniform_torch(seed, idx).view(k1 - k0, ny, nx)
+    return out
+
+
 def uniform_field(seed: int, nx: int, ny: int, nz: int, chunk: int = 1 << 24) -> np.ndarray:
     """U[0,1) per node, draw index = linear offset ``i + nx*(j + ny*k)``."""
     n = nx * ny * nz

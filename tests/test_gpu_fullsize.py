@@ -10,6 +10,9 @@ for the batch, on whole problems.
   z-chunks (FP64 on the pre-scaled coefficient, and FP32): the smallest
   problems and the largest one against the oracle's own runs.
 * FP64 768^3 (byte offsets past 2^32), sampled like 512^3.
+* FP64 and FP32 1296^3: 2,176,782,336 nodes, element offsets past 2^31 (fields made
+  on the device from the same counter-based draws the host uses for the samples'
+  cones), dt from maximum(Ci) over the whole field.
 * The gradient workload (256^3, nt = 200, FP64): directional derivatives of the
   adjoint against central differences of FP64 forward runs, to 1e-6.
 """
@@ -212,3 +215,97 @@ def test_gradient_256_directional_derivatives(every):
     fd = (loss(T0 + h * w, Ci) - loss(T0 - h * w, Ci)) / (2 * h)
     ad = float(api.dot(dT0, w))
     assert abs(fd - ad) <= 1e-6 * abs(ad)
+
+
+# ------------------------------------------------------- past 2^31 elements
+N_BIG = 1296  # 1296^3 = 2,176,782,336 nodes > 2^31 = 2,147,483,648
+PTS_BIG = [(648, 648, 648), (1294, 1294, 1294), (3, 1200, 1279), (1000, 5, 1294), (1295, 600, 1285),
+           (700, 1293, 1280)]
+SEED_T_BIG = 99
+
+
+def big_fields(dev):
+    """T0 = 1.7 + U (seed 99) and the workload's Ci on the 1296^3 grid, made on the device
+    from the counter-based draws (inputs.uniform_field_torch)."""
+    n = N_BIG
+    T = inputs.uniform_field_torch(SEED_T_BIG, n, n, n, dev)
+    T += inputs.T_BASE
+    C = inputs.uniform_field_torch(inputs.SEED_CI, n, n, n, dev)
+    C.mul_(0.5).add_(1.0).mul_(1.0 / inputs.C0)
+    return T, C
+
+
+def big_cones(pts, nt):
+    """(T0, Ci) on each sample's dependency cone, from the same draws on the host."""
+    n = N_BIG
+    out = []
+    for (i, j, k) in pts:
+        i0, i1 = max(0, i - nt), min(n, i + nt + 1)
+        j0, j1 = max(0, j - nt), min(n, j + nt + 1)
+        k0, k1 = max(0, k - nt), min(n, k + nt + 1)
+        kk, jj, ii = np.meshgrid(np.arange(k0, k1), np.arange(j0, j1), np.arange(i0, i1), indexing="ij")
+        idx = (ii + n * (jj + n * kk)).astype(np.uint64)
+        T0 = inputs.T_BASE + inputs.uniform(SEED_T_BIG, idx)
+        u = inputs.uniform(inputs.SEED_CI, idx)
+        Ci = ((u * 0.5) + 1.0) * (1.0 / inputs.C0)
+        out.append(((i - i0, j - j0, k - k0), T0, Ci))
+    return out
+
+
+def cone_refs(cones, lam, dt, inv, nt):
+    """The oracle's T(nt) at each sample, run on its cone (a cone thinner than three
+    nodes holds a boundary sample, which keeps its value)."""
+    ref = []
+    for (li, lj, lk), T0, Ci in cones:
+        res = oracle.run(T0, Ci, lam, dt, *inv, nt) if min(T0.shape) >= 3 else T0
+        ref.append(res[lk, lj, li])
+    return np.array(ref)
+
+
+def test_fp64_past_2e31_elements():
+    n, nt = N_BIG, 2
+    dev = torch.device("cuda")
+    T, C = big_fields(dev)
+    assert T.numel() > 2 ** 31
+    cones = big_cones(PTS_BIG, nt)
+    # the cones' inputs are the device fields' values (same draws, same operations)
+    for (pt, (_, T0c, Cic)) in zip(PTS_BIG, cones):
+        i, j, k = pt
+        assert T0c[min(k, nt), min(j, nt), min(i, nt)] == float(T[k, j, i])
+        assert Cic[min(k, nt), min(j, nt), min(i, nt)] == float(C[k, j, i])
+    assert api.maximum(C) == float(C.max())  # the reduction over the whole field
+    dt = api.stable_dt(C, 1.0)
+    inv = inputs.inverse_spacing(n, n, n)
+    api.scale_ci(C, 1.0, dt, inv, out=C)  # in place: Cs
+    T2 = torch.empty_like(T)
+    res = api.run(T, T2, C, 1.0, dt, inv, nt, ci_scaled=True)
+    got = sample(res, PTS_BIG)
+    ref = cone_refs(cones, 1.0, dt, inv, nt)
+    assert np.max(np.abs(got - ref)) <= FP64_TOL * 2.7
+    assert api.device_error() == 0
+    del T, T2, C, res
+    torch.cuda.empty_cache()
+
+
+def test_fp32_past_2e31_elements():
+    n, nt = N_BIG, 2
+    dev = torch.device("cuda")
+    D = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    C32 = torch.empty_like(D)
+    for k0 in range(0, n, 64):  # FP64 draws a slab at a time, rounded to FP32 like the host
+        k1 = min(n, k0 + 64)
+        idx = torch.arange(k0 * n * n, k1 * n * n, dtype=torch.int64, device=dev)
+        D[k0:k1] = ((inputs.T_BASE + inputs.uniform_torch(SEED_T_BIG, idx)) - inputs.T_BASE).view(k1 - k0, n, n)
+        u = inputs.uniform_torch(inputs.SEED_CI, idx)
+        C32[k0:k1] = (((u * 0.5) + 1.0) * (1.0 / inputs.C0)).view(k1 - k0, n, n)
+    dt = api.stable_dt(C32, 1.0)
+    inv = inputs.inverse_spacing(n, n, n)
+    res = api.run(D, torch.empty_like(D), C32, 1.0, dt, inv, nt)
+    got = sample(res, PTS_BIG)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    cones = [(loc, f32(T0 - inputs.T_BASE), f32(Ci)) for loc, T0, Ci in big_cones(PTS_BIG, nt)]
+    ref = cone_refs(cones, 1.0, dt, inv, nt)
+    assert np.max(np.abs(got - ref)) <= nt * 13 * U32 * 1.0
+    assert api.device_error() == 0
+    del D, C32, res
+    torch.cuda.empty_cache()
