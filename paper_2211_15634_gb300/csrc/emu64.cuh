@@ -72,8 +72,8 @@ __device__ __forceinline__ double bitsd(unsigned long long b) {
 __device__ __forceinline__ int emu_exp(unsigned long long v) { return (int)((v >> 52) & 0x7ff); }
 
 // FP64 bit pattern nearest to K * |S| * 2^sc, S an exact signed integer
-// (sign bit not set; the caller applies the sign).  Zero for S == 0 and on
-// underflow.
+// (sign bit not set; the caller applies the sign).  Zero for S == 0; below the
+// normal range the subnormal nearest to the kept product bits (gradual underflow).
 __device__ __forceinline__ unsigned long long emu_scaled_mag(unsigned long long a, int sc, EmuK K) {
     const int lz = __clzll((long long)a);  // 64 when a == 0
     a <<= (lz & 63);
@@ -83,18 +83,32 @@ __device__ __forceinline__ unsigned long long emu_scaled_mag(unsigned long long 
     const int sh = 9 + top;
     const unsigned long long M = (P + (1ull << (sh - 1))) >> sh;  // [2^52, 2^53], rounded
     const int be = 125 + top + K.e + sc - lz + 1022;            // biased exponent - 1
+    if (be < 0) {
+        // subnormal: the mantissa in units of 2^-1074 is P * 2^(be - sh), rounded to nearest
+        // (a carry into bit 52 gives the smallest normal, as it should)
+        const int s2 = sh - be;
+        return s2 >= 64 ? 0ull : (P + (1ull << (s2 - 1))) >> s2;
+    }
     const unsigned long long bits = ((unsigned long long)(long long)be << 52) + M;
-    return (a == 0ull || be < 0) ? 0ull : bits;
+    return a == 0ull ? 0ull : bits;
 }
 
-// Exact FP64 bit pattern of |S| * 2^sc (rounded to nearest when |S| >= 2^53).
+// Exact FP64 bit pattern of |S| * 2^sc (rounded to nearest when |S| >= 2^53).  Below the
+// normal range it is the subnormal |S| * 2^(sc + 1074) in units of 2^-1074, exact: every
+// sum these routines pack is a whole multiple of 2^-1074 (sc >= -1074 on the fast and
+// window paths; on the general path at sc = emax' - 1079 < -1074 the sum is a multiple
+// of 2^(5 - emax') units, since no value of exponent >= 1 loses bits there).
 __device__ __forceinline__ unsigned long long emu_pack_mag(unsigned long long a, int sc) {
     const int lz = __clzll((long long)a);
-    a <<= (lz & 63);                                          // leading one at bit 63
-    const unsigned long long M = (a + 0x400ull) >> 11;        // [2^52, 2^53]
     const int be = 63 - lz + sc + 1022;
+    if (be < 0) {
+        const int t = sc + 1074;
+        return t >= 0 ? (a << t) : (a >> -t);
+    }
+    const unsigned long long n = a << (lz & 63);              // leading one at bit 63
+    const unsigned long long M = (n + 0x400ull) >> 11;        // [2^52, 2^53]
     const unsigned long long bits = ((unsigned long long)(long long)be << 52) + M;
-    return (a == 0ull || be < 0) ? 0ull : bits;
+    return a == 0ull ? 0ull : bits;
 }
 
 __device__ __forceinline__ unsigned long long emu_abs(long long S, unsigned long long *sign) {
@@ -183,7 +197,8 @@ __device__ __forceinline__ double emu_fast_node(unsigned long long c, unsigned l
 
 // Signed fixed-point value of FP64 bits v at scale 2^(Emax' - 1079), where
 // Emax' = max(Emax, 1) is the largest biased exponent of the group (57-bit
-// magnitudes; values 64+ binades below Emax' become 0).
+// magnitudes: a value more than 4 binades below Emax' loses low-order bits, one
+// 57 or more below becomes 0).
 __device__ __forceinline__ long long emu_fixed(unsigned long long v, int emax1) {
     const int e = (int)((v >> 52) & 0x7ff);
     const unsigned long long man = (v & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
