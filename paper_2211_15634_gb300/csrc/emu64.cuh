@@ -73,7 +73,8 @@ __device__ __forceinline__ int emu_exp(unsigned long long v) { return (int)((v >
 
 // FP64 bit pattern nearest to K * |S| * 2^sc, S an exact signed integer
 // (sign bit not set; the caller applies the sign).  Zero for S == 0; below the
-// normal range the subnormal nearest to the kept product bits (gradual underflow).
+// normal range the subnormal nearest to the kept product bits (gradual underflow);
+// Inf from 2^1024 up.
 __device__ __forceinline__ unsigned long long emu_scaled_mag(unsigned long long a, int sc, EmuK K) {
     const int lz = __clzll((long long)a);  // 64 when a == 0
     a <<= (lz & 63);
@@ -83,7 +84,8 @@ __device__ __forceinline__ unsigned long long emu_scaled_mag(unsigned long long 
     const int sh = 9 + top;
     const unsigned long long M = (P + (1ull << (sh - 1))) >> sh;  // [2^52, 2^53], rounded
     const int be = 125 + top + K.e + sc - lz + 1022;            // biased exponent - 1
-    if (be < 0) {
+    if ((unsigned)be >= 0x7feu) {  // outside the normal range (one compare on the common path)
+        if (be > 0) return a == 0ull ? 0ull : 0x7ff0000000000000ull;  // |value| >= 2^1024: Inf
         // subnormal: the mantissa in units of 2^-1074 is P * 2^(be - sh), rounded to nearest
         // (a carry into bit 52 gives the smallest normal, as it should)
         const int s2 = sh - be;
@@ -93,15 +95,17 @@ __device__ __forceinline__ unsigned long long emu_scaled_mag(unsigned long long 
     return a == 0ull ? 0ull : bits;
 }
 
-// Exact FP64 bit pattern of |S| * 2^sc (rounded to nearest when |S| >= 2^53).  Below the
-// normal range it is the subnormal |S| * 2^(sc + 1074) in units of 2^-1074, exact: every
+// Exact FP64 bit pattern of |S| * 2^sc (rounded to nearest when |S| >= 2^53; Inf from
+// 2^1024 up).  Below the normal range it is the subnormal |S| * 2^(sc + 1074) in units of
+// 2^-1074, exact: every
 // sum these routines pack is a whole multiple of 2^-1074 (sc >= -1074 on the fast and
 // window paths; on the general path at sc = emax' - 1079 < -1074 the sum is a multiple
 // of 2^(5 - emax') units, since no value of exponent >= 1 loses bits there).
 __device__ __forceinline__ unsigned long long emu_pack_mag(unsigned long long a, int sc) {
     const int lz = __clzll((long long)a);
     const int be = 63 - lz + sc + 1022;
-    if (be < 0) {
+    if ((unsigned)be >= 0x7feu) {  // outside the normal range (one compare on the common path)
+        if (be > 0) return 0x7ff0000000000000ull;  // |value| >= 2^1024: Inf (a != 0 here)
         const int t = sc + 1074;
         return t >= 0 ? (a << t) : (a >> -t);
     }

@@ -7,7 +7,9 @@
   underflow, as the oracle's IEEE arithmetic has it), of either sign, and a field of
   mixed signs around zero there (the general path with its smallest scales);
 * NaN and Inf at interior nodes spread exactly as in the oracle's evaluation: the
-  same nodes end NaN, the same end Inf, and the finite ones agree within 1e-12.
+  same nodes end NaN, the same end Inf, and the finite ones agree within 1e-12;
+* a field at the top of the range whose Laplacian overflows goes to +-Inf (then NaN)
+  where the oracle's does.
 
 The FP64 forms: the pre-scaled step with four and with two nodes per thread, the
 column kernel (odd nx), Ci as given on equal spacings (one pack and a DMUL) and on
@@ -182,3 +184,21 @@ def test_fp32_nan_and_inf_spread_like_the_oracle(nt):
     ref = oracle.run(D0.astype(np.float64), Ci.astype(np.float64), 1.0, dt, *inv, nt)
     check_nonfinite(got, ref, 1.0, nt * 13 * U32)
     assert api.device_error() == 0
+
+
+@pytest.mark.parametrize("form", ["scaled4", "scaled2", "column", "pairs"])
+def test_fp64_overflowing_laplacian_gives_inf_like_the_oracle(form):
+    """A checkerboard of 2^1023 and 1.9 * 2^1023 (one binade): the sum of the neighbours
+    minus six centres is about +-5.4 * 2^1023, past the largest double, so the interior
+    goes to +-Inf as in the oracle (whose scaled second differences overflow) - not to
+    a wrapped bit pattern - and the next step to NaN, again as in the oracle."""
+    (nx, ny, nz), inv, d2 = grid(form)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    T0 = np.where((i + j + k) % 2 == 0, 1.0, 1.9) * 2.0 ** 1023
+    Ci = inputs.ci_random(nx, ny, nz)
+    dt = d2 / Ci.max() / 6.1
+    for nt in (1, 2):
+        ref = oracle.run(T0, Ci, 1.0, dt, *inv, nt)
+        inner = ref[1:-1, 1:-1, 1:-1]
+        assert np.all(np.isinf(inner)) if nt == 1 else np.all(np.isnan(inner))
+        check_nonfinite(run64(form, T0, Ci, 1.0, dt, inv, nt), ref, 2.0 ** 1023, 1e-12)
