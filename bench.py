@@ -48,7 +48,8 @@ def parse_args():
     p.add_argument("--nt", type=int, default=100)
     p.add_argument("--no-secondary", action="store_true", help="skip FP32 / gradient / batch lines")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-steps", type=int, default=0,
+                   help="problems timed end to end (0: --steps, the device-timed step count)")
     p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint2", "batch", "step2d"],
                    default=None,
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON); "
@@ -873,14 +874,15 @@ def run_ours(args):
         bufs = (T, T2, C)
         api.solve(T0h, Cih, lam, None, inv, nt, out_host=outh, buffers=bufs)
         t0 = time.perf_counter()
-        for _ in range(max(1, args.e2e_steps)):
+        e2e_steps = max(1, args.e2e_steps if args.e2e_steps > 0 else K)
+        for _ in range(e2e_steps):
             api.solve(T0h, Cih, lam, None, inv, nt, out_host=outh, buffers=bufs)
-        serial_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
+        serial_s = (time.perf_counter() - t0) / e2e_steps
         pipe = api.SolvePipeline(tuple(T0.shape), torch.float64, lam, inv, nt)
         for _ in range(2):  # warm-up: one problem through each of the two buffer sets
             pipe.submit(T0h, Cih, outh)
         pipe.finish()
-        steps = max(1, args.e2e_steps)
+        steps = e2e_steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(steps):
