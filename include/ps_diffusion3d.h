@@ -205,8 +205,11 @@ int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double 
  * t/every - 1 when every divides t, else to one of two work grids (slots
  * nt/every and nt/every + 1; none when every == 1), never the grid the step
  * reads.  Grid slot i is states + i*grid_stride elements (grid_stride >=
- * nx*ny*nz, a multiple of 16 bytes); every grid's boundary must already equal
- * T0's (ps_diffusion3d_copy_boundary_many).  *final_slot = the slot holding
+ * nx*ny*nz, a multiple of 16 bytes).  The call sets the boundary of every
+ * grid it may write (the nt/every slots and the work grids) to T0's: where
+ * the TMA z-march serves the steps, they store the x and y faces themselves
+ * and only the two z faces are copied; else the whole boundary is copied
+ * (the caller need not prepare the grids).  *final_slot = the slot holding
  * T(nt): >= 0 a state slot, -1 / -2 work grid 0 / 1, -3 T0 itself (nt = 0).
  * Flags: PS_RUN_CI_SCALED, PS_RUN_NATIVE_F64 as for ps_diffusion3d_step_ex.
  * One launch per step from a host loop in the library. */

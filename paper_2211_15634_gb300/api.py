@@ -136,28 +136,52 @@ def copy_boundary(T2, T) -> None:
 class StateBlock:
     """``count`` state grids of T0's shape in one allocation, grid i starting
     ``stride`` elements after grid i-1 (a 16-byte boundary), every one holding
-    T0's boundary (set by one launch).  ``grids[i]`` is grid i as a tensor."""
+    T0's boundary (set by one launch; ``boundary=False`` leaves the grids unset, for
+    :func:`run_states`, which sets the boundary of every grid it writes).
+    ``grids[i]`` is grid i as a tensor."""
 
-    def __init__(self, T0, count: int):
+    def __init__(self, T0, count: int, boundary: bool = True):
         code = _code(T0)
         nx, ny, nz = _grid(T0)
         n = nx * ny * nz
         per16 = 16 // T0.element_size()
         self.stride = (n + per16 - 1) // per16 * per16
         self.flat = torch.empty(max(count, 1) * self.stride, dtype=T0.dtype, device=T0.device)
-        if count:
+        if count and boundary:
             check(_lib.load().ps_diffusion3d_copy_boundary_many(
                 self.flat.data_ptr(), count, self.stride, _field(T0, "T0", code), nx, ny, nz, code,
                 _stream(T0)))
-        self.grids = [self.flat[i * self.stride:i * self.stride + n].view(T0.shape)
-                      for i in range(count)]
+        self.grids = _GridViews(self.flat, self.stride, count, tuple(T0.shape))
 
     def ptr(self) -> int:
         return self.flat.data_ptr()
 
 
+class _GridViews:
+    """The grids of a :class:`StateBlock` as tensor views made on access (an index or a
+    slice): a block of hundreds of grids costs no host time until its grids are used,
+    so the steps that fill it are launched first."""
+
+    def __init__(self, flat, stride: int, count: int, shape):
+        self.flat, self.stride, self.count, self.shape = flat, stride, count, shape
+        self.n = shape[0] * shape[1] * shape[2]
+
+    def __len__(self) -> int:
+        return self.count
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(self.count))]
+        if i < 0:
+            i += self.count
+        if not 0 <= i < self.count:
+            raise IndexError("state grid index out of range")
+        return self.flat[i * self.stride:i * self.stride + self.n].view(self.shape)
+
+
 def state_block(T0, count: int):
-    """The ``count`` grids of a :class:`StateBlock` as a list of tensors."""
+    """The ``count`` grids of a :class:`StateBlock` (a sequence of tensors, each made on
+    access)."""
     return StateBlock(T0, count).grids
 
 
@@ -165,7 +189,9 @@ def run_states(T0, block: "StateBlock", every: int, Ci, lam: float, dt: float, i
                *, ci_scaled: bool = False) -> torch.Tensor:
     """nt steps from T0 keeping the state after step t in grid t/every - 1 of
     ``block`` when every divides t (else in its two work grids after those);
-    returns the tensor holding T(nt).  One library call (``ps_diffusion3d_run_states``)."""
+    returns the tensor holding T(nt).  The boundary of every grid it writes is set to
+    T0's (by the steps themselves where the TMA z-march serves them, the z faces by a
+    copy).  One library call (``ps_diffusion3d_run_states``)."""
     code = _code(T0)
     _same(T0, Ci)
     nx, ny, nz = _grid(T0)

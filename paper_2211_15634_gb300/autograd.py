@@ -74,7 +74,7 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
     # checkpoints (the state after every `every`-th step) and two work grids in one block,
     # all with T0's boundary; the steps write straight into them (one library call)
     nslots = nt // every
-    block = api.StateBlock(T0, nslots + (2 if every > 1 else 0))
+    block = api.StateBlock(T0, nslots + (2 if every > 1 else 0), boundary=False)  # run_states sets it
     cur = api.run_states(T0, block, every, C, lam, dt, inv, nt, ci_scaled=scaled)
     ckpts = [T0] + block.grids[:(nt - 1) // every]
     return cur, ckpts
@@ -99,7 +99,7 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     if overlap is None:
         overlap = ybar.is_cuda and nseg > 1 and seg_len > 0
     # grids for the recomputed states of a segment, with the boundary of T0
-    segs = [api.StateBlock(ckpts[0], seg_len) for _ in range(2 if overlap else 1)]
+    segs = [api.StateBlock(ckpts[0], seg_len, boundary=False) for _ in range(2 if overlap else 1)]
     main = torch.cuda.current_stream(ybar.device) if overlap else None
     side = torch.cuda.Stream(ybar.device) if overlap else None
     ready, used = {}, [None, None]  # recompute of segment s done; sweep done with buffer b

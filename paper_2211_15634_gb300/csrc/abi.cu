@@ -178,19 +178,23 @@ static int check_step_args(const void *T2, const void *T, const void *Ci, double
 }
 
 // One step; E2 / E: correction fields of the two-float state (PS_RUN_COMPENSATED).
+// write_bnd: the step also stores T's x and y boundary nodes of planes 1 .. nz-2 into T2
+// where the z-march serves it (step_writes_xy_boundary; not with PS_RUN_COMPENSATED).
 static cudaError_t enqueue_step(void *T2, const void *T, void *E2, const void *E, const void *Ci,
-                                StepCoef c, Grid3 g, int dtype, unsigned flags, cudaStream_t s) {
+                                StepCoef c, Grid3 g, int dtype, unsigned flags, cudaStream_t s,
+                                bool write_bnd = false) {
     if (dtype == PS_F64) {
         if (flags & PS_RUN_CI_SCALED)
-            return launch_step_f64_scaled((double *)T2, (const double *)T, (const double *)Ci, g, s);
+            return launch_step_f64_scaled((double *)T2, (const double *)T, (const double *)Ci, g, s,
+                                          write_bnd);
         if (flags & PS_RUN_NATIVE_F64)
             return launch_step_f64_native((double *)T2, (const double *)T, (const double *)Ci, c, g, s);
-        return launch_step_f64_fast((double *)T2, (const double *)T, (const double *)Ci, c, g, s);
+        return launch_step_f64_fast((double *)T2, (const double *)T, (const double *)Ci, c, g, s, write_bnd);
     }
     if (flags & PS_RUN_COMPENSATED)
         return launch_step_f32_comp((float *)T2, (const float *)T, (float *)E2, (const float *)E,
                                     (const float *)Ci, c, g, s);
-    return launch_step_f32((float *)T2, (const float *)T, (const float *)Ci, c, g, s);
+    return launch_step_f32((float *)T2, (const float *)T, (const float *)Ci, c, g, s, write_bnd);
 }
 
 // True when PS_RUN_TEMPORAL2 can fuse step pairs for these arguments (the mode
@@ -492,6 +496,20 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
     auto grid = [&](int slot) { return (void *)(base + (size_t)slot * (size_t)grid_stride * esz); };
     const StepCoef c = make_coef(lam, dt, _dx, _dy, _dz);
     const Grid3 g{nx, ny, nz};
+    // The boundary of every grid this call writes is T0's.  Where the z-march serves the
+    // steps they store the x and y faces themselves (in their coalesced row stores), so
+    // only the two z faces of each grid are copied here; else the whole boundary is.
+    const bool scaled = (flags & PS_RUN_CI_SCALED) != 0, native = (flags & PS_RUN_NATIVE_F64) != 0;
+    const int ngrids = nslots + nwork;
+    bool steps_bnd = true;
+    for (int k = 0; k < ngrids && steps_bnd; ++k)
+        steps_bnd = step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), T0, Ci) &&
+                    step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), grid(k), Ci);
+    if (nt > 0 && ngrids > 0) {
+        cudaError_t e = launch_copy_boundary_many(states, ngrids, grid_stride, T0, g, (int)esz,
+                                                  (cudaStream_t)stream, steps_bnd);
+        if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_run_states (boundary)");
+    }
     const void *cur = T0;
     int cur_slot = -3, work_next = 0;  // -3: T0; -1, -2: work grids 0, 1
     for (int t = 1; t <= nt; ++t) {
@@ -506,7 +524,8 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
             dst = grid(nslots + work_next);
             work_next ^= 1;
         }
-        cudaError_t e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, (cudaStream_t)stream);
+        cudaError_t e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, (cudaStream_t)stream,
+                                     steps_bnd);
         if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_run_states");
         cur = dst;
         cur_slot = slot;

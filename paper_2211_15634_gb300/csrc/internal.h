@@ -43,17 +43,23 @@ int api_fail(int status, const char *msg);
 int api_cuda_fail(cudaError_t e, const char *where);
 
 // ---- forward step kernels (step_f64.cu, step_f32.cu) ----
+// write_bnd: where the TMA z-march serves the step, it also stores the x and y boundary
+// nodes of planes 1 .. nz-2 as copies of T's (step_writes_xy_boundary tells where).
 cudaError_t launch_step_f64_native(double *T2, const double *T, const double *Ci, StepCoef c,
                                    Grid3 g, cudaStream_t s);
 cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, StepCoef c,
-                                 Grid3 g, cudaStream_t s);
+                                 Grid3 g, cudaStream_t s, bool write_bnd = false);
 cudaError_t launch_step_f32(float *T2, const float *T, const float *Ci, StepCoef c, Grid3 g,
-                            cudaStream_t s);
+                            cudaStream_t s, bool write_bnd = false);
+// True when the one-step launcher for these arguments takes the TMA z-march, so that
+// write_bnd is honoured (FP64: scaled = PS_RUN_CI_SCALED, native = PS_RUN_NATIVE_F64).
+bool step_writes_xy_boundary(int dtype, bool scaled, bool native, StepCoef c, Grid3 g, const void *T2,
+                             const void *T, const void *Ci);
 // compensated FP32 step on the two-float state (T, E) -> (T2, E2)
 cudaError_t launch_step_f32_comp(float *T2, const float *T, float *E2, const float *E, const float *Ci,
                                  StepCoef c, Grid3 g, cudaStream_t s);
 cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool write_bnd = false);
 cudaError_t launch_scale_ci(double *Cs, const double *Ci, double K, int64_t n, cudaStream_t s);
 // two steps per pass (zmarch2.cu): T2 = step(step(T)); the caller checks zmarch2_supported
 // (the same preconditions as the one-step TMA kernel)
@@ -87,7 +93,7 @@ cudaError_t launch_adjoint2_f32(float *Tbar, float *Cibar, const float *ybar, co
 // ---- helpers (misc.cu) ----
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes, cudaStream_t s);
 cudaError_t launch_copy_boundary_many(void *dst, int64_t count, int64_t gstride, const void *T,
-                                      Grid3 g, int elem_bytes, cudaStream_t s);
+                                      Grid3 g, int elem_bytes, cudaStream_t s, bool z_faces_only = false);
 cudaError_t launch_to_deviation(float *D, const double *T, double t_ref, int64_t n, cudaStream_t s);
 cudaError_t launch_from_deviation(double *T, const float *D, double t_ref, int64_t n,
                                   cudaStream_t s);

@@ -4,56 +4,53 @@
 
 namespace psd {
 
-// blockIdx.y selects the face: 0/1 z = 0 / nz-1, 2/3 y = 0 / ny-1, 4/5 x = 0 / nx-1;
-// blockIdx.z the destination grid (dst + blockIdx.z * gstride).  Edges and corners
-// belong to several faces and are written with the same value more than once.
+// blockIdx.y selects the face: 0/1 z = 0 / nz-1, 2/3 y = 0 / ny-1, 4/5 x = 0 / nx-1.
+// A thread takes face nodes t = blockIdx.x*blockDim.x + threadIdx.x (grid-stride), finds
+// each node's offset once, reads it once and stores it into all `count` destination grids
+// (dst + c * gstride): consecutive threads hold consecutive nodes of a face, so the stores
+// into one grid are coalesced wherever the face is (the z and y faces, rows of x).  Edges
+// and corners belong to several faces and are written with the same value more than once.
 template <typename E>
 __global__ void k_copy_boundary(E *__restrict__ dst, const E *__restrict__ src, int64_t nx,
-                                int64_t ny, int64_t nz, int64_t gstride) {
+                                int64_t ny, int64_t nz, int64_t gstride, int64_t count) {
     const int face = blockIdx.y;
-    dst += (int64_t)blockIdx.z * gstride;
-    const int64_t count = face < 2 ? nx * ny : (face < 4 ? nx * nz : ny * nz);
+    const int64_t rows = face < 2 ? ny : nz;            // the face is rows x cols nodes
+    const int64_t cols = face < 4 ? nx : ny;
+    const int64_t nodes = rows * cols;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nodes; t += stride) {
+        const int64_t r = t / cols, q = t - r * cols;   // one division per node, not per grid
         int64_t p;
-        if (face < 2) {
-            const int64_t k = face == 0 ? 0 : nz - 1;
-            p = t + nx * ny * k;
-        } else if (face < 4) {
-            const int64_t j = face == 2 ? 0 : ny - 1;
-            const int64_t i = t % nx, k = t / nx;
-            p = i + nx * (j + ny * k);
-        } else {
-            const int64_t i = face == 4 ? 0 : nx - 1;
-            const int64_t j = t % ny, k = t / ny;
-            p = i + nx * (j + ny * k);
-        }
-        dst[p] = src[p];
+        if (face < 2)
+            p = q + nx * (r + ny * (face == 0 ? 0 : nz - 1));
+        else if (face < 4)
+            p = q + nx * ((face == 2 ? 0 : ny - 1) + ny * r);
+        else
+            p = (face == 4 ? 0 : nx - 1) + nx * (q + ny * r);
+        const E v = src[p];
+        E *d = dst + p;
+        for (int64_t c = 0; c < count; ++c, d += gstride) *d = v;
     }
 }
 
+// z_faces_only: the two z faces (planes 0 and nz-1) alone, for grids whose x and y faces
+// the steps write themselves.
 cudaError_t launch_copy_boundary_many(void *dst, int64_t count, int64_t gstride, const void *T,
-                                      Grid3 g, int elem_bytes, cudaStream_t s) {
+                                      Grid3 g, int elem_bytes, cudaStream_t s, bool z_faces_only) {
+    if (count <= 0) return cudaSuccess;
     const int64_t maxface = g.nx * g.ny > g.nx * g.nz ? g.nx * g.ny : g.nx * g.nz;
     const int64_t mf = maxface > g.ny * g.nz ? maxface : g.ny * g.nz;
     int64_t blocks = (mf + 255) / 256;
-    const int64_t cap = (4LL * sm_count() + count - 1) / count;  // about 4 blocks per SM in all
+    const int64_t cap = 2LL * sm_count();  // six faces: about 12 blocks per SM in all
     if (blocks > cap) blocks = cap;
-    for (int64_t c0 = 0; c0 < count; c0 += 65535) {
-        const int64_t c = count - c0 < 65535 ? count - c0 : 65535;
-        const dim3 grid((unsigned)blocks, 6, (unsigned)c);
-        if (elem_bytes == 8)
-            k_copy_boundary<unsigned long long><<<grid, 256, 0, s>>>(
-                (unsigned long long *)dst + c0 * gstride, (const unsigned long long *)T, g.nx, g.ny,
-                g.nz, gstride);
-        else
-            k_copy_boundary<unsigned><<<grid, 256, 0, s>>>((unsigned *)dst + c0 * gstride,
-                                                          (const unsigned *)T, g.nx, g.ny, g.nz,
-                                                          gstride);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const dim3 grid((unsigned)blocks, z_faces_only ? 2 : 6, 1);  // faces 0 .. grid.y-1
+    if (elem_bytes == 8)
+        k_copy_boundary<unsigned long long><<<grid, 256, 0, s>>>(
+            (unsigned long long *)dst, (const unsigned long long *)T, g.nx, g.ny, g.nz, gstride, count);
+    else
+        k_copy_boundary<unsigned><<<grid, 256, 0, s>>>((unsigned *)dst, (const unsigned *)T, g.nx, g.ny,
+                                                      g.nz, gstride, count);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_copy_boundary(void *T2, const void *T, Grid3 g, int elem_bytes,

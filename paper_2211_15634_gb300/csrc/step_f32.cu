@@ -11,9 +11,9 @@ static CoefT<float> coef_f32(StepCoef c) {
 }
 
 cudaError_t launch_step_f32(float *T2, const float *T, const float *Ci, StepCoef c, Grid3 g,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool write_bnd) {
     if (step_tma_ok(g, 4, T2, T, Ci))
-        return launch_zmarch(Z_F32, T2, T, nullptr, nullptr, Ci, c, g, s);
+        return launch_zmarch(Z_F32, T2, T, nullptr, nullptr, Ci, c, g, s, write_bnd);
     return launch_step_basic<float, false>(T2, T, nullptr, nullptr, Ci, coef_f32(c), g.nx, g.ny, g.nz,
                                            sm_count(), s);
 }

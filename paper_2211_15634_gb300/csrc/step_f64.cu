@@ -24,11 +24,12 @@ static bool emu_ok(StepCoef c) {
 }
 
 cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, StepCoef c,
-                                 Grid3 g, cudaStream_t s) {
+                                 Grid3 g, cudaStream_t s, bool write_bnd) {
     if (!emu_ok(c)) return launch_step_f64_native(T2, T, Ci, c, g, s);
     const bool iso = c.ax == c.ay && c.ay == c.az;
     if (step_tma_ok(g, 8, T2, T, Ci))
-        return launch_zmarch(iso ? Z_F64_EMU_ISO : Z_F64_EMU_ANISO, T2, T, nullptr, nullptr, Ci, c, g, s);
+        return launch_zmarch(iso ? Z_F64_EMU_ISO : Z_F64_EMU_ANISO, T2, T, nullptr, nullptr, Ci, c, g, s,
+                             write_bnd);
     const EmuCoef ek{emu_const(c.dtlam * c.ax), emu_const(c.dtlam * c.ay), emu_const(c.dtlam * c.az),
                      c.dtlam, c.ax, c.ay, c.az, c.dtlam * c.ax};
     return launch_step_basic_emu(T2, T, Ci, ek, iso, g.nx, g.ny, g.nz, sm_count(), s);
@@ -36,11 +37,20 @@ cudaError_t launch_step_f64_fast(double *T2, const double *T, const double *Ci, 
 
 // Ci already scaled to dt*lam*_dx^2*Ci (isotropic grids): one DFMA per node.
 cudaError_t launch_step_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, bool write_bnd) {
     const StepCoef dummy{1.0, 1.0, 1.0, 1.0};
-    if (step_tma_ok(g, 8, T2, T, Cs)) return launch_zmarch(Z_F64_SCALED, T2, T, nullptr, nullptr, Cs, dummy, g, s);
+    if (step_tma_ok(g, 8, T2, T, Cs))
+        return launch_zmarch(Z_F64_SCALED, T2, T, nullptr, nullptr, Cs, dummy, g, s, write_bnd);
     const EmuCoef ek{};
     return launch_step_basic_emu(T2, T, Cs, ek, true, g.nx, g.ny, g.nz, sm_count(), s, true);
+}
+
+bool step_writes_xy_boundary(int dtype, bool scaled, bool native, StepCoef c, Grid3 g, const void *T2,
+                             const void *T, const void *Ci) {
+    if (dtype != PS_F64) return step_tma_ok(g, 4, T2, T, Ci);  // launch_step_f32
+    if (scaled) return step_tma_ok(g, 8, T2, T, Ci);           // launch_step_f64_scaled
+    if (native || !emu_ok(c)) return false;                     // the plain column kernel
+    return step_tma_ok(g, 8, T2, T, Ci);                        // launch_step_f64_fast
 }
 
 const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c,

@@ -176,8 +176,9 @@ ZParams zparams_for(StepCoef c, Grid3 g, int64_t pitch) {
 }
 
 cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *E2, const void *Ein, const void *Ci,
-                          StepCoef c, Grid3 g, cudaStream_t s) {
-    const ZParams p = make_params(c);
+                          StepCoef c, Grid3 g, cudaStream_t s, bool write_bnd) {
+    ZParams p = make_params(c);
+    p.write_bnd = (write_bnd && mode != Z_F32_COMP) ? 1 : 0;
     const int kchunk = launch_override(PS_OVERRIDE_KCHUNK);
     const bool positive = c.dtlam * c.ax > 0 && c.dtlam * c.ay > 0 && c.dtlam * c.az > 0;
     switch (mode) {

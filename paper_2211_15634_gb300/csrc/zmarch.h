@@ -25,6 +25,7 @@ struct ZParams {
     int kchunk, ntx;
     EmuCoef ek;
     float fdtlam, fax, fay, faz;
+    int write_bnd;  // also store the x and y boundary nodes of the output planes (T's values)
 };
 
 // True when the TMA path can serve this grid and these pointers.
@@ -54,9 +55,10 @@ unsigned adjoint_device_error(bool clear);
 cudaError_t launch_adjoint_scaled(double *Tbar, double *Csbar, const double *ybar, const double *T,
                                   const double *Cs, Grid3 g, cudaStream_t s);
 // One step of the TMA z-march in `mode`; E2 / Ein: the correction fields of the
-// two-float state (Z_F32_COMP only, else unused).
+// two-float state (Z_F32_COMP only, else unused).  write_bnd: also store the x and y
+// boundary nodes of planes 1 .. nz-2 as copies of T's (not with Z_F32_COMP).
 cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *E2, const void *Ein, const void *Ci,
-                          StepCoef c, Grid3 g, cudaStream_t s);
+                          StepCoef c, Grid3 g, cudaStream_t s, bool write_bnd = false);
 unsigned zmarch_device_error(bool clear);
 
 }  // namespace psd

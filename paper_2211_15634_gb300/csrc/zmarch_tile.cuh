@@ -307,8 +307,19 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                     if (gx >= 1 && gx <= p.nx - 2) {
                         T2[base + i] = vget<V, E>(out, i);
                         if constexpr (kComp) E2[base + i] = vget<V, E>(cv, i);
+                    } else if (!kComp && p.write_bnd && gx <= p.nx - 1) {
+                        T2[base + i] = vget<V, E>(qc, i);  // x = 0 or nx-1: T's boundary value
                     }
                 }
+            }
+        } else if (!kComp && p.write_bnd && gy <= p.ny - 1) {
+            // y = 0 or ny-1: a boundary row, stored as T's (its values are in the ring)
+            if (gx0 + PX - 1 <= p.nx - 1) {
+                *(V *)(T2 + base) = qc;
+            } else {
+#pragma unroll
+                for (int i = 0; i < PX; ++i)
+                    if (gx0 + i <= p.nx - 1) T2[base + i] = vget<V, E>(qc, i);
             }
         }
         if (!ok) {

@@ -442,6 +442,44 @@ def test_state_block_copies_boundary_into_every_grid(dtype):
         assert np.array_equal(gh[~inner], Th[~inner]) and np.all(gh[inner] == -1.0)
 
 
+RUN_STATES_FORMS = {  # name: (shape nx, ny, nz; dtype; pre-scaled?)
+    "f64_scaled4": ((68, 21, 13), torch.float64, True),
+    "f64_scaled2": ((66, 19, 13), torch.float64, True),
+    "f64_as_given": ((68, 21, 13), torch.float64, False),
+    "f32": ((68, 19, 13), torch.float32, False),
+    "f64_column": ((67, 21, 13), torch.float64, True),  # odd nx: the plain column kernel
+}
+
+
+@pytest.mark.parametrize("every", [1, 4])
+@pytest.mark.parametrize("form", list(RUN_STATES_FORMS))
+def test_run_states_sets_the_boundary_of_unprepared_grids(form, every):
+    """State grids handed to run_states with NaN everywhere: every grid the call writes
+    ends, boundary included, bit for bit equal to the step loop's state (the z-march
+    steps store the x and y faces, the call copies the z faces; the column kernel's
+    grids get the whole boundary copied)."""
+    (nx, ny, nz), dtype, scaled = RUN_STATES_FORMS[form]
+    nt = 9
+    T0h, Ci, lam, dt, inv = iso_problem(nx, ny, nz)
+    T0 = to_dev(T0h, dtype)
+    C = to_dev(Ci, dtype)
+    if scaled:
+        C = api.scale_ci(C, lam, dt, inv)
+    block = api.StateBlock(T0, nt // every + (2 if every > 1 else 0), boundary=False)
+    block.flat.fill_(float("nan"))
+    final = api.run_states(T0, block, every, C, lam, dt, inv, nt, ci_scaled=scaled)
+    a, b = T0.clone(), T0.clone()
+    cur = a
+    for t in range(1, nt + 1):
+        dst = b if cur is a else a
+        api.step(dst, cur, C, lam, dt, inv, ci_scaled=scaled)
+        cur = dst
+        if t % every == 0:
+            assert torch.equal(block.grids[t // every - 1], cur), t
+    assert torch.equal(final, cur)
+    assert api.device_error() == 0
+
+
 @pytest.mark.parametrize("nt,every", [(0, 1), (1, 1), (7, 1), (7, 3), (9, 3), (5, 8), (12, 5)])
 def test_run_states_keeps_the_states_of_a_step_loop(nt, every):
     """The library's state-keeping time loop: slot t/every - 1 holds the state after
