@@ -98,7 +98,7 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     seg_len = max(0, min(every, nt) - 1)  # recomputed states per segment
     if overlap is None:
         overlap = ybar.is_cuda and nseg > 1 and seg_len > 0
-    # grids for the recomputed states of a segment, with the boundary of T0
+    # grids for the recomputed states of a segment (run_states gives them T0's boundary)
     segs = [api.StateBlock(ckpts[0], seg_len, boundary=False) for _ in range(2 if overlap else 1)]
     main = torch.cuda.current_stream(ybar.device) if overlap else None
     side = torch.cuda.Stream(ybar.device) if overlap else None
@@ -114,7 +114,7 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
             api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
             return
         with torch.cuda.stream(side):
-            side.wait_stream(main)  # the checkpoints, Cs and the buffers' boundaries
+            side.wait_stream(main)  # the checkpoints and Cs are final
             if used[b] is not None:
                 side.wait_event(used[b])  # the sweep no longer reads this buffer
             api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
