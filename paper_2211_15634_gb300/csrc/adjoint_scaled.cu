@@ -50,6 +50,15 @@ __device__ __forceinline__ long long adjs_fixed(unsigned long long v, int E) {
 // Exact-when-possible FP64 of the integer S at scale 2^sc.
 __device__ __forceinline__ double adjs_pack(long long S, int sc) { return emu_pack(S, sc); }
 
+// The same for a scale at which every packed sum is normal (or zero): |S| < 2^61 at
+// scale 2^(E-1079) has an exponent between E - 57 and E + 3, so for E in [57, 2042] the
+// range checks can go (the CTA-uniform scale picks this form for the whole plane).
+__device__ __forceinline__ double adjs_pack_normal(long long S, int sc) {
+    unsigned long long sg;
+    const unsigned long long a = emu_abs(S, &sg);
+    return bitsd(emu_pack_mag_normal(a, sc) | sg);
+}
+
 static __device__ __noinline__ double adjs_lap_general(unsigned long long c, unsigned long long xm,
                                                        unsigned long long xp, unsigned long long ym,
                                                        unsigned long long yp, unsigned long long zm,
@@ -250,7 +259,10 @@ k_adjoint_scaled(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
             const long long S1 = ((wc0 + wr) + (wu.y + wd.y)) + (wm1 + wp1) - 6 * wc1;
             const int sc = Esc - 1079;
             double2 tb;
-            if (Esc == 0x7ff) {  // a non-finite w in this CTA's march: report NaN
+            if (Esc >= 57 && Esc <= 2042) {  // CTA-uniform: the packed sums are normal
+                tb.x = yc.x + adjs_pack_normal(S0, sc);
+                tb.y = yc.y + adjs_pack_normal(S1, sc);
+            } else if (Esc == 0x7ff) {  // a non-finite w in this CTA's march: report NaN
                 tb.x = tb.y = __longlong_as_double(0x7ff8000000000000ll);
             } else {
                 tb.x = yc.x + adjs_pack(S0, sc);
@@ -275,12 +287,15 @@ k_adjoint_scaled(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
                 const unsigned long long u0 = dbits(tu.x), u1 = dbits(tu.y), d0 = dbits(td.x),
                                          d1 = dbits(td.y), m0b = dbits(tm.x), m1b = dbits(tm.y),
                                          p0 = dbits(tp.x), p1 = dbits(tp.y);
-                const unsigned hc0 = (unsigned)(c0 >> 32);
+                unsigned hc0 = (unsigned)(c0 >> 32);
                 unsigned hw[11] = {(unsigned)(xl >> 32), (unsigned)(xr >> 32), (unsigned)(u0 >> 32),
                                    (unsigned)(d0 >> 32), (unsigned)(m0b >> 32), (unsigned)(p0 >> 32),
                                    (unsigned)(u1 >> 32), (unsigned)(d1 >> 32), (unsigned)(m1b >> 32),
                                    (unsigned)(p1 >> 32), (unsigned)(c1 >> 32)};
                 if (!all_in) {  // values of unstored nodes must not force the general path
+                    // a lane that stores neither node (past the grid: zeros) votes for the fast
+                    // path: its reference is 1.0's word (its outputs are never stored)
+                    if (!m0 && !m1) hc0 = 0x3ff00000u;
                     if (!m0) hw[0] = hw[2] = hw[3] = hw[4] = hw[5] = hc0;
                     if (!m1) hw[1] = hw[6] = hw[7] = hw[8] = hw[9] = hc0;
                     if (!m0 && !m1) hw[10] = hc0;
@@ -295,8 +310,8 @@ k_adjoint_scaled(const __grid_constant__ CUtensorMap tmT, const __grid_constant_
                     const unsigned long long flip = c0 & 0x8000000000000000ull;  // negative: minus
                     unsigned long long g0, g1;
                     const unsigned long long a0 = emu_abs(S0t, &g0), a1 = emu_abs(S1t, &g1);
-                    L0 = bitsd(emu_pack_mag(a0, sct) | (g0 ^ flip));
-                    L1 = bitsd(emu_pack_mag(a1, sct) | (g1 ^ flip));
+                    L0 = bitsd(emu_pack_mag_normal(a0, sct) | (g0 ^ flip));
+                    L1 = bitsd(emu_pack_mag_normal(a1, sct) | (g1 ^ flip));
                 } else {
                     L0 = m0 ? adjs_lap_general(c0, xl, c1, u0, d0, m0b, p0) : 0.0;
                     L1 = m1 ? adjs_lap_general(c1, c0, xr, u1, d1, m1b, p1) : 0.0;

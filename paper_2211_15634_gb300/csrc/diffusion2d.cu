@@ -157,7 +157,12 @@ k_ymarch2d(typename M2D<MODE>::E *__restrict__ T2, const typename M2D<MODE>::E *
             // one same-binade check over this lane's distinct values (words of nodes that
             // are not written replaced by the reference, so they cannot force the general
             // path); the whole warp takes the short path together when all lanes pass
-            const unsigned hc = (unsigned)(dbits(c[0]) >> 32);
+            bool any_wr = false;
+#pragma unroll
+            for (int i = 0; i < PX; ++i) any_wr = any_wr || wr[i];
+            // a lane that writes none of its nodes (past the grid) votes for the fast path:
+            // its reference is 1.0's word (its outputs are never stored)
+            const unsigned hc = any_wr ? (unsigned)(dbits(c[0]) >> 32) : 0x3ff00000u;
             unsigned hw[3 * PX + 1];
             hw[0] = wr[0] ? (unsigned)(dbits(left) >> 32) : hc;
             hw[1] = wr[PX - 1] ? (unsigned)(dbits(right) >> 32) : hc;

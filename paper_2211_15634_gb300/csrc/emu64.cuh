@@ -95,6 +95,18 @@ __device__ __forceinline__ unsigned long long emu_scaled_mag(unsigned long long 
     return a == 0ull ? 0ull : bits;
 }
 
+// The FP64 bit pattern of |S| * 2^sc for a result known to be normal or zero (rounded to
+// nearest when |S| >= 2^53): the fast paths, whose common binade lies in the exponent range
+// that emu_same_binade_hi admits, so no range check is spent on them.
+__device__ __forceinline__ unsigned long long emu_pack_mag_normal(unsigned long long a, int sc) {
+    const int lz = __clzll((long long)a);
+    const unsigned long long n = a << (lz & 63);              // leading one at bit 63
+    const unsigned long long M = (n + 0x400ull) >> 11;        // [2^52, 2^53]
+    const int be = 63 - lz + sc + 1022;
+    const unsigned long long bits = ((unsigned long long)(long long)be << 52) + M;
+    return a == 0ull ? 0ull : bits;
+}
+
 // Exact FP64 bit pattern of |S| * 2^sc (rounded to nearest when |S| >= 2^53; Inf from
 // 2^1024 up).  Below the normal range it is the subnormal |S| * 2^(sc + 1074) in units of
 // 2^-1074, exact: every
@@ -133,19 +145,28 @@ __device__ __forceinline__ unsigned lop_xor_or(unsigned a, unsigned b, unsigned 
     return r;
 }
 
+// Biased exponents of the binades the fast paths take: a sum of seven values of one
+// binade e, packed at scale 2^(e - 1075), is then a normal double (or zero) - its
+// exponent lies between e - 53 and e + 3 - so the fast packs need no range check.
+// Values outside (below 2^-970 or from 2^1020) take the general path.
+__device__ __forceinline__ bool emu_fast_exponent(unsigned hc) {
+    return ((hc >> 20) & 0x7ffu) - 53u <= 2042u - 53u;
+}
+
 // True when every high word in h shares the sign and exponent field (top 12
-// bits) with hc and hc is not Inf/NaN: then the FP64 values they belong to
-// lie in one binade and their bit patterns differ by whole ulps.
+// bits) with hc and hc's exponent is in the fast range (emu_fast_exponent, which
+// leaves out Inf/NaN): then the FP64 values they belong to lie in one binade and
+// their bit patterns differ by whole ulps.
 template <int N>
 __device__ __forceinline__ bool emu_same_binade_hi(const unsigned (&h)[N], unsigned hc) {
     unsigned d = lop_xor_or(h[0], h[1], hc);
 #pragma unroll
     for (int i = 2; i < N; ++i) d = lop_or_xor(d, h[i], hc);
-    return ((d & 0xfff00000u) | ((hc & 0x7ff00000u) == 0x7ff00000u)) == 0u;
+    return (d & 0xfff00000u) == 0u && emu_fast_exponent(hc);
 }
 
-// True when the six neighbours share sign and exponent with the centre and the
-// centre is finite.
+// True when the six neighbours share sign and exponent with the centre and that
+// exponent is in the fast range (emu_fast_exponent).
 __device__ __forceinline__ bool emu_same_binade(unsigned long long c, unsigned long long xm,
                                                 unsigned long long xp, unsigned long long ym,
                                                 unsigned long long yp, unsigned long long zm,
@@ -154,7 +175,7 @@ __device__ __forceinline__ bool emu_same_binade(unsigned long long c, unsigned l
     const unsigned d = ((unsigned)(xm >> 32) ^ hc) | ((unsigned)(xp >> 32) ^ hc) |
                        ((unsigned)(ym >> 32) ^ hc) | ((unsigned)(yp >> 32) ^ hc) |
                        ((unsigned)(zm >> 32) ^ hc) | ((unsigned)(zp >> 32) ^ hc);
-    return ((d & 0xfff00000u) == 0u) && ((hc & 0x7ff00000u) != 0x7ff00000u);
+    return ((d & 0xfff00000u) == 0u) && emu_fast_exponent(hc);
 }
 
 // L (as FP64 bits, with sign) from exact per-axis sums at scale 2^sc.
@@ -193,7 +214,7 @@ __device__ __forceinline__ double emu_fast_node(unsigned long long c, unsigned l
     if (kDmul && kIso) {
         unsigned long long sg;
         const unsigned long long a = emu_abs(sx + sy + sz, &sg);
-        const double Sd = bitsd(emu_pack_mag(a, sc) | (sg ^ flip));
+        const double Sd = bitsd(emu_pack_mag_normal(a, sc) | (sg ^ flip));
         return fma(ci * k.Kx, Sd, bitsd(c));
     }
     return fma(ci, emu_L<kIso>(sx, sy, sz, sc, flip, k), bitsd(c));
@@ -288,7 +309,7 @@ __device__ __forceinline__ double emu_fast_node_scaled(unsigned long long c, uns
     const unsigned long long flip = c & 0x8000000000000000ull;  // negative values: minus
     unsigned long long sg;
     const unsigned long long a = emu_abs(S, &sg);
-    return fma(cs, bitsd(emu_pack_mag(a, (e ? e : 1) - 1075) | (sg ^ flip)), bitsd(c));
+    return fma(cs, bitsd(emu_pack_mag_normal(a, e - 1075) | (sg ^ flip)), bitsd(c));
 }
 
 static __device__ __noinline__ double emu_general_node_scaled(unsigned long long c, unsigned long long xm,

@@ -23,7 +23,7 @@ namespace psd {
 
 __device__ unsigned g_zmarch_error;  // set when an mbarrier wait times out
 
-template <int MODE, int BY, int NST>
+template <int MODE, int BY, int NST, bool kBnd>
 __global__ void __launch_bounds__(32 * BY, 1)
 k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmC,
          const __grid_constant__ CUtensorMap tmE, void *__restrict__ T2v, void *__restrict__ E2v,
@@ -34,7 +34,7 @@ k_zmarch(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtens
     const int Y0 = (int)(blockIdx.x / p.ntx) * BY;
     const int k0 = 1 + (int)blockIdx.y * p.kchunk;
     const int k1 = (int)min((int64_t)k0 + p.kchunk, p.nz - 1);  // output planes [k0, k1)
-    zmarch_tile<MODE, BY, NST>(&tmT, &tmC, T2v, E2v, p, X0, Y0, k0, k1, &g_zmarch_error, &tmE);
+    zmarch_tile<MODE, BY, NST, 32, kBnd>(&tmT, &tmC, T2v, E2v, p, X0, Y0, k0, k1, &g_zmarch_error, &tmE);
 }
 
 // Failure-path self-test: one CTA waits on an mbarrier that nothing ever arrives on.
@@ -102,7 +102,7 @@ bool step_tma_ok(Grid3 g, int esz, const void *a, const void *b, const void *c) 
     return launch_override(PS_OVERRIDE_STEP_PLAIN) != 1 && zmarch_supported(g, esz, a, b, c);
 }
 
-template <int MODE, int BY, int NST>
+template <int MODE, int BY, int NST, bool kBnd = false>
 static cudaError_t launch_zmarch_t(void *T2, const void *T, void *E2, const void *Ein, const void *Ci,
                                    Grid3 g, ZParams p, int kchunk, cudaStream_t s) {
     using E = typename ZTraits<MODE>::E;
@@ -113,7 +113,7 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *E2, const void
     constexpr size_t smem = NST * (TBA + CBA + EBA) + NST * 8;
     static unsigned attr_gen[64] = {0};
     cudaError_t ae;
-    if (!set_smem_attr_once((const void *)k_zmarch<MODE, BY, NST>, (int)smem, attr_gen, &ae)) return ae;
+    if (!set_smem_attr_once((const void *)k_zmarch<MODE, BY, NST, kBnd>, (int)smem, attr_gen, &ae)) return ae;
     CUtensorMap mT, mC, mE;
     if (!make_tensor_map_3d(&mT, T, sizeof(E), g, W, H) ||
         !make_tensor_map_3d(&mC, Ci, sizeof(E), g, BX, BY))
@@ -144,8 +144,8 @@ static cudaError_t launch_zmarch_t(void *T2, const void *T, void *E2, const void
     p.pitch = g.nx;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    return launch_pdl(k_zmarch<MODE, BY, NST>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem, s,
-                      mT, mC, mE, T2, E2, p);
+    return launch_pdl(k_zmarch<MODE, BY, NST, kBnd>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem,
+                      s, mT, mC, mE, T2, E2, p);
 }
 
 static ZParams make_params(StepCoef c) {
@@ -175,32 +175,42 @@ ZParams zparams_for(StepCoef c, Grid3 g, int64_t pitch) {
     return p;
 }
 
+// One mode's launch, with the boundary-writing instantiation where asked (the forms
+// that state-keeping time loops use; never the two-float step).
+template <int MODE, int BY, int NST>
+static cudaError_t launch_zmarch_b(void *T2, const void *T, void *E2, const void *Ein, const void *Ci, Grid3 g,
+                                   ZParams p, int kchunk, cudaStream_t s, bool write_bnd) {
+    if (MODE != Z_F32_COMP && write_bnd)
+        return launch_zmarch_t<MODE, BY, NST, MODE != Z_F32_COMP>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+    return launch_zmarch_t<MODE, BY, NST, false>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+}
+
 cudaError_t launch_zmarch(int mode, void *T2, const void *T, void *E2, const void *Ein, const void *Ci,
                           StepCoef c, Grid3 g, cudaStream_t s, bool write_bnd) {
-    ZParams p = make_params(c);
-    p.write_bnd = (write_bnd && mode != Z_F32_COMP) ? 1 : 0;
+    const ZParams p = make_params(c);
     const int kchunk = launch_override(PS_OVERRIDE_KCHUNK);
     const bool positive = c.dtlam * c.ax > 0 && c.dtlam * c.ay > 0 && c.dtlam * c.az > 0;
+    const bool wb = write_bnd;
     switch (mode) {
         case Z_F64_EMU_ISO:
         case Z_F64_EMU_ANISO:
-            if (!positive) return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+            if (!positive) return launch_zmarch_b<Z_F64_NATIVE, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s, wb);
             // isotropic grids: fma(Ci*K, S, T), two FP64 ops and the fewest integer ops
             // (measured faster than one DFMA after a 64 x 64-bit high multiply by K)
             if (mode == Z_F64_EMU_ISO)
-                return launch_zmarch_t<Z_F64_EMU_ISO_DMUL, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
-            return launch_zmarch_t<Z_F64_EMU_ANISO, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+                return launch_zmarch_b<Z_F64_EMU_ISO_DMUL, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s, wb);
+            return launch_zmarch_b<Z_F64_EMU_ANISO, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s, wb);
         case Z_F64_NATIVE:
-            return launch_zmarch_t<Z_F64_NATIVE, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+            return launch_zmarch_b<Z_F64_NATIVE, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s, wb);
         case Z_F64_SCALED:
             // four nodes per thread (4-row tiles, 128 threads) where rows allow 32-byte
             // accesses: measured 2-3% faster at 512^3 and 768^3 than two per thread
             // (8-row tiles of four per thread, at two CTAs per SM, were 15% slower)
             if (f64_scaled_wide(g, T2, T, Ci))
-                return launch_zmarch_t<Z_F64_SCALED4, 4, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
-            return launch_zmarch_t<Z_F64_SCALED, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+                return launch_zmarch_b<Z_F64_SCALED4, 4, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s, wb);
+            return launch_zmarch_b<Z_F64_SCALED, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s, wb);
         case Z_F32:
-            return launch_zmarch_t<Z_F32, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
+            return launch_zmarch_b<Z_F32, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s, wb);
         case Z_F32_COMP:
             return launch_zmarch_t<Z_F32_COMP, 8, 4>(T2, T, E2, Ein, Ci, g, p, kchunk, s);
     }

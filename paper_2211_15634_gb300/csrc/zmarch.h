@@ -25,7 +25,6 @@ struct ZParams {
     int kchunk, ntx;
     EmuCoef ek;
     float fdtlam, fax, fay, faz;
-    int write_bnd;  // also store the x and y boundary nodes of the output planes (T's values)
 };
 
 // True when the TMA path can serve this grid and these pointers.

@@ -64,13 +64,14 @@ __device__ __forceinline__ E vget(const V &v, int i) {
 }
 
 // One CTA (BY * LPR threads): output planes [k0, k1) of the BX x BY tile at (X0, Y0) (the
-// tile's node coordinates, boundary included; only interior nodes are written).
+// tile's node coordinates, boundary included; only interior nodes are written, and with
+// kBnd the x and y boundary nodes of those planes too, as copies of T's).
 // tmT / tmC: tensor maps of T (box W x H) and Ci (box BX x BY), in parameter or
 // global memory.  Rows are p.pitch elements apart, planes p.pitch * p.ny.
 // Z_F32_COMP (two-float state D + E): tmE maps E (box W x H, staged with T in the same
 // stage) and E2v receives the new correction field; other modes ignore both.
 // A timed-out wait sets bit 0 of *err and the CTA leaves after draining its copies.
-template <int MODE, int BY, int NST, int LPR = 32>
+template <int MODE, int BY, int NST, int LPR = 32, bool kBnd = false>
 __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtensorMap *tmC,
                                             void *__restrict__ T2v, void *__restrict__ E2v,
                                             const ZParams &p, int X0, int Y0, int k0, int k1,
@@ -213,7 +214,7 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                 }
 #pragma unroll
                 for (int i = 1; i < PX; ++i) hw[1 + 4 * PX + i] = (unsigned)(c[i] >> 32);
-                const unsigned hc = (unsigned)(c[0] >> 32);
+                unsigned hc = (unsigned)(c[0] >> 32);
                 if (!all_x) {
                     // Lanes at the grid's x edges: a node that is not stored (x = 0,
                     // x = nx-1, or past the grid where TMA filled zeros) must not
@@ -222,6 +223,12 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                     bool use[PX];
 #pragma unroll
                     for (int i = 0; i < PX; ++i) use[i] = gx0 + i >= 1 && gx0 + i <= p.nx - 2;
+                    bool any_use = false;
+#pragma unroll
+                    for (int i = 0; i < PX; ++i) any_use = any_use || use[i];
+                    // a lane that stores none of its nodes (past the grid: zeros) votes for the
+                    // fast path: its reference is 1.0's word (its outputs are never stored)
+                    if (!any_use) hc = 0x3ff00000u;
                     if (!use[0]) hw[0] = hc;       // left: x-neighbour of node 0 only
                     if (!use[PX - 1]) hw[1] = hc;  // right: x-neighbour of the last node only
 #pragma unroll
@@ -307,12 +314,12 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                     if (gx >= 1 && gx <= p.nx - 2) {
                         T2[base + i] = vget<V, E>(out, i);
                         if constexpr (kComp) E2[base + i] = vget<V, E>(cv, i);
-                    } else if (!kComp && p.write_bnd && gx <= p.nx - 1) {
+                    } else if (kBnd && !kComp && gx <= p.nx - 1) {
                         T2[base + i] = vget<V, E>(qc, i);  // x = 0 or nx-1: T's boundary value
                     }
                 }
             }
-        } else if (!kComp && p.write_bnd && gy <= p.ny - 1) {
+        } else if (kBnd && !kComp && gy <= p.ny - 1) {
             // y = 0 or ny-1: a boundary row, stored as T's (its values are in the ring)
             if (gx0 + PX - 1 <= p.nx - 1) {
                 *(V *)(T2 + base) = qc;
