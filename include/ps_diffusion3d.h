@@ -211,8 +211,11 @@ int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double 
  * and only the two z faces are copied; else the whole boundary is copied
  * (the caller need not prepare the grids).  *final_slot = the slot holding
  * T(nt): >= 0 a state slot, -1 / -2 work grid 0 / 1, -3 T0 itself (nt = 0).
- * Flags: PS_RUN_CI_SCALED, PS_RUN_NATIVE_F64 as for ps_diffusion3d_step_ex.
- * One launch per step from a host loop in the library. */
+ * Flags: PS_RUN_CI_SCALED, PS_RUN_NATIVE_F64 as for ps_diffusion3d_step_ex;
+ * PS_RUN_GRAPH captures the boundary copy and the nt launches into a CUDA
+ * graph on the first call for this argument set (pointers, stride, every,
+ * coefficients, sizes) and replays it afterwards.  Else one launch per step
+ * from a host loop in the library. */
 int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride, int every,
                               const void *Ci, double lam, double dt, double _dx, double _dy,
                               double _dz, int64_t nx, int64_t ny, int64_t nz, int nt, int dtype,

@@ -64,10 +64,12 @@ def coefficient(Ci, lam, dt, inv):
     return Ci, False
 
 
-def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
+def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True):
     """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...]).
 
-    ``coef`` = :func:`coefficient` (computed here when None)."""
+    ``coef`` = :func:`coefficient` (computed here when None).  ``graph``: replay the
+    state-keeping loop from the library's graph cache (keyed by the buffers, which the
+    caching allocator hands back unchanged in a loop of gradients)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     if nt == 0:
         return T0.clone(), [T0]
@@ -75,20 +77,21 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None):
     # all with T0's boundary; the steps write straight into them (one library call)
     nslots = nt // every
     block = api.StateBlock(T0, nslots + (2 if every > 1 else 0), boundary=False)  # run_states sets it
-    cur = api.run_states(T0, block, every, C, lam, dt, inv, nt, ci_scaled=scaled)
+    cur = api.run_states(T0, block, every, C, lam, dt, inv, nt, ci_scaled=scaled, graph=graph)
     ckpts = [T0] + block.grids[:(nt - 1) // every]
     return cur, ckpts
 
 
 def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None,
-                          overlap=None):
+                          overlap=None, graph=True):
     """Reverse sweep; returns (dL/dT0, dL/dCi).  ``pairs``: take the transposed
     steps two per launch where ``api.adjoint2`` applies (default off).  ``overlap``
     (default on for CUDA tensors with more than one segment to recompute): recompute
     segment s-1's states on a side stream while segment s's transposed steps run,
     into the second of two segment buffers (one more segment of memory); the kernels
     and their order on every buffer are unchanged, so the gradient is bit for bit
-    the one-stream sweep's."""
+    the one-stream sweep's.  ``graph``: the segments' recomputes are replayed from the
+    graph cache, as in :func:`forward_checkpointed`."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     pairs = bool(pairs) and not scaled and api.adjoint2_supported(ybar_nt)
     ybar = ybar_nt.contiguous().clone()
@@ -111,13 +114,13 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
             return
         b = s % len(segs)
         if not overlap:
-            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
+            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph)
             return
         with torch.cuda.stream(side):
             side.wait_stream(main)  # the checkpoints and Cs are final
             if used[b] is not None:
                 side.wait_event(used[b])  # the sweep no longer reads this buffer
-            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled)
+            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph)
             ready[s] = torch.cuda.Event()
             ready[s].record(side)
 

@@ -241,9 +241,11 @@ static cudaError_t enqueue_run(void *T, void *T2, void *comp, const void *Ci, St
 }
 
 // ---------------------------------------------------------------- graphs
+// device, four pointers, lam, dt, _dx, _dy, _dz, nx, ny, nz, nt, dtype, flags (with a marker
+// bit per kind of loop), and one more size (the grid stride of a state-keeping loop)
 using GraphKey = std::tuple<int, const void *, const void *, const void *, const void *, double,
                             double, double, double, double, int64_t, int64_t, int64_t, int, int,
-                            unsigned>;
+                            unsigned, int64_t>;
 struct CachedGraph {
     cudaGraphExec_t exec;
     uint64_t last_use;  // value of g_graph_clock at the last replay
@@ -320,7 +322,7 @@ static int run_graph(void *T, void *T2, void *comp, const void *Ci, double lam, 
                      double _dx, double _dy, double _dz, Grid3 g, int nt, int dtype,
                      unsigned flags, cudaStream_t s) {
     const GraphKey key{current_device(), T, T2, comp, Ci, lam, dt, _dx, _dy, _dz, g.nx, g.ny, g.nz,
-                       nt, dtype, flags & ~PS_RUN_GRAPH};
+                       nt, dtype, flags & ~PS_RUN_GRAPH, 0};
     return graph_replay(
         key,
         [&](cudaStream_t cs) {
@@ -471,6 +473,53 @@ int ps_diffusion3d_copy_boundary_many(void *dst, int64_t count, int64_t grid_str
     return PS_OK;
 }
 
+// The grid slot holding the state after step t of a state-keeping loop (see
+// ps_diffusion3d_run_states), and the enqueue of its boundary copy and steps.
+namespace psd {
+static int states_slot_after(int t, int every, int &cur_slot, int &work_next) {
+    int slot;
+    if (t % every == 0) {
+        slot = t / every - 1;
+    } else {  // a work grid, never the one this step reads
+        if (cur_slot == -1 - work_next) work_next ^= 1;
+        slot = -1 - work_next;
+        work_next ^= 1;
+    }
+    cur_slot = slot;
+    return slot;
+}
+
+static cudaError_t enqueue_run_states(const void *T0, char *base, int64_t grid_stride, size_t esz, int every,
+                                      const void *Ci, StepCoef c, Grid3 g, int nt, int dtype, unsigned flags,
+                                      cudaStream_t s) {
+    const int nslots = nt / every, nwork = (every > 1 && nt > 0) ? 2 : 0;
+    auto grid = [&](int slot) { return (void *)(base + (size_t)slot * (size_t)grid_stride * esz); };
+    // The boundary of every grid this call writes is T0's.  Where the z-march serves the
+    // steps they store the x and y faces themselves (in their coalesced row stores), so
+    // only the two z faces of each grid are copied here; else the whole boundary is.
+    const bool scaled = (flags & PS_RUN_CI_SCALED) != 0, native = (flags & PS_RUN_NATIVE_F64) != 0;
+    const int ngrids = nslots + nwork;
+    bool steps_bnd = true;
+    for (int k = 0; k < ngrids && steps_bnd; ++k)
+        steps_bnd = step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), T0, Ci) &&
+                    step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), grid(k), Ci);
+    if (nt > 0 && ngrids > 0) {
+        cudaError_t e = launch_copy_boundary_many(base, ngrids, grid_stride, T0, g, (int)esz, s, steps_bnd);
+        if (e != cudaSuccess) return e;
+    }
+    const void *cur = T0;
+    int cur_slot = -3, work_next = 0;  // -3: T0; -1, -2: work grids 0, 1
+    for (int t = 1; t <= nt; ++t) {
+        const int slot = states_slot_after(t, every, cur_slot, work_next);
+        void *dst = slot >= 0 ? grid(slot) : grid(nslots + (-1 - slot));
+        cudaError_t e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, s, steps_bnd);
+        if (e != cudaSuccess) return e;
+        cur = dst;
+    }
+    return cudaSuccess;
+}
+}  // namespace psd
+
 int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride, int every,
                               const void *Ci, double lam, double dt, double _dx, double _dy,
                               double _dz, int64_t nx, int64_t ny, int64_t nz, int nt, int dtype,
@@ -479,7 +528,8 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
     if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
     if (every < 1) return fail(PS_ERR_ARG, "every = %d < 1", every);
     if (!final_slot) return fail(PS_ERR_ARG, "final_slot is NULL");
-    if (flags & ~(PS_RUN_CI_SCALED | PS_RUN_NATIVE_F64)) return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
+    if (flags & ~(PS_RUN_CI_SCALED | PS_RUN_NATIVE_F64 | PS_RUN_GRAPH))
+        return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
     PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
     if ((flags & PS_RUN_NATIVE_F64) && dtype != PS_F64)
         return fail(PS_ERR_UNSUPPORTED, "PS_RUN_NATIVE_F64 needs PS_F64");
@@ -492,43 +542,28 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
     const size_t span = (size_t)grid_stride * esz * (size_t)(nslots + nwork);
     if (span && (overlap2(states, span, T0, (size_t)n * esz) || overlap2(states, span, Ci, (size_t)n * esz)))
         return fail(PS_ERR_ALIAS, "the state grids overlap T0 or Ci");
-    char *base = (char *)states;
-    auto grid = [&](int slot) { return (void *)(base + (size_t)slot * (size_t)grid_stride * esz); };
     const StepCoef c = make_coef(lam, dt, _dx, _dy, _dz);
     const Grid3 g{nx, ny, nz};
-    // The boundary of every grid this call writes is T0's.  Where the z-march serves the
-    // steps they store the x and y faces themselves (in their coalesced row stores), so
-    // only the two z faces of each grid are copied here; else the whole boundary is.
-    const bool scaled = (flags & PS_RUN_CI_SCALED) != 0, native = (flags & PS_RUN_NATIVE_F64) != 0;
-    const int ngrids = nslots + nwork;
-    bool steps_bnd = true;
-    for (int k = 0; k < ngrids && steps_bnd; ++k)
-        steps_bnd = step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), T0, Ci) &&
-                    step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), grid(k), Ci);
-    if (nt > 0 && ngrids > 0) {
-        cudaError_t e = launch_copy_boundary_many(states, ngrids, grid_stride, T0, g, (int)esz,
-                                                  (cudaStream_t)stream, steps_bnd);
-        if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_run_states (boundary)");
-    }
-    const void *cur = T0;
-    int cur_slot = -3, work_next = 0;  // -3: T0; -1, -2: work grids 0, 1
-    for (int t = 1; t <= nt; ++t) {
-        int slot;
-        void *dst;
-        if (t % every == 0) {
-            slot = t / every - 1;
-            dst = grid(slot);
-        } else {  // a work grid, never the one this step reads
-            if (cur_slot == -1 - work_next) work_next ^= 1;
-            slot = -1 - work_next;
-            dst = grid(nslots + work_next);
-            work_next ^= 1;
-        }
-        cudaError_t e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, (cudaStream_t)stream,
-                                     steps_bnd);
+    // the slot of T(nt), the same whichever way the steps are issued
+    int cur_slot = -3, work_next = 0;
+    for (int t = 1; t <= nt; ++t) states_slot_after(t, every, cur_slot, work_next);
+    char *base = (char *)states;
+    const unsigned f = flags & ~PS_RUN_GRAPH;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((flags & PS_RUN_GRAPH) && nt > 0) {
+        // state-keeping keys: marker bit 0x40000000, `every` in the third pointer slot
+        const GraphKey key{current_device(), T0, states, (const void *)(intptr_t)every, Ci, lam, dt, _dx, _dy,
+                           _dz, nx, ny, nz, nt, dtype, 0x40000000u | f, grid_stride};
+        const int st = graph_replay(
+            key,
+            [&](cudaStream_t cs) {
+                return enqueue_run_states(T0, base, grid_stride, esz, every, Ci, c, g, nt, dtype, f, cs);
+            },
+            "capturing the state-keeping time loop", s);
+        if (st != PS_OK) return st;
+    } else {
+        cudaError_t e = enqueue_run_states(T0, base, grid_stride, esz, every, Ci, c, g, nt, dtype, f, s);
         if (e != cudaSuccess) return cuda_fail(e, "ps_diffusion3d_run_states");
-        cur = dst;
-        cur_slot = slot;
     }
     *final_slot = cur_slot;
     return PS_OK;
@@ -761,7 +796,7 @@ int ps_diffusion2d_run(void *T, void *T2, const void *Ci, double lam, double dt,
     if (flags & PS_RUN_GRAPH) {
         // 2-D keys: nz = -2 marks them apart from the 3-D time loops
         const GraphKey key{current_device(), T, T2, nullptr, Ci, lam, dt, _dx, _dy, 0.0, nx, ny, -2, nt, dtype,
-                           flags & ~PS_RUN_GRAPH};
+                           flags & ~PS_RUN_GRAPH, 0};
         return graph_replay(
             key, [&](cudaStream_t cs) { return enqueue_run2d(T, T2, Ci, c, nx, ny, nt, dtype, flags, cs); },
             "capturing the 2-D time loop", s);
@@ -1355,7 +1390,7 @@ static int batch_run(const void *dev_table, const BatchHeader &h, int nt, unsign
     // the table's work-item count and kernel are part of the key: the z-march launch
     // size is baked into the graph (a new table may reuse a freed table's address)
     const GraphKey key{current_device(), dev_table, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, 0.0,
-                       0.0, h.nitems, h.zmode, h.kernel, nt, h.dtype, 0x80000000u | (pairs ? 1u : 0u)};
+                       0.0, h.nitems, h.zmode, h.kernel, nt, h.dtype, 0x80000000u | (pairs ? 1u : 0u), 0};
     return graph_replay(
         key, [&](cudaStream_t cs) { return enqueue_batch_run(dev_table, h, nt, pairs, cs); },
         "capturing the batch loop", s);

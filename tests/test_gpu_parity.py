@@ -442,6 +442,31 @@ def test_state_block_copies_boundary_into_every_grid(dtype):
         assert np.array_equal(gh[~inner], Th[~inner]) and np.all(gh[inner] == -1.0)
 
 
+@pytest.mark.parametrize("every", [1, 4])
+def test_run_states_graph_equals_launches(every):
+    """The state-keeping loop replayed from the graph cache: every grid bit for bit the
+    loop's launched one by one; the second call replays the captured graph."""
+    nx, ny, nz = 68, 21, 13
+    nt = 9
+    T0h, Ci, lam, dt, inv = iso_problem(nx, ny, nz)
+    T0 = to_dev(T0h)
+    Cs = api.scale_ci(to_dev(Ci), lam, dt, inv)
+    count = nt // every + (2 if every > 1 else 0)
+    plain = api.StateBlock(T0, count, boundary=False)
+    f0 = api.run_states(T0, plain, every, Cs, lam, dt, inv, nt, ci_scaled=True)
+    api.clear_graph_cache()
+    block = api.StateBlock(T0, count, boundary=False)
+    for call in range(2):
+        block.flat.fill_(float("nan"))
+        f = api.run_states(T0, block, every, Cs, lam, dt, inv, nt, ci_scaled=True, graph=True)
+        assert api.graph_cache_size() == 1, call
+        for t in range(every, nt + 1, every):
+            assert torch.equal(block.grids[t // every - 1], plain.grids[t // every - 1]), (call, t)
+        assert torch.equal(f, f0)
+    api.clear_graph_cache()
+    assert api.device_error() == 0
+
+
 RUN_STATES_FORMS = {  # name: (shape nx, ny, nz; dtype; pre-scaled?)
     "f64_scaled4": ((68, 21, 13), torch.float64, True),
     "f64_scaled2": ((66, 19, 13), torch.float64, True),
