@@ -234,11 +234,15 @@ size_t ps_graph_cache_size(void);
  * compare launch shapes bit for bit and for a tuner that times them.  Each
  * value is process-wide and read on the host at launch; 0 (the initial
  * value) leaves the choice to the library's own rule.  Chunk values are
- * planes (or rows) per CTA, 1 .. 4096; flag values 0 or 1.  None changes a
- * result: the z-chunk and tile-width choices give bit for bit the same
- * fields, the plain compensated FP32 step equals the staged one bit for bit
+ * planes (or rows) per CTA, 1 .. 4096; flag values 0 or 1.  The forward
+ * steps' z-chunk and tile-width choices give bit for bit the same fields,
+ * the plain compensated FP32 step equals the staged one bit for bit
  * (explicit roundings), and the other plain kernels agree with the staged
- * ones to rounding.  Setting a value that differs from the current one empties the
+ * ones to rounding.  The FP64 transposed step holds w in fixed point at a
+ * scale shared by a CTA's tile and z-chunk, so its chunk can change the
+ * low-order bits of Tbar (values more than four binades below the largest
+ * of the chunk lose bits below 2^-56 of it), within the stated tolerance.
+ * Setting a value that differs from the current one empties the
  * CUDA-graph cache (a captured graph keeps the shapes of its capture).
  * ------------------------------------------------------------------- */
 typedef enum {

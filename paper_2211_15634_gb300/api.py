@@ -683,8 +683,10 @@ def graph_cache_size() -> int:
 def set_launch_override(name: str, value: int) -> int:
     """Set a launch-shape override (``ps_set_launch_override``): ``name`` is one of
     ``kchunk, kchunk2, adj_kchunk, chunk2d`` (planes or rows per CTA, 0 = the library's
-    rule) or ``adj_plain, f64_px2, step_plain`` (0/1).  Returns the previous value.  No override
-    changes a result; a change empties the graph cache."""
+    rule) or ``adj_plain, f64_px2, step_plain`` (0/1).  Returns the previous value.  The forward
+    steps' shapes give bit for bit the same fields; the FP64 transposed step's z-chunk sets
+    its fixed-point scale and so can change low-order bits within tolerance.  A change
+    empties the graph cache."""
     lib = _lib.load()
     which = _lib.PS_OVERRIDE[name]
     old = ctypes.c_int(0)
