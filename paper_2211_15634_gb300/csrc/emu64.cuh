@@ -377,9 +377,10 @@ __device__ __forceinline__ void emu_lane_general(const unsigned long long (&c)[P
 }
 
 // True when every high word in h and hc has the sign of hc and a biased exponent in
-// [e, e + 4] for one e >= 1 (no zero, subnormal, Inf or NaN): the values lie, with
-// one sign, in a window of five adjacent binades - where the general path's 57-bit
-// fixed point is exact too, so both give the same sums.  *emin = e.
+// [e, e + 4] for one e in [53, 2038] (no zero, subnormal, Inf or NaN): the values lie,
+// with one sign, in a window of five adjacent binades - where the general path's 57-bit
+// fixed point is exact too, so both give the same sums - and their sums (below 2^61
+// units of 2^(e-1075)) pack to normal doubles without range checks.  *emin = e.
 template <int N>
 __device__ __forceinline__ bool emu_window_hi(const unsigned (&h)[N], unsigned hc, int *emin) {
     unsigned lo = hc & 0x7ff00000u, hi = lo, sg = 0u;
@@ -391,7 +392,7 @@ __device__ __forceinline__ bool emu_window_hi(const unsigned (&h)[N], unsigned h
         sg |= h[i] ^ hc;
     }
     *emin = (int)(lo >> 20);
-    return (sg & 0x80000000u) == 0u && hi - lo <= 0x00400000u && lo != 0u && hi != 0x7ff00000u;
+    return (sg & 0x80000000u) == 0u && hi - lo <= 0x00400000u && lo >= (53u << 20) && lo <= (2038u << 20);
 }
 
 // |v| in units of the ulp of binade emin, for v of biased exponent e in [emin, emin + 4]:
@@ -432,7 +433,7 @@ __device__ __forceinline__ void emu_lane_window(const unsigned long long (&c)[PX
         if (kScaled) {
             unsigned long long sg;
             const unsigned long long a = emu_abs(sx + sy + sz, &sg);
-            out[i] = fma(ci[i], bitsd(emu_pack_mag(a, sc) | (sg ^ flip)), bitsd(c[i]));
+            out[i] = fma(ci[i], bitsd(emu_pack_mag_normal(a, sc) | (sg ^ flip)), bitsd(c[i]));
         } else {
             out[i] = fma(ci[i], emu_L<kIso>(sx, sy, sz, sc, flip, k), bitsd(c[i]));
         }
