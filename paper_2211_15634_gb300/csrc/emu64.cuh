@@ -380,35 +380,38 @@ __device__ __forceinline__ void emu_lane_general(const unsigned long long (&c)[P
 // [e, e + 4] for one e in [53, 2038] (no zero, subnormal, Inf or NaN): the values lie,
 // with one sign, in a window of five adjacent binades - where the general path's 57-bit
 // fixed point is exact too, so both give the same sums - and their sums (below 2^61
-// units of 2^(e-1075)) pack to normal doubles without range checks.  *emin = e.
+// units of 2^(e-1075)) pack to normal doubles without range checks.  With one sign the
+// words order as their magnitudes, so the smallest and largest word give the lowest and
+// highest exponent.  *ewin = the top 12 bits (sign and exponent e) of the smallest word.
 template <int N>
-__device__ __forceinline__ bool emu_window_hi(const unsigned (&h)[N], unsigned hc, int *emin) {
-    unsigned lo = hc & 0x7ff00000u, hi = lo, sg = 0u;
+__device__ __forceinline__ bool emu_window_hi(const unsigned (&h)[N], unsigned hc, unsigned *ewin) {
+    unsigned lo = hc, hi = hc, sg = 0u;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        const unsigned e = h[i] & 0x7ff00000u;
-        lo = min(lo, e);
-        hi = max(hi, e);
-        sg |= h[i] ^ hc;
+        lo = min(lo, h[i]);
+        hi = max(hi, h[i]);
+        sg = lop_or_xor(sg, h[i], hc);
     }
-    *emin = (int)(lo >> 20);
-    return (sg & 0x80000000u) == 0u && hi - lo <= 0x00400000u && lo >= (53u << 20) && lo <= (2038u << 20);
+    const unsigned el = (lo >> 20) & 0x7ffu;
+    *ewin = lo >> 20;
+    return (sg & 0x80000000u) == 0u && (hi >> 20) - (lo >> 20) <= 4u && el - 53u <= 2038u - 53u;
 }
 
-// |v| in units of the ulp of binade emin, for v of biased exponent e in [emin, emin + 4]:
-// the 53-bit significand shifted left by e - emin (< 2^57).  Exact.
-__device__ __forceinline__ long long emu_window_units(unsigned long long v, int emin) {
+// |v| in units of the ulp of binade e, for v of the window's sign and a biased exponent
+// in [e, e + 4] (ewin = sign and e as emu_window_hi gives them): the 53-bit significand
+// shifted left by the exponent difference (< 2^57).  Exact.
+__device__ __forceinline__ long long emu_window_units(unsigned long long v, unsigned ewin) {
     const unsigned hi = (unsigned)(v >> 32);
-    const int d = (int)((hi >> 20) & 0x7ffu) - emin;
+    const int d = (int)((hi >> 20) & 0x7ffu) - (int)(ewin & 0x7ffu);
     const unsigned long long m = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | (unsigned)v;
     return (long long)(m << d);
 }
 
 // The PX stencils of one thread when all their values lie, with one sign, in a
-// window of five binades (emu_window_hi, emin = the lowest): each value becomes an
-// exact integer in units of the lowest binade's ulp with a few integer instructions
-// (|value| < 2^57 units, so the sums of seven stay below 2^61), the sums are exact,
-// and the node finishes as on the general path (same real sum, same rounding: bit for
+// window of five binades (emu_window_hi; ewin: their sign and lowest exponent): each
+// value becomes an exact integer in units of the lowest binade's ulp with a few integer
+// instructions (|value| < 2^57 units, so the sums of seven stay below 2^61), the sums
+// are exact, and the node finishes as on the general path (same real sum, same rounding: bit for
 // bit emu_lane_general's result) at about half its cost.  flip: the values' sign.
 template <int PX, bool kScaled, bool kIso>
 __device__ __forceinline__ void emu_lane_window(const unsigned long long (&c)[PX], unsigned long long xl,
@@ -416,20 +419,20 @@ __device__ __forceinline__ void emu_lane_window(const unsigned long long (&c)[PX
                                                 const unsigned long long (&yp)[PX],
                                                 const unsigned long long (&zm)[PX],
                                                 const unsigned long long (&zp)[PX], const double (&ci)[PX],
-                                                const EmuCoef &k, int emin, double (&out)[PX]) {
+                                                const EmuCoef &k, unsigned ewin, double (&out)[PX]) {
     const unsigned long long flip = c[0] & 0x8000000000000000ull;
-    const int sc = emin - 1075;
+    const int sc = (int)(ewin & 0x7ffu) - 1075;
     long long uc[PX];
 #pragma unroll
-    for (int i = 0; i < PX; ++i) uc[i] = emu_window_units(c[i], emin);
-    const long long ul = emu_window_units(xl, emin), ur = emu_window_units(xr, emin);
+    for (int i = 0; i < PX; ++i) uc[i] = emu_window_units(c[i], ewin);
+    const long long ul = emu_window_units(xl, ewin), ur = emu_window_units(xr, ewin);
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
         const long long uxm = i == 0 ? ul : uc[i - 1], uxp = i == PX - 1 ? ur : uc[i + 1];
         const long long c2 = 2 * uc[i];
         const long long sx = uxm + uxp - c2;
-        const long long sy = emu_window_units(ym[i], emin) + emu_window_units(yp[i], emin) - c2;
-        const long long sz = emu_window_units(zm[i], emin) + emu_window_units(zp[i], emin) - c2;
+        const long long sy = emu_window_units(ym[i], ewin) + emu_window_units(yp[i], ewin) - c2;
+        const long long sz = emu_window_units(zm[i], ewin) + emu_window_units(zp[i], ewin) - c2;
         if (kScaled) {
             unsigned long long sg;
             const unsigned long long a = emu_abs(sx + sy + sz, &sg);

@@ -266,11 +266,11 @@ __device__ __forceinline__ void zmarch_tile(const CUtensorMap *tmT, const CUtens
                     double ci[PX], o[PX];
 #pragma unroll
                     for (int i = 0; i < PX; ++i) ci[i] = (double)vget<V, E>(civ, i);
-                    int emin;
-                    const bool near = emu_window_hi(hw, hc, &emin);
+                    unsigned ewin;
+                    const bool near = emu_window_hi(hw, hc, &ewin);
                     if (__all_sync(rmask, near))
                         emu_lane_window<PX, kScaled, kIso>(c, xm[0], xp[PX - 1], ym, yp, zm, zp, ci, p.ek,
-                                                           emin, o);
+                                                           ewin, o);
                     else
                         emu_lane_general<PX, kScaled, kIso>(c, xm[0], xp[PX - 1], ym, yp, zm, zp, ci,
                                                             p.ek, o);
