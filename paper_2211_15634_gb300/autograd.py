@@ -6,7 +6,8 @@ steps.  By default (``every=None``) every state is kept when the nt fields fit
 in the device's free memory with a margin (no recompute: the reverse sweep
 reads each state once), else every ``ceil(sqrt(nt))`` steps.  ``backward`` walks the
 segments in reverse: it recomputes the states of one segment from its
-checkpoint with the forward kernel, then applies the transposed step
+checkpoint with the forward kernel (the last segment's states are kept from the
+forward pass, which computes them anyway), then applies the transposed step
 (``ps_diffusion3d_adjoint``) from the segment's last step to its first,
 accumulating dL/dCi; the next segment's recompute runs on a side stream meanwhile.
 dt is held constant (not differentiated through maximum(Ci)).  Memory: about
@@ -65,25 +66,37 @@ def coefficient(Ci, lam, dt, inv):
 
 
 def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True):
-    """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...]).
+    """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...], last).
 
-    ``coef`` = :func:`coefficient` (computed here when None).  ``graph``: replay the
-    state-keeping loop from the library's graph cache (keyed by the buffers, which the
-    caching allocator hands back unchanged in a loop of gradients)."""
+    ``last`` holds the states of the last segment (after steps t_last+1 .. nt, t_last
+    the last checkpoint's step) in a :class:`api.StateBlock` of ``every`` grids - the
+    forward computes them anyway, so the reverse sweep need not recompute that segment
+    (None when every state is kept).  ``coef`` = :func:`coefficient` (computed here
+    when None).  ``graph``: replay the state-keeping loops from the library's graph
+    cache (keyed by the buffers, which the caching allocator hands back unchanged in a
+    loop of gradients)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     if nt == 0:
-        return T0.clone(), [T0]
-    # checkpoints (the state after every `every`-th step) and two work grids in one block,
-    # all with T0's boundary; the steps write straight into them (one library call)
-    nslots = nt // every
-    block = api.StateBlock(T0, nslots + (2 if every > 1 else 0), boundary=False)  # run_states sets it
-    cur = api.run_states(T0, block, every, C, lam, dt, inv, nt, ci_scaled=scaled, graph=graph)
-    ckpts = [T0] + block.grids[:(nt - 1) // every]
-    return cur, ckpts
+        return T0.clone(), [T0], None
+    if every == 1:
+        # every state in one block; the steps write straight into it (one library call)
+        block = api.StateBlock(T0, nt, boundary=False)  # run_states sets the boundaries
+        cur = api.run_states(T0, block, 1, C, lam, dt, inv, nt, ci_scaled=scaled, graph=graph)
+        return cur, [T0] + block.grids[:nt - 1], None
+    t_last = (nt - 1) // every * every  # step of the last checkpoint
+    ckpts = [T0]
+    if t_last > 0:
+        # checkpoints (the state after every `every`-th step) and two work grids in one block
+        block = api.StateBlock(T0, t_last // every + 2, boundary=False)
+        api.run_states(T0, block, every, C, lam, dt, inv, t_last, ci_scaled=scaled, graph=graph)
+        ckpts += block.grids[:t_last // every]
+    last = api.StateBlock(T0, every, boundary=False)
+    cur = api.run_states(ckpts[-1], last, 1, C, lam, dt, inv, nt - t_last, ci_scaled=scaled, graph=graph)
+    return cur, ckpts, last
 
 
 def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None,
-                          overlap=None, graph=True):
+                          overlap=None, graph=True, last=None):
     """Reverse sweep; returns (dL/dT0, dL/dCi).  ``pairs``: take the transposed
     steps two per launch where ``api.adjoint2`` applies (default off).  ``overlap``
     (default on for CUDA tensors with more than one segment to recompute): recompute
@@ -91,7 +104,9 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     into the second of two segment buffers (one more segment of memory); the kernels
     and their order on every buffer are unchanged, so the gradient is bit for bit
     the one-stream sweep's.  ``graph``: the segments' recomputes are replayed from the
-    graph cache, as in :func:`forward_checkpointed`."""
+    graph cache, as in :func:`forward_checkpointed`.  ``last``: the last segment's
+    states from :func:`forward_checkpointed` (that segment is then not recomputed, and
+    its block serves as one of the segment buffers afterwards)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     pairs = bool(pairs) and not scaled and api.adjoint2_supported(ybar_nt)
     ybar = ybar_nt.contiguous().clone()
@@ -99,10 +114,15 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
     nseg = len(ckpts)
     seg_len = max(0, min(every, nt) - 1)  # recomputed states per segment
+    in_place = {nseg - 1} if last is not None else set()  # segments whose states are there
     if overlap is None:
-        overlap = ybar.is_cuda and nseg > 1 and seg_len > 0
-    # grids for the recomputed states of a segment (run_states gives them T0's boundary)
-    segs = [api.StateBlock(ckpts[0], seg_len, boundary=False) for _ in range(2 if overlap else 1)]
+        overlap = ybar.is_cuda and nseg - len(in_place) > 1 and seg_len > 0
+    # grids for the recomputed states of a segment (run_states gives them T0's boundary);
+    # segment s uses buffer s % len(segs), the last segment's is `last` when given
+    segs = [None] * (2 if overlap else 1)
+    if last is not None:
+        segs[(nseg - 1) % len(segs)] = last
+    segs = [b if b is not None else api.StateBlock(ckpts[0], seg_len, boundary=False) for b in segs]
     main = torch.cuda.current_stream(ybar.device) if overlap else None
     side = torch.cuda.Stream(ybar.device) if overlap else None
     ready, used = {}, [None, None]  # recompute of segment s done; sweep done with buffer b
@@ -110,7 +130,7 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     def recompute(s):
         t0 = s * every
         t1 = min(t0 + every, nt)
-        if t1 - t0 <= 1:
+        if t1 - t0 <= 1 or s in in_place:
             return
         b = s % len(segs)
         if not overlap:
@@ -168,12 +188,13 @@ class Diffusion3DFn(torch.autograd.Function):
         Ci = Ci.detach().contiguous()
         every = auto_every(T0, int(nt)) if every is None else int(every)
         coef = coefficient(Ci, lam, dt, tuple(inv_spacing))
-        out, ckpts = forward_checkpointed(T0, Ci, lam, dt, tuple(inv_spacing), int(nt), every, coef)
-        # T(nt) lives in the state block with the checkpoints: hand out a field of its own,
-        # so that a caller who keeps T(nt) does not keep the block alive after backward
+        out, ckpts, last = forward_checkpointed(T0, Ci, lam, dt, tuple(inv_spacing), int(nt), every, coef)
+        # T(nt) lives in a state block: hand out a field of its own, so that a caller who
+        # keeps T(nt) does not keep the block alive after backward
         out = out.clone()
         ctx.cfg = (lam, dt, tuple(inv_spacing), int(nt), every)
         ctx.ckpts = ckpts
+        ctx.last = last
         ctx.coef = coef
         ctx.save_for_backward(Ci)
         return out
@@ -183,8 +204,9 @@ class Diffusion3DFn(torch.autograd.Function):
         (Ci,) = ctx.saved_tensors
         lam, dt, inv, nt, every = ctx.cfg
         dT0, dCi = backward_checkpointed(grad_out, Ci, lam, dt, inv, nt, every, ctx.ckpts,
-                                         ctx.coef)
+                                         ctx.coef, last=ctx.last)
         ctx.ckpts = None
+        ctx.last = None
         ctx.coef = None
         return dT0, dCi, None, None, None, None, None
 
@@ -196,8 +218,9 @@ def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None
     every = auto_every(T0, int(nt)) if every is None else int(every)
     inv = tuple(inv_spacing)
     coef = coefficient(Ci.contiguous(), lam, dt, inv)
-    out, ckpts = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef)
+    out, ckpts, last = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef)
     resid = torch.empty_like(out)
     L = api.half_sq_dist(out, Tobs, residual=resid)
-    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs)
+    del out  # a grid of `last`, which the sweep reuses
+    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs, last=last)
     return L, dT0, dCi
