@@ -669,10 +669,11 @@ def secondary_metrics(torch, api, ag, inputs, log):
     torch.cuda.empty_cache()
 
     # gradient / forward at 256^3, nt = 200: L = 1/2||T(nt) - T_obs||^2, dL/dCi and dL/dT0.
-    # The forward run it is compared with is the fastest forward of the same problem
-    # (graph-captured; FP64 on the pre-scaled coefficient, as the gradient's own forward).
-    # Checkpoints every ceil(sqrt(nt)) steps (recompute per segment), and every state
-    # kept (27 GB at 256^3 FP64, no recompute).
+    # The forward run it is compared with is the library's default time loop of the same
+    # problem (graph-captured one-step launches; FP64 on the pre-scaled coefficient, as the
+    # gradient's own forward); FP32 also against the fused-pair forward (grad_over_fwd2),
+    # its fastest.  Checkpoints every ceil(sqrt(nt)) steps (recompute per segment), and
+    # every state kept (27 GB at 256^3 FP64, no recompute).
     n, nt = 256, 200
     T0 = inputs.t0_gaussian(n, n, n)
     Ct = inputs.ci_smooth(n, n, n)
@@ -694,6 +695,10 @@ def secondary_metrics(torch, api, ag, inputs, log):
         Cf, scaled = ag.coefficient(Cd, 1.0, dt, inv)
         t_fwd = timed(lambda: api.run(fa, fb, Cf, 1.0, dt, inv, nt, graph=True, ci_scaled=scaled))
         out[f"fwd_256_{name}_ms"] = round(1e3 * t_fwd, 2)
+        t_fwd2 = None
+        if dtype == torch.float32:
+            t_fwd2 = timed(lambda: api.run(fa, fb, Cf, 1.0, dt, inv, nt, graph=True, temporal2=True))
+            out[f"fwd2_256_{name}_ms"] = round(1e3 * t_fwd2, 2)
         # the transposed step alone (CUDA events, warm), before the gradient runs: releasing
         # their 13-27 GB state block slows later kernels on older buffers by a third
         ybar = Td - Td.mean()
@@ -706,7 +711,10 @@ def secondary_metrics(torch, api, ag, inputs, log):
         out[f"adjoint_256_{name}_gbs"] = round(6 * n ** 3 * Td.element_size() / t_adj / 1e9, 1)
         for tag, every in (("sqrt_nt", ag.default_every(nt)), ("all_states", 1)):
             t_grad = timed(lambda: ag.loss_and_grad(Td, Cd, Tobs, 1.0, dt, inv, nt, every=every), reps=2)
+            out[f"grad_256_{name}_{tag}_ms"] = round(1e3 * t_grad, 2)
             out[f"grad_over_fwd_256_{name}_{tag}"] = round(t_grad / t_fwd, 3)
+            if t_fwd2 is not None:
+                out[f"grad_over_fwd2_256_{name}_{tag}"] = round(t_grad / t_fwd2, 3)
             torch.cuda.empty_cache()
         del Td, Ctd, Cd, Cf, a, b, Tobs, fa, fb, ybar, Tbar, Cib
         api.clear_graph_cache()

@@ -186,14 +186,15 @@ def state_block(T0, count: int):
 
 
 def run_states(T0, block: "StateBlock", every: int, Ci, lam: float, dt: float, inv_spacing, nt: int,
-               *, ci_scaled: bool = False, graph: bool = False) -> torch.Tensor:
+               *, ci_scaled: bool = False, graph: bool = False, temporal2: bool = False) -> torch.Tensor:
     """nt steps from T0 keeping the state after step t in grid t/every - 1 of
     ``block`` when every divides t (else in its two work grids after those);
     returns the tensor holding T(nt).  The boundary of every grid it writes is set to
     T0's (by the steps themselves where the TMA z-march serves them, the z faces by a
     copy).  One library call (``ps_diffusion3d_run_states``); ``graph=True`` replays its
     launches from the library's graph cache (keyed by the pointers: worth it when the same
-    buffers come back, as in a loop of gradients)."""
+    buffers come back, as in a loop of gradients).  ``temporal2=True`` (FP32, every = 1):
+    fused step pairs that write both states, bit for bit the same grids."""
     code = _code(T0)
     _same(T0, Ci)
     nx, ny, nz = _grid(T0)
@@ -205,8 +206,8 @@ def run_states(T0, block: "StateBlock", every: int, Ci, lam: float, dt: float, i
     check(_lib.load().ps_diffusion3d_run_states(
         _field(T0, "T0", code), block.ptr(), block.stride, int(every), _field(Ci, "Ci", code), lam,
         dt, *inv_spacing, nx, ny, nz, int(nt), code,
-        (_lib.PS_RUN_CI_SCALED if ci_scaled else 0) | (_lib.PS_RUN_GRAPH if graph else 0),
-        _stream(T0), ctypes.byref(slot)))
+        (_lib.PS_RUN_CI_SCALED if ci_scaled else 0) | (_lib.PS_RUN_GRAPH if graph else 0)
+        | (_lib.PS_RUN_TEMPORAL2 if temporal2 else 0), _stream(T0), ctypes.byref(slot)))
     s = slot.value
     if s == -3:
         return T0

@@ -7,7 +7,8 @@ in the device's free memory with a margin (no recompute: the reverse sweep
 reads each state once), else every ``ceil(sqrt(nt))`` steps.  ``backward`` walks the
 segments in reverse: it recomputes the states of one segment from its
 checkpoint with the forward kernel (the last segment's states are kept from the
-forward pass, which computes them anyway), then applies the transposed step
+forward pass, which computes them anyway; on FP32 grids the forward's loops that
+keep every state run fused step pairs that write both states), then applies the transposed step
 (``ps_diffusion3d_adjoint``) from the segment's last step to its first,
 accumulating dL/dCi; the next segment's recompute runs on a side stream meanwhile.
 dt is held constant (not differentiated through maximum(Ci)).  Memory: about
@@ -65,7 +66,17 @@ def coefficient(Ci, lam, dt, inv):
     return Ci, False
 
 
-def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True):
+def state_pairs_default(T0) -> bool:
+    """Whether the forward pass's state-keeping loops run fused step pairs that write both
+    states (``api.run_states(temporal2=True)``: FP32 only; bit for bit the same states).
+    Measured at 256^3, nt = 200: 200 states in 6.05 against 6.69 ms, the gradient with every
+    state kept 18.83 against 19.47 ms.  The reverse sweep's recomputes stay single steps by
+    default: there they run beside the transposed steps, and in pairs the sqrt(nt)
+    gradient measured slower (23.72 against 23.18 ms)."""
+    return T0.dtype == torch.float32
+
+
+def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True, state_pairs=None):
     """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...], last).
 
     ``last`` holds the states of the last segment (after steps t_last+1 .. nt, t_last
@@ -74,14 +85,16 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True)
     (None when every state is kept).  ``coef`` = :func:`coefficient` (computed here
     when None).  ``graph``: replay the state-keeping loops from the library's graph
     cache (keyed by the buffers, which the caching allocator hands back unchanged in a
-    loop of gradients)."""
+    loop of gradients).  ``state_pairs``: the loops that keep every state (every = 1, and
+    the last segment) run fused step pairs (default :func:`state_pairs_default`)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
+    pairs = state_pairs_default(T0) if state_pairs is None else bool(state_pairs)
     if nt == 0:
         return T0.clone(), [T0], None
     if every == 1:
         # every state in one block; the steps write straight into it (one library call)
         block = api.StateBlock(T0, nt, boundary=False)  # run_states sets the boundaries
-        cur = api.run_states(T0, block, 1, C, lam, dt, inv, nt, ci_scaled=scaled, graph=graph)
+        cur = api.run_states(T0, block, 1, C, lam, dt, inv, nt, ci_scaled=scaled, graph=graph, temporal2=pairs)
         return cur, [T0] + block.grids[:nt - 1], None
     t_last = (nt - 1) // every * every  # step of the last checkpoint
     ckpts = [T0]
@@ -91,12 +104,13 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True)
         api.run_states(T0, block, every, C, lam, dt, inv, t_last, ci_scaled=scaled, graph=graph)
         ckpts += block.grids[:t_last // every]
     last = api.StateBlock(T0, every, boundary=False)
-    cur = api.run_states(ckpts[-1], last, 1, C, lam, dt, inv, nt - t_last, ci_scaled=scaled, graph=graph)
+    cur = api.run_states(ckpts[-1], last, 1, C, lam, dt, inv, nt - t_last, ci_scaled=scaled, graph=graph,
+                         temporal2=pairs)
     return cur, ckpts, last
 
 
 def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None,
-                          overlap=None, graph=True, last=None):
+                          overlap=None, graph=True, last=None, state_pairs=None):
     """Reverse sweep; returns (dL/dT0, dL/dCi).  ``pairs``: take the transposed
     steps two per launch where ``api.adjoint2`` applies (default off).  ``overlap``
     (default on for CUDA tensors with more than one segment to recompute): recompute
@@ -106,8 +120,11 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     the one-stream sweep's.  ``graph``: the segments' recomputes are replayed from the
     graph cache, as in :func:`forward_checkpointed`.  ``last``: the last segment's
     states from :func:`forward_checkpointed` (that segment is then not recomputed, and
-    its block serves as one of the segment buffers afterwards)."""
+    its block serves as one of the segment buffers afterwards).  ``state_pairs``: the
+    recomputes run fused step pairs, as in :func:`forward_checkpointed` (default off, see
+    :func:`state_pairs_default`)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
+    spairs = bool(state_pairs)
     pairs = bool(pairs) and not scaled and api.adjoint2_supported(ybar_nt)
     ybar = ybar_nt.contiguous().clone()
     tbar = torch.empty_like(ybar)
@@ -134,13 +151,15 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
             return
         b = s % len(segs)
         if not overlap:
-            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph)
+            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph,
+                           temporal2=spairs)
             return
         with torch.cuda.stream(side):
             side.wait_stream(main)  # the checkpoints and Cs are final
             if used[b] is not None:
                 side.wait_event(used[b])  # the sweep no longer reads this buffer
-            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph)
+            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph,
+                           temporal2=spairs)
             ready[s] = torch.cuda.Event()
             ready[s].record(side)
 
@@ -211,16 +230,19 @@ class Diffusion3DFn(torch.autograd.Function):
         return dT0, dCi, None, None, None, None, None
 
 
-def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None):
+def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None, state_pairs=None):
     """L = 1/2||T(nt) - Tobs||^2 (FP64 on the GPU) and (dL/dT0, dL/dCi); ``every``
     as for :class:`Diffusion3DFn` (None: every state kept when it fits); ``pairs``
-    as for :func:`backward_checkpointed`."""
+    as for :func:`backward_checkpointed`, ``state_pairs`` as for
+    :func:`forward_checkpointed`."""
     every = auto_every(T0, int(nt)) if every is None else int(every)
     inv = tuple(inv_spacing)
     coef = coefficient(Ci.contiguous(), lam, dt, inv)
-    out, ckpts, last = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef)
+    out, ckpts, last = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef,
+                                            state_pairs=state_pairs)
     resid = torch.empty_like(out)
     L = api.half_sq_dist(out, Tobs, residual=resid)
     del out  # a grid of `last`, which the sweep reuses
-    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs, last=last)
+    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs, last=last,
+                                     state_pairs=state_pairs)
     return L, dT0, dCi

@@ -503,13 +503,30 @@ static cudaError_t enqueue_run_states(const void *T0, char *base, int64_t grid_s
     for (int k = 0; k < ngrids && steps_bnd; ++k)
         steps_bnd = step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), T0, Ci) &&
                     step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), grid(k), Ci);
+    // PS_RUN_TEMPORAL2 (FP32, every state kept): fused pairs that write both states with
+    // their x and y faces, where the pair kernel serves every grid (all are 16-byte
+    // aligned at one stride, so the first two decide) and the single steps of an odd nt
+    // store their faces too; else single steps
+    const bool pairs_ok = (flags & PS_RUN_TEMPORAL2) && every == 1 && dtype == PS_F32 && nt >= 2 && steps_bnd &&
+                          temporal2_ok(g, dtype, T0, grid(0), Ci) && temporal2_ok(g, dtype, grid(0), grid(1), Ci);
     if (nt > 0 && ngrids > 0) {
         cudaError_t e = launch_copy_boundary_many(base, ngrids, grid_stride, T0, g, (int)esz, s, steps_bnd);
         if (e != cudaSuccess) return e;
     }
     const void *cur = T0;
+    int t = 1;
+    if (pairs_ok) {
+        // fused pairs that keep both states: states t and t+1 (slots t-1, t) from state t-1
+        for (; t + 1 <= nt; t += 2) {
+            cudaError_t e = launch_step2_states_f32((float *)grid(t - 1), (float *)grid(t), (const float *)cur,
+                                                    (const float *)Ci, c, g, s);
+            if (e != cudaSuccess) return e;
+            cur = grid(t);
+        }
+    }
     int cur_slot = -3, work_next = 0;  // -3: T0; -1, -2: work grids 0, 1
-    for (int t = 1; t <= nt; ++t) {
+    for (int u = 1; u < t; ++u) states_slot_after(u, every, cur_slot, work_next);
+    for (; t <= nt; ++t) {
         const int slot = states_slot_after(t, every, cur_slot, work_next);
         void *dst = slot >= 0 ? grid(slot) : grid(nslots + (-1 - slot));
         cudaError_t e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, s, steps_bnd);
@@ -528,11 +545,13 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
     if (nt < 0) return fail(PS_ERR_ARG, "nt = %d < 0", nt);
     if (every < 1) return fail(PS_ERR_ARG, "every = %d < 1", every);
     if (!final_slot) return fail(PS_ERR_ARG, "final_slot is NULL");
-    if (flags & ~(PS_RUN_CI_SCALED | PS_RUN_NATIVE_F64 | PS_RUN_GRAPH))
+    if (flags & ~(PS_RUN_CI_SCALED | PS_RUN_NATIVE_F64 | PS_RUN_GRAPH | PS_RUN_TEMPORAL2))
         return fail(PS_ERR_ARG, "unknown flags 0x%x", flags);
     PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
     if ((flags & PS_RUN_NATIVE_F64) && dtype != PS_F64)
         return fail(PS_ERR_UNSUPPORTED, "PS_RUN_NATIVE_F64 needs PS_F64");
+    if ((flags & PS_RUN_TEMPORAL2) && (dtype != PS_F32 || every != 1))
+        return fail(PS_ERR_UNSUPPORTED, "PS_RUN_TEMPORAL2 in the state-keeping loop needs PS_F32 and every = 1");
     const int64_t n = nx * ny * nz;
     const size_t esz = elem_bytes(dtype);
     if (grid_stride < n || (grid_stride * (int64_t)esz) % 16 != 0)

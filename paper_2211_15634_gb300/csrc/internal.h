@@ -68,6 +68,10 @@ cudaError_t launch_step2_f32(float *T2, const float *T, const float *Ci, StepCoe
                              cudaStream_t s);
 cudaError_t launch_step2_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
                                     cudaStream_t s);
+// A fused FP32 pair that keeps both states: T1 = step(T) to T1o, T2 = step(T1), both
+// written at every node of planes 1 .. nz-2 (x and y faces as copies of T's).
+cudaError_t launch_step2_states_f32(float *T1o, float *T2, const float *T, const float *Ci, StepCoef c,
+                                    Grid3 g, cudaStream_t s);
 unsigned zmarch2_device_error(bool clear);
 const char *step_f64_kernel_name(Grid3 g, const void *T2, const void *T, const void *Ci, StepCoef c,
                                  bool scaled);

@@ -14,24 +14,27 @@ namespace psd {
 
 __device__ unsigned g_zmarch2_error;  // set when an mbarrier wait times out
 
-template <typename E, int BY, int NT, int NC>
+// kStates: T1 = step(T) also goes to T1o, and T1o and T2 are written with their x and
+// y faces (zmarch2_tile).
+template <typename E, int BY, int NT, int NC, bool kStates>
 __global__ void __launch_bounds__(32 * BY, Z2Ring<E>::MINB)
 k_zmarch2(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmC,
-          E *__restrict__ T2, const Z2Params p) {
+          E *__restrict__ T2, const Z2Params p, E *__restrict__ T1o) {
     grid_dep_wait();  // the previous launch's writes (and its reads of T2) are complete
     grid_dep_launch();
     const int X0 = (int)(blockIdx.x % p.ntx) * (32 * Z2Traits<E>::PX), Y0 = (int)(blockIdx.x / p.ntx) * BY;
     const int k0 = 1 + (int)blockIdx.y * p.kchunk;
     const int k1 = (int)min((int64_t)k0 + p.kchunk, p.nz - 1);  // output planes [k0, k1)
-    zmarch2_tile<E, BY, NT, NC>(&tmT, &tmC, T2, p, X0, Y0, k0, k1, &g_zmarch2_error);
+    zmarch2_tile<E, BY, NT, NC, kStates>(&tmT, &tmC, T2, p, X0, Y0, k0, k1, &g_zmarch2_error, T1o);
 }
 
 bool zmarch2_supported(Grid3 g, int esz, const void *a, const void *b, const void *c) {
     return zmarch_supported(g, esz, a, b, c);
 }
 
-template <typename E>
-static cudaError_t launch_z2(E *T2, const E *T, const E *Ci, Z2Params p, Grid3 g, cudaStream_t s) {
+template <typename E, bool kStates = false>
+static cudaError_t launch_z2(E *T2, const E *T, const E *Ci, Z2Params p, Grid3 g, cudaStream_t s,
+                             E *T1o = nullptr) {
     constexpr int BY = 8, NT = Z2Ring<E>::NT, NC = Z2Ring<E>::NC, PX = Z2Traits<E>::PX,
                   HX = 16 / (int)sizeof(E), BX = 32 * PX, W = BX + 2 * HX;
     constexpr unsigned TBA = (W * (BY + 4) * sizeof(E) + 127) / 128 * 128;
@@ -39,7 +42,7 @@ static cudaError_t launch_z2(E *T2, const E *T, const E *Ci, Z2Params p, Grid3 g
     constexpr size_t smem = NT * TBA + (NC + 2) * CBA + (NT + NC) * 8;
     static unsigned attr_gen[64] = {0};
     cudaError_t ae;
-    if (!set_smem_attr_once((const void *)k_zmarch2<E, BY, NT, NC>, (int)smem, attr_gen, &ae)) return ae;
+    if (!set_smem_attr_once((const void *)k_zmarch2<E, BY, NT, NC, kStates>, (int)smem, attr_gen, &ae)) return ae;
     CUtensorMap mT, mC;
     if (!make_tensor_map_3d(&mT, T, sizeof(E), g, W, BY + 4) ||
         !make_tensor_map_3d(&mC, Ci, sizeof(E), g, W, BY + 2))
@@ -60,8 +63,8 @@ static cudaError_t launch_z2(E *T2, const E *T, const E *Ci, Z2Params p, Grid3 g
     p.pitch = g.nx;
     p.ntx = (int)ntx;
     p.kchunk = kchunk;
-    return launch_pdl(k_zmarch2<E, BY, NT, NC>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem, s, mT,
-                      mC, T2, p);
+    return launch_pdl(k_zmarch2<E, BY, NT, NC, kStates>, dim3((unsigned)tiles, (unsigned)gz, 1), dim3(32 * BY), smem,
+                      s, mT, mC, T2, p, T1o);
 }
 
 cudaError_t launch_step2_f32(float *T2, const float *T, const float *Ci, StepCoef c, Grid3 g,
@@ -77,6 +80,16 @@ cudaError_t launch_step2_f32(float *T2, const float *T, const float *Ci, StepCoe
 cudaError_t launch_step2_f64_scaled(double *T2, const double *T, const double *Cs, Grid3 g,
                                     cudaStream_t s) {
     return launch_z2<double>(T2, T, Cs, Z2Params{}, g, s);
+}
+
+cudaError_t launch_step2_states_f32(float *T1o, float *T2, const float *T, const float *Ci, StepCoef c,
+                                    Grid3 g, cudaStream_t s) {
+    Z2Params p{};
+    p.dtlam = (float)c.dtlam;
+    p.ax = (float)c.ax;
+    p.ay = (float)c.ay;
+    p.az = (float)c.az;
+    return launch_z2<float, true>(T2, T, Ci, p, g, s, T1o);
 }
 
 unsigned zmarch2_device_error(bool clear) {

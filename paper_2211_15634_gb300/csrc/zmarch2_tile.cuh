@@ -85,10 +85,14 @@ struct Z2Ring {
 // parameter or global memory.  Rows are p.pitch elements apart, planes
 // p.pitch * p.ny.  A timed-out wait sets bit 0 of *err and the CTA leaves after
 // draining its copies.
-template <typename E, int BY, int NT, int NC>
+// kStates (the state-keeping loop of a reverse sweep): the intermediate state
+// T1 = step(T) goes to T1o as well, and both T1o and T2 are written at every node of
+// the output planes, their x and y faces as copies of T's (the boundary is fixed),
+// so that fresh state grids need only their two z faces set.
+template <typename E, int BY, int NT, int NC, bool kStates = false>
 __device__ __forceinline__ void zmarch2_tile(const CUtensorMap *tmT, const CUtensorMap *tmC,
                                              E *__restrict__ T2, const Z2Params &p, int X0, int Y0,
-                                             int k0, int k1, unsigned *err) {
+                                             int k0, int k1, unsigned *err, E *__restrict__ T1o = nullptr) {
     using V = typename Z2Traits<E>::V;
     constexpr int PX = Z2Traits<E>::PX, HX = 16 / (int)sizeof(E), BX = 32 * PX, W = BX + 2 * HX;
     constexpr int H0 = BY + 4, H1 = BY + 2;         // T box rows, Ci box / T1 tile rows
@@ -275,7 +279,7 @@ __device__ __forceinline__ void zmarch2_tile(const CUtensorMap *tmT, const CUten
             atomicOr(err, 1u);
         }
         // T2 of plane z (T1 tile z is complete since the previous barrier)
-        if (yin && ok) {
+        if ((kStates ? gy <= ny - 1 : yin) && ok) {
             const E *Wz = sW + wz * CS;
             const int o = r1 * W + c0;
             const V up = *(const V *)(Wz + o - W), dn = *(const V *)(Wz + o + W);
@@ -292,7 +296,24 @@ __device__ __forceinline__ void zmarch2_tile(const CUtensorMap *tmT, const CUten
                                        z2get<V, E>(ci, i), p));
             }
             const int64_t base = (int64_t)gx0 + p.pitch * ((int64_t)gy + p.ny * (int64_t)z);
-            if (all_x) {
+            if constexpr (kStates) {
+                // T1 of plane z and T2 at every node of the row: T's value (held in T1's
+                // non-interior entries) where the node is not interior
+#pragma unroll
+                for (int i = 0; i < PX; ++i)
+                    if (!in[i]) z2set<V, E>(out, i, z2get<V, E>(t1c, i));
+                if (gx0 + PX - 1 <= nx - 1) {
+                    *(V *)(T1o + base) = t1c;
+                    *(V *)(T2 + base) = out;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < PX; ++i)
+                        if (gx0 + i <= nx - 1) {
+                            T1o[base + i] = z2get<V, E>(t1c, i);
+                            T2[base + i] = z2get<V, E>(out, i);
+                        }
+                }
+            } else if (all_x) {
                 *(V *)(T2 + base) = out;
             } else {
 #pragma unroll
