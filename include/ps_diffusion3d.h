@@ -215,11 +215,13 @@ int ps_diffusion3d_run_ex(void *T, void *T2, void *comp, const void *Ci, double 
  * PS_RUN_GRAPH captures the boundary copy and the nt launches into a CUDA
  * graph on the first call for this argument set (pointers, stride, every,
  * coefficients, sizes) and replays it afterwards.  Else one launch per step
- * from a host loop in the library.  PS_RUN_TEMPORAL2 (PS_F32 with every = 1,
- * else PS_ERR_UNSUPPORTED): the steps run as fused pairs that write both states
- * (one pass over HBM per two states: read the state and Ci, write two states),
- * bit for bit the same grids; grids the fused-pair kernel cannot serve, and
- * the last step of an odd nt, run single steps. */
+ * from a host loop in the library.  PS_RUN_TEMPORAL2 (PS_F32, else
+ * PS_ERR_UNSUPPORTED): the steps run as fused pairs, bit for bit the same
+ * states - with every = 1 pairs that write both states (one pass over HBM per
+ * two states: read the state and Ci, write two states); with every > 1 pairs
+ * that never step over a kept state (a single step where one would).  Grids
+ * the fused-pair kernel cannot serve run single steps.  Which work grid holds
+ * T(nt) can differ from the single-step loop's (*final_slot says). */
 int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride, int every,
                               const void *Ci, double lam, double dt, double _dx, double _dy,
                               double _dz, int64_t nx, int64_t ny, int64_t nz, int nt, int dtype,

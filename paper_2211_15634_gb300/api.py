@@ -193,8 +193,9 @@ def run_states(T0, block: "StateBlock", every: int, Ci, lam: float, dt: float, i
     T0's (by the steps themselves where the TMA z-march serves them, the z faces by a
     copy).  One library call (``ps_diffusion3d_run_states``); ``graph=True`` replays its
     launches from the library's graph cache (keyed by the pointers: worth it when the same
-    buffers come back, as in a loop of gradients).  ``temporal2=True`` (FP32, every = 1):
-    fused step pairs that write both states, bit for bit the same grids."""
+    buffers come back, as in a loop of gradients).  ``temporal2=True`` (FP32): fused step
+    pairs, bit for bit the same kept states (every = 1: pairs that write both states;
+    every > 1: pairs that never step over a kept state)."""
     code = _code(T0)
     _same(T0, Ci)
     nx, ny, nz = _grid(T0)

@@ -85,8 +85,8 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True,
     (None when every state is kept).  ``coef`` = :func:`coefficient` (computed here
     when None).  ``graph``: replay the state-keeping loops from the library's graph
     cache (keyed by the buffers, which the caching allocator hands back unchanged in a
-    loop of gradients).  ``state_pairs``: the loops that keep every state (every = 1, and
-    the last segment) run fused step pairs (default :func:`state_pairs_default`)."""
+    loop of gradients).  ``state_pairs``: the loops run fused step pairs (default
+    :func:`state_pairs_default`)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     pairs = state_pairs_default(T0) if state_pairs is None else bool(state_pairs)
     if nt == 0:
@@ -101,7 +101,7 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True,
     if t_last > 0:
         # checkpoints (the state after every `every`-th step) and two work grids in one block
         block = api.StateBlock(T0, t_last // every + 2, boundary=False)
-        api.run_states(T0, block, every, C, lam, dt, inv, t_last, ci_scaled=scaled, graph=graph)
+        api.run_states(T0, block, every, C, lam, dt, inv, t_last, ci_scaled=scaled, graph=graph, temporal2=pairs)
         ckpts += block.grids[:t_last // every]
     last = api.StateBlock(T0, every, boundary=False)
     cur = api.run_states(ckpts[-1], last, 1, C, lam, dt, inv, nt - t_last, ci_scaled=scaled, graph=graph,

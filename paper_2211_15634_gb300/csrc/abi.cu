@@ -489,11 +489,42 @@ static int states_slot_after(int t, int every, int &cur_slot, int &work_next) {
     return slot;
 }
 
+// The launches of a state-keeping loop: each advances the state by `steps` (1, or 2
+// for a fused pair) and writes it to slot `dst` (>= 0 a state slot, -1 / -2 work grid
+// 0 / 1).  With every = 1 a pair also keeps its intermediate state (in slot dst - 1);
+// with every > 1 a pair never steps over a state that is kept.  Returns the slot of
+// T(nt) (-3: T0 itself, nt = 0).
+struct StatesOp {
+    int steps, dst;
+};
+static int plan_states(int nt, int every, bool pairs, std::vector<StatesOp> *ops) {
+    int cur_slot = -3, work_next = 0, t = 0;
+    while (t < nt) {
+        const int next_kept = every == 1 ? t + 2 : (t / every + 1) * every;
+        const int k = (pairs && t + 2 <= nt && t + 2 <= next_kept) ? 2 : 1;
+        if (k == 2 && every == 1) states_slot_after(t + 1, every, cur_slot, work_next);
+        const int dst = states_slot_after(t + k, every, cur_slot, work_next);
+        if (ops) ops->push_back({k, dst});
+        t += k;
+    }
+    return cur_slot;
+}
+
+// Whether PS_RUN_TEMPORAL2 runs fused pairs for this state-keeping loop (at least two
+// grids): FP32 where the pair kernel serves every grid (all 16-byte aligned at one
+// stride, so T0 and the first two grids decide).
+static bool states_pairs(unsigned flags, int dtype, int nt, Grid3 g, const void *T0, const void *grid0,
+                         const void *grid1, const void *Ci) {
+    return (flags & PS_RUN_TEMPORAL2) && dtype == PS_F32 && nt >= 2 && temporal2_ok(g, dtype, T0, grid0, Ci) &&
+           temporal2_ok(g, dtype, grid0, grid1, Ci);
+}
+
 static cudaError_t enqueue_run_states(const void *T0, char *base, int64_t grid_stride, size_t esz, int every,
                                       const void *Ci, StepCoef c, Grid3 g, int nt, int dtype, unsigned flags,
                                       cudaStream_t s) {
     const int nslots = nt / every, nwork = (every > 1 && nt > 0) ? 2 : 0;
     auto grid = [&](int slot) { return (void *)(base + (size_t)slot * (size_t)grid_stride * esz); };
+    auto slot_grid = [&](int slot) { return slot >= 0 ? grid(slot) : grid(nslots + (-1 - slot)); };
     // The boundary of every grid this call writes is T0's.  Where the z-march serves the
     // steps they store the x and y faces themselves (in their coalesced row stores), so
     // only the two z faces of each grid are copied here; else the whole boundary is.
@@ -503,33 +534,28 @@ static cudaError_t enqueue_run_states(const void *T0, char *base, int64_t grid_s
     for (int k = 0; k < ngrids && steps_bnd; ++k)
         steps_bnd = step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), T0, Ci) &&
                     step_writes_xy_boundary(dtype, scaled, native, c, g, grid(k), grid(k), Ci);
-    // PS_RUN_TEMPORAL2 (FP32, every state kept): fused pairs that write both states with
-    // their x and y faces, where the pair kernel serves every grid (all are 16-byte
-    // aligned at one stride, so the first two decide) and the single steps of an odd nt
-    // store their faces too; else single steps
-    const bool pairs_ok = (flags & PS_RUN_TEMPORAL2) && every == 1 && dtype == PS_F32 && nt >= 2 && steps_bnd &&
-                          temporal2_ok(g, dtype, T0, grid(0), Ci) && temporal2_ok(g, dtype, grid(0), grid(1), Ci);
+    // PS_RUN_TEMPORAL2 (FP32): fused pairs.  With every = 1 they keep both states and
+    // store both states' x and y faces; with every > 1 they keep only their second state
+    // and write interior nodes only, so the whole boundary is copied then.
+    const bool pairs = ngrids >= 2 && states_pairs(flags, dtype, nt, g, T0, grid(0), grid(1), Ci);
+    const bool faces_by_steps = steps_bnd && !(pairs && every > 1);
     if (nt > 0 && ngrids > 0) {
-        cudaError_t e = launch_copy_boundary_many(base, ngrids, grid_stride, T0, g, (int)esz, s, steps_bnd);
+        cudaError_t e = launch_copy_boundary_many(base, ngrids, grid_stride, T0, g, (int)esz, s, faces_by_steps);
         if (e != cudaSuccess) return e;
     }
+    std::vector<StatesOp> ops;
+    plan_states(nt, every, pairs, &ops);
     const void *cur = T0;
-    int t = 1;
-    if (pairs_ok) {
-        // fused pairs that keep both states: states t and t+1 (slots t-1, t) from state t-1
-        for (; t + 1 <= nt; t += 2) {
-            cudaError_t e = launch_step2_states_f32((float *)grid(t - 1), (float *)grid(t), (const float *)cur,
-                                                    (const float *)Ci, c, g, s);
-            if (e != cudaSuccess) return e;
-            cur = grid(t);
-        }
-    }
-    int cur_slot = -3, work_next = 0;  // -3: T0; -1, -2: work grids 0, 1
-    for (int u = 1; u < t; ++u) states_slot_after(u, every, cur_slot, work_next);
-    for (; t <= nt; ++t) {
-        const int slot = states_slot_after(t, every, cur_slot, work_next);
-        void *dst = slot >= 0 ? grid(slot) : grid(nslots + (-1 - slot));
-        cudaError_t e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, s, steps_bnd);
+    for (const StatesOp &op : ops) {
+        void *dst = slot_grid(op.dst);
+        cudaError_t e;
+        if (op.steps == 2 && every == 1)
+            e = launch_step2_states_f32((float *)grid(op.dst - 1), (float *)dst, (const float *)cur,
+                                        (const float *)Ci, c, g, s);
+        else if (op.steps == 2)
+            e = enqueue_step2(dst, cur, Ci, c, g, dtype, s);
+        else
+            e = enqueue_step(dst, cur, nullptr, nullptr, Ci, c, g, dtype, flags, s, faces_by_steps);
         if (e != cudaSuccess) return e;
         cur = dst;
     }
@@ -550,8 +576,8 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
     PS_TRY(check_scaled(flags, dtype, _dx, _dy, _dz));
     if ((flags & PS_RUN_NATIVE_F64) && dtype != PS_F64)
         return fail(PS_ERR_UNSUPPORTED, "PS_RUN_NATIVE_F64 needs PS_F64");
-    if ((flags & PS_RUN_TEMPORAL2) && (dtype != PS_F32 || every != 1))
-        return fail(PS_ERR_UNSUPPORTED, "PS_RUN_TEMPORAL2 in the state-keeping loop needs PS_F32 and every = 1");
+    if ((flags & PS_RUN_TEMPORAL2) && dtype != PS_F32)
+        return fail(PS_ERR_UNSUPPORTED, "PS_RUN_TEMPORAL2 in the state-keeping loop needs PS_F32");
     const int64_t n = nx * ny * nz;
     const size_t esz = elem_bytes(dtype);
     if (grid_stride < n || (grid_stride * (int64_t)esz) % 16 != 0)
@@ -563,10 +589,12 @@ int ps_diffusion3d_run_states(const void *T0, void *states, int64_t grid_stride,
         return fail(PS_ERR_ALIAS, "the state grids overlap T0 or Ci");
     const StepCoef c = make_coef(lam, dt, _dx, _dy, _dz);
     const Grid3 g{nx, ny, nz};
-    // the slot of T(nt), the same whichever way the steps are issued
-    int cur_slot = -3, work_next = 0;
-    for (int t = 1; t <= nt; ++t) states_slot_after(t, every, cur_slot, work_next);
     char *base = (char *)states;
+    // the slot of T(nt), from the same plan the launches follow
+    const int nall = nslots + nwork;
+    auto grid_at = [&](int k) { return (const void *)(base + (size_t)k * (size_t)grid_stride * esz); };
+    const bool pairs = nall >= 2 && states_pairs(flags, dtype, nt, g, T0, grid_at(0), grid_at(1), Ci);
+    const int cur_slot = plan_states(nt, every, pairs, nullptr);
     const unsigned f = flags & ~PS_RUN_GRAPH;
     cudaStream_t s = (cudaStream_t)stream;
     if ((flags & PS_RUN_GRAPH) && nt > 0) {

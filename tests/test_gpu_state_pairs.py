@@ -1,9 +1,10 @@
 """The FP32 state-keeping loop in fused step pairs (``api.run_states(temporal2=True)``,
-``ps_diffusion3d_run_states`` with PS_RUN_TEMPORAL2): each pair writes both states it
-computes, with their x and y faces, so every grid - boundary included - equals the
-one-step loop's state bit for bit; grids the fused-pair kernel cannot serve, and the last
-step of an odd nt, fall back to single steps.  The gradient built on these loops equals
-the one built on single steps bit for bit."""
+``ps_diffusion3d_run_states`` with PS_RUN_TEMPORAL2).  Keeping every state, each pair
+writes both states it computes, with their x and y faces; keeping every k-th, a pair
+never steps over a kept state.  Every kept grid - boundary included - and T(nt) equal
+the one-step loop's states bit for bit; grids the fused-pair kernel cannot serve fall
+back to single steps.  The gradient built on these loops equals the one built on single
+steps bit for bit."""
 import numpy as np
 import pytest
 import torch
@@ -28,22 +29,23 @@ def fp32_problem(nx, ny, nz):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-@pytest.mark.parametrize("nt", [1, 2, 3, 8])
+@pytest.mark.parametrize("nt,every", [(1, 1), (2, 1), (3, 1), (8, 1), (7, 2), (9, 3), (10, 5), (4, 7)])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_state_pairs_equal_single_steps(shape, nt, graph):
+def test_state_pairs_equal_single_steps(shape, nt, every, graph):
     nx, ny, nz = shape
     D0, C, lam, dt, inv = fp32_problem(nx, ny, nz)
     D0h = to_host(D0)
-    block = api.StateBlock(D0, nt, boundary=False)
+    block = api.StateBlock(D0, nt // every + (2 if every > 1 else 0), boundary=False)
     block.flat.fill_(float("nan"))  # unprepared grids: the call sets every boundary
-    final = api.run_states(D0, block, 1, C, lam, dt, inv, nt, graph=graph, temporal2=True)
+    final = api.run_states(D0, block, every, C, lam, dt, inv, nt, graph=graph, temporal2=True)
     a, b = D0.clone(), D0.clone()
     cur = a
     for t in range(1, nt + 1):
         dst = b if cur is a else a
         api.step(dst, cur, C, lam, dt, inv)
         cur = dst
-        assert torch.equal(block.grids[t - 1], cur), t
+        if t % every == 0:
+            assert torch.equal(block.grids[t // every - 1], cur), t
     assert torch.equal(final, cur)
     assert np.array_equal(to_host(D0), D0h)  # T0 is not modified
     api.clear_graph_cache()
@@ -51,14 +53,13 @@ def test_state_pairs_equal_single_steps(shape, nt, graph):
 
 
 def test_state_pairs_flag_rules():
-    """PS_RUN_TEMPORAL2 in the state-keeping loop: FP32 with every = 1 only."""
+    """PS_RUN_TEMPORAL2 in the state-keeping loop: FP32 only."""
     nx, ny, nz = 68, 21, 13
     D0, C, lam, dt, inv = fp32_problem(nx, ny, nz)
-    with pytest.raises(PsError):
-        api.run_states(D0, api.StateBlock(D0, 4 + 2), 2, C, lam, dt, inv, 8, temporal2=True)
     T0 = D0.double()
-    with pytest.raises(PsError):
-        api.run_states(T0, api.StateBlock(T0, 4), 1, C.double(), lam, dt, inv, 4, temporal2=True)
+    for every in (1, 2):
+        with pytest.raises(PsError):
+            api.run_states(T0, api.StateBlock(T0, 4 + 2), every, C.double(), lam, dt, inv, 4, temporal2=True)
 
 
 @pytest.mark.parametrize("every", [1, 3, 20])
