@@ -6,7 +6,7 @@ steps.  By default (``every=None``) every state is kept when the nt fields fit
 in the device's free memory with a margin (no recompute: the reverse sweep
 reads each state once), else every ``ceil(sqrt(nt))`` steps.  ``backward`` walks the
 segments in reverse: it recomputes the states of one segment from its
-checkpoint with the forward kernel (the last segment's states are kept from the
+checkpoint with the forward kernel (the last two segments' states are kept from the
 forward pass, which computes them anyway; on FP32 grids the forward's loops that
 keep every state run fused step pairs that write both states), then applies the transposed step
 (``ps_diffusion3d_adjoint``) from the segment's last step to its first,
@@ -77,16 +77,16 @@ def state_pairs_default(T0) -> bool:
 
 
 def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True, state_pairs=None):
-    """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...], last).
+    """Run nt steps; return (final state, [checkpoint at step 0, every, 2*every, ...], kept).
 
-    ``last`` holds the states of the last segment (after steps t_last+1 .. nt, t_last
-    the last checkpoint's step) in a :class:`api.StateBlock` of ``every`` grids - the
-    forward computes them anyway, so the reverse sweep need not recompute that segment
-    (None when every state is kept).  ``coef`` = :func:`coefficient` (computed here
-    when None).  ``graph``: replay the state-keeping loops from the library's graph
-    cache (keyed by the buffers, which the caching allocator hands back unchanged in a
-    loop of gradients).  ``state_pairs``: the loops run fused step pairs (default
-    :func:`state_pairs_default`)."""
+    ``kept`` maps each of the last two segments to a :class:`api.StateBlock` of ``every``
+    grids holding its states (after its steps 1, 2, ...) - the forward computes them
+    anyway, and the reverse sweep needs two segment buffers, so it takes these two
+    segments without recomputing them (None when every state is kept).  ``coef`` =
+    :func:`coefficient` (computed here when None).  ``graph``: replay the state-keeping
+    loops from the library's graph cache (keyed by the buffers, which the caching
+    allocator hands back unchanged in a loop of gradients).  ``state_pairs``: the loops
+    run fused step pairs (default :func:`state_pairs_default`)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     pairs = state_pairs_default(T0) if state_pairs is None else bool(state_pairs)
     if nt == 0:
@@ -96,33 +96,40 @@ def forward_checkpointed(T0, Ci, lam, dt, inv, nt, every, coef=None, graph=True,
         block = api.StateBlock(T0, nt, boundary=False)  # run_states sets the boundaries
         cur = api.run_states(T0, block, 1, C, lam, dt, inv, nt, ci_scaled=scaled, graph=graph, temporal2=pairs)
         return cur, [T0] + block.grids[:nt - 1], None
-    t_last = (nt - 1) // every * every  # step of the last checkpoint
+    nseg = (nt - 1) // every + 1
+    first_kept = max(0, nseg - 2)
+    t_keep = first_kept * every  # checkpoint step where the kept segments start
     ckpts = [T0]
-    if t_last > 0:
+    if t_keep > 0:
         # checkpoints (the state after every `every`-th step) and two work grids in one block
-        block = api.StateBlock(T0, t_last // every + 2, boundary=False)
-        api.run_states(T0, block, every, C, lam, dt, inv, t_last, ci_scaled=scaled, graph=graph, temporal2=pairs)
-        ckpts += block.grids[:t_last // every]
-    last = api.StateBlock(T0, every, boundary=False)
-    cur = api.run_states(ckpts[-1], last, 1, C, lam, dt, inv, nt - t_last, ci_scaled=scaled, graph=graph,
-                         temporal2=pairs)
-    return cur, ckpts, last
+        block = api.StateBlock(T0, t_keep // every + 2, boundary=False)
+        api.run_states(T0, block, every, C, lam, dt, inv, t_keep, ci_scaled=scaled, graph=graph, temporal2=pairs)
+        ckpts += block.grids[:t_keep // every]
+    kept = {}
+    cur = ckpts[-1]
+    for s in range(first_kept, nseg):
+        t0, t1 = s * every, min(s * every + every, nt)
+        kept[s] = api.StateBlock(T0, every, boundary=False)
+        cur = api.run_states(cur, kept[s], 1, C, lam, dt, inv, t1 - t0, ci_scaled=scaled, graph=graph,
+                             temporal2=pairs)
+        if s + 1 < nseg:
+            ckpts.append(cur)  # the checkpoint at step t1
+    return cur, ckpts, kept
 
 
 def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None, pairs=None,
-                          overlap=None, graph=True, last=None, state_pairs=None):
+                          overlap=None, graph=True, kept=None, state_pairs=None):
     """Reverse sweep; returns (dL/dT0, dL/dCi).  ``pairs``: take the transposed
     steps two per launch where ``api.adjoint2`` applies (default off).  ``overlap``
-    (default on for CUDA tensors with more than one segment to recompute): recompute
-    segment s-1's states on a side stream while segment s's transposed steps run,
-    into the second of two segment buffers (one more segment of memory); the kernels
-    and their order on every buffer are unchanged, so the gradient is bit for bit
-    the one-stream sweep's.  ``graph``: the segments' recomputes are replayed from the
-    graph cache, as in :func:`forward_checkpointed`.  ``last``: the last segment's
-    states from :func:`forward_checkpointed` (that segment is then not recomputed, and
-    its block serves as one of the segment buffers afterwards).  ``state_pairs``: the
-    recomputes run fused step pairs, as in :func:`forward_checkpointed` (default off, see
-    :func:`state_pairs_default`)."""
+    (default on for CUDA tensors when a segment is recomputed): recompute segment s-1's
+    states on a side stream while segment s's transposed steps run, into a second
+    segment buffer (one more segment of memory); the kernels and their order on every
+    buffer are unchanged, so the gradient is bit for bit the one-stream sweep's.
+    ``graph``: the segments' recomputes are replayed from the graph cache, as in
+    :func:`forward_checkpointed`.  ``kept``: segments whose states the forward kept
+    (:func:`forward_checkpointed`); they are not recomputed, and their blocks then serve
+    as the recomputes' buffers.  ``state_pairs``: the recomputes run fused step pairs, as
+    in :func:`forward_checkpointed` (default off, see :func:`state_pairs_default`)."""
     C, scaled = coefficient(Ci, lam, dt, inv) if coef is None else coef
     spairs = bool(state_pairs)
     pairs = bool(pairs) and not scaled and api.adjoint2_supported(ybar_nt)
@@ -131,34 +138,35 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
     cibar = torch.zeros_like(Ci)  # dL/dCs when scaled
     nseg = len(ckpts)
     seg_len = max(0, min(every, nt) - 1)  # recomputed states per segment
-    in_place = {nseg - 1} if last is not None else set()  # segments whose states are there
+    seg_buf = dict(kept) if kept else {}  # segment -> block holding its states
     if overlap is None:
-        overlap = ybar.is_cuda and nseg - len(in_place) > 1 and seg_len > 0
-    # grids for the recomputed states of a segment (run_states gives them T0's boundary);
-    # segment s uses buffer s % len(segs), the last segment's is `last` when given
-    segs = [None] * (2 if overlap else 1)
-    if last is not None:
-        segs[(nseg - 1) % len(segs)] = last
-    segs = [b if b is not None else api.StateBlock(ckpts[0], seg_len, boundary=False) for b in segs]
+        overlap = ybar.is_cuda and nseg > 1 and seg_len > 0 and nseg > len(seg_buf)
+    # the recompute of segment s writes into the block of segment s + nbuf, whose sweep is
+    # done (s + 2 beside the sweep of s + 1 on the side stream; s + 1 on one stream)
+    nbuf = 2 if overlap else 1
     main = torch.cuda.current_stream(ybar.device) if overlap else None
     side = torch.cuda.Stream(ybar.device) if overlap else None
-    ready, used = {}, [None, None]  # recompute of segment s done; sweep done with buffer b
+    ready, swept = {}, {}  # recompute of segment s done; sweep of segment s done
 
     def recompute(s):
         t0 = s * every
         t1 = min(t0 + every, nt)
-        if t1 - t0 <= 1 or s in in_place:
+        if t1 - t0 <= 1 or s in seg_buf:
             return
-        b = s % len(segs)
+        owner = s + nbuf
+        blk = seg_buf.pop(owner, None)
+        if blk is None:
+            blk = api.StateBlock(ckpts[0], seg_len, boundary=False)  # run_states sets the boundaries
+        seg_buf[s] = blk
         if not overlap:
-            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph,
+            api.run_states(ckpts[s], blk, 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph,
                            temporal2=spairs)
             return
         with torch.cuda.stream(side):
             side.wait_stream(main)  # the checkpoints and Cs are final
-            if used[b] is not None:
-                side.wait_event(used[b])  # the sweep no longer reads this buffer
-            api.run_states(ckpts[s], segs[b], 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph,
+            if owner in swept:
+                side.wait_event(swept[owner])  # the sweep no longer reads this block
+            api.run_states(ckpts[s], blk, 1, C, lam, dt, inv, t1 - t0 - 1, ci_scaled=scaled, graph=graph,
                            temporal2=spairs)
             ready[s] = torch.cuda.Event()
             ready[s].record(side)
@@ -176,8 +184,7 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
                 recompute(s)
             t0 = s * every
             t1 = min(t0 + every, nt)
-            b = s % len(segs)
-            states = [ckpts[s]] + segs[b].grids[:t1 - t0 - 1]
+            states = [ckpts[s]] + (seg_buf[s].grids[:t1 - t0 - 1] if t1 - t0 > 1 else [])
             t = t1 - 1
             while t >= t0:
                 if pairs and t - 1 >= t0:  # steps t and t-1 in one pass
@@ -188,8 +195,8 @@ def backward_checkpointed(ybar_nt, Ci, lam, dt, inv, nt, every, ckpts, coef=None
                     t -= 1
                 ybar, tbar = tbar, ybar
             if overlap:
-                used[b] = torch.cuda.Event()
-                used[b].record(main)
+                swept[s] = torch.cuda.Event()
+                swept[s].record(main)
     finally:
         if overlap:  # later work on the caller's stream (and frees of these buffers) after the side stream's
             main.wait_stream(side)
@@ -207,13 +214,13 @@ class Diffusion3DFn(torch.autograd.Function):
         Ci = Ci.detach().contiguous()
         every = auto_every(T0, int(nt)) if every is None else int(every)
         coef = coefficient(Ci, lam, dt, tuple(inv_spacing))
-        out, ckpts, last = forward_checkpointed(T0, Ci, lam, dt, tuple(inv_spacing), int(nt), every, coef)
+        out, ckpts, kept = forward_checkpointed(T0, Ci, lam, dt, tuple(inv_spacing), int(nt), every, coef)
         # T(nt) lives in a state block: hand out a field of its own, so that a caller who
         # keeps T(nt) does not keep the block alive after backward
         out = out.clone()
         ctx.cfg = (lam, dt, tuple(inv_spacing), int(nt), every)
         ctx.ckpts = ckpts
-        ctx.last = last
+        ctx.kept = kept
         ctx.coef = coef
         ctx.save_for_backward(Ci)
         return out
@@ -223,9 +230,9 @@ class Diffusion3DFn(torch.autograd.Function):
         (Ci,) = ctx.saved_tensors
         lam, dt, inv, nt, every = ctx.cfg
         dT0, dCi = backward_checkpointed(grad_out, Ci, lam, dt, inv, nt, every, ctx.ckpts,
-                                         ctx.coef, last=ctx.last)
+                                         ctx.coef, kept=ctx.kept)
         ctx.ckpts = None
-        ctx.last = None
+        ctx.kept = None
         ctx.coef = None
         return dT0, dCi, None, None, None, None, None
 
@@ -238,11 +245,11 @@ def loss_and_grad(T0, Ci, Tobs, lam, dt, inv_spacing, nt, every=None, pairs=None
     every = auto_every(T0, int(nt)) if every is None else int(every)
     inv = tuple(inv_spacing)
     coef = coefficient(Ci.contiguous(), lam, dt, inv)
-    out, ckpts, last = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef,
+    out, ckpts, kept = forward_checkpointed(T0.contiguous(), Ci.contiguous(), lam, dt, inv, nt, every, coef,
                                             state_pairs=state_pairs)
     resid = torch.empty_like(out)
     L = api.half_sq_dist(out, Tobs, residual=resid)
-    del out  # a grid of `last`, which the sweep reuses
-    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs, last=last,
+    del out  # a grid of a kept block, which the sweep reuses
+    dT0, dCi = backward_checkpointed(resid, Ci, lam, dt, inv, nt, every, ckpts, coef, pairs, kept=kept,
                                      state_pairs=state_pairs)
     return L, dT0, dCi

@@ -103,6 +103,26 @@ def test_checkpoint_interval_does_not_change_gradient(every):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("every", [2, 3, 4, 6])
+def test_one_stream_sweep_gives_the_same_gradient(every):
+    """The sweep without the side stream (recompute, then transposed steps, on one
+    stream; the kept last two segments, then each recompute in the block of the segment
+    swept before it): bit for bit the gradient of the one-segment run."""
+    nx, ny, nz, nt = 24, 14, 18, 13
+    T0, Ci, Tobs, lam, dt, inv = inverse_problem(nx, ny, nz, nt)
+    base = ag.loss_and_grad(to_dev(T0), to_dev(Ci), to_dev(Tobs), lam, dt, inv, nt, every=nt)
+    T0d, Cid, Tobsd = to_dev(T0), to_dev(Ci), to_dev(Tobs)
+    coef = ag.coefficient(Cid, lam, dt, inv)
+    out, ckpts, kept = ag.forward_checkpointed(T0d, Cid, lam, dt, inv, nt, every, coef)
+    assert len(ckpts) == (nt - 1) // every + 1 and sorted(kept) == [len(ckpts) - 2, len(ckpts) - 1]
+    resid = torch.empty_like(out)
+    L = api.half_sq_dist(out, Tobsd, residual=resid)
+    dT0, dCi = ag.backward_checkpointed(resid, Cid, lam, dt, inv, nt, every, ckpts, coef, overlap=False,
+                                        kept=kept)
+    for a, b in zip(base, (L, dT0, dCi)):
+        assert torch.equal(a, b)
+
+
 def test_gradient_central_differences_16():
     """Directional derivatives of the GPU loss against central differences of GPU
     forward runs on 16^3 (relative 1e-6)."""
