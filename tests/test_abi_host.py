@@ -237,6 +237,18 @@ def test_temporal2_rejects_unsupported_modes(lib):
     assert run(_lib.PS_F64, 0x40) == _lib.PS_ERR_ARG
 
 
+def test_run_states_temporal2_is_fp32_only(lib):
+    """The state-keeping loop takes PS_RUN_TEMPORAL2 for FP32 only (any interval); the
+    refusal comes before anything is launched."""
+    slot = ctypes.c_int(-9)
+    for every in (1, 3):
+        st = lib.ps_diffusion3d_run_states(A, B, 512, every, C, 1.0, 1e-3, 7.0, 7.0, 7.0, 8, 8, 8, 6,
+                                           _lib.PS_F64, _lib.PS_RUN_TEMPORAL2, None, ctypes.byref(slot))
+        assert st == _lib.PS_ERR_UNSUPPORTED
+        assert b"TEMPORAL2" in lib.ps_last_error()
+    assert slot.value == -9  # nothing written
+
+
 def test_copy_boundary_many_rejects_bad_stride_and_overlap(lib):
     many = lib.ps_diffusion3d_copy_boundary_many
     assert many(B, 3, 511, A, 8, 8, 8, _lib.PS_F64, None) == _lib.PS_ERR_ARG   # < nx*ny*nz
