@@ -50,10 +50,11 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=0,
                    help="problems timed end to end (0: --steps, the device-timed step count)")
-    p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint2", "batch", "step2d"],
+    p.add_argument("--kernel-loop", choices=["step", "adjoint", "adjoint2", "batch", "step2d", "states"],
                    default=None,
                    help="profiling aid: launch only this kernel --reps times at --size (no JSON); "
-                        "step2d on a --size^2 grid")
+                        "step2d on a --size^2 grid; states: the FP32 state-keeping loop of --reps "
+                        "states in fused pairs that keep both states")
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     p.add_argument("--field", choices=["gauss", "sine", "gauss_dev"], default="gauss",
                    help="kernel loop step (FP64): the workload's Gaussian on 1.7, or a field that leaves "
@@ -111,6 +112,13 @@ def run_kernel_loop(args):
                 api.step(dst, src, Cs, 1.0, dt, inv, ci_scaled=scaled)
         name = "compensated FP32 step" if comp is not None else api.step_kernel_name(
             T2, T, Cs, 1.0, dt, inv, ci_scaled=scaled, temporal2=args.temporal2)
+    elif args.kernel_loop == "states":
+        # FP32: --reps states kept, in fused pairs that write both states
+        if args.dtype != "f32":
+            raise SystemExit("--kernel-loop states is FP32 (--dtype f32)")
+        block = api.StateBlock(T, args.reps, boundary=False)
+        api.run_states(T, block, 1, C, 1.0, dt, inv, args.reps, temporal2=True)
+        name = "state-keeping loop (fused pairs keeping both states)"
     elif args.kernel_loop == "adjoint2":
         # FP32: two transposed steps per pass (states T and T2)
         if args.dtype != "f32":
