@@ -309,3 +309,94 @@ def test_fp32_past_2e31_elements():
     assert api.device_error() == 0
     del D, C32, res
     torch.cuda.empty_cache()
+
+
+SEED_YBAR_BIG = 77
+
+
+def adjoint_blocks(pts, n):
+    """(ybar, T, Ci) on the 5^3 block around each sample (clipped at the domain), from the
+    host draws: the sample's transposed step reads w and T at its six neighbours, which
+    are interior nodes of the block exactly when they are interior nodes of the grid."""
+    out = []
+    for (i, j, k) in pts:
+        i0, i1 = max(0, i - 2), min(n, i + 3)
+        j0, j1 = max(0, j - 2), min(n, j + 3)
+        k0, k1 = max(0, k - 2), min(n, k + 3)
+        kk, jj, ii = np.meshgrid(np.arange(k0, k1), np.arange(j0, j1), np.arange(i0, i1), indexing="ij")
+        idx = (ii + n * (jj + n * kk)).astype(np.uint64)
+        T = inputs.T_BASE + inputs.uniform(SEED_T_BIG, idx)
+        Ci = ((inputs.uniform(inputs.SEED_CI, idx) * 0.5) + 1.0) * (1.0 / inputs.C0)
+        ybar = inputs.uniform(SEED_YBAR_BIG, idx) - 0.5
+        out.append(((i - i0, j - j0, k - k0), ybar, T, Ci))
+    return out
+
+
+def adjoint_refs(blocks, lam, dt, inv, cast=None):
+    """The oracle's transposed step (Tbar, dL/dCi term) at each block's sample."""
+    tb, cb = [], []
+    for (li, lj, lk), ybar, T, Ci in blocks:
+        if cast is not None:
+            ybar, T, Ci = cast(ybar), cast(T), cast(Ci)
+        cib = np.zeros_like(T)
+        tbar = oracle.adjoint_step(ybar, T, Ci, cib, lam, dt, *inv)
+        tb.append(tbar[lk, lj, li])
+        cb.append(cib[lk, lj, li])
+    return np.array(tb), np.array(cb)
+
+
+def test_fp64_transposed_step_past_2e31_elements():
+    """The FP64 transposed step on the pre-scaled coefficient at 1296^3 (element offsets
+    past 2^31): Tbar and dL/dCi at samples - interior, faces, edges - against the
+    oracle's transposed step on each sample's block."""
+    n = N_BIG
+    dev = torch.device("cuda")
+    T, C = big_fields(dev)
+    ybar = inputs.uniform_field_torch(SEED_YBAR_BIG, n, n, n, dev)
+    ybar -= 0.5
+    dt = api.stable_dt(C, 1.0)
+    inv = inputs.inverse_spacing(n, n, n)
+    api.scale_ci(C, 1.0, dt, inv, out=C)  # in place: Cs
+    Tbar, Csbar = torch.empty_like(T), torch.zeros_like(T)
+    api.adjoint(Tbar, Csbar, ybar, T, C, 1.0, dt, inv, ci_scaled=True)
+    del T, C, ybar
+    api.scale_ci(Csbar, 1.0, dt, inv, out=Csbar)  # dL/dCi = dt*lam*_dx^2 * dL/dCs
+    got_t, got_c = sample(Tbar, PTS_BIG), sample(Csbar, PTS_BIG)
+    ref_t, ref_c = adjoint_refs(adjoint_blocks(PTS_BIG, n), 1.0, dt, inv)
+    assert np.max(np.abs(got_t - ref_t)) <= 1e-14
+    assert np.max(np.abs(got_c - ref_c)) <= 1e-12 * np.max(np.abs(ref_c))
+    assert np.count_nonzero(ref_c) >= 3  # interior samples carry a dL/dCi term
+    assert api.device_error() == 0
+    del Tbar, Csbar
+    torch.cuda.empty_cache()
+
+
+def test_fp32_transposed_step_past_2e31_elements():
+    """The same on FP32 fields (the states in deviation storage), against the oracle on the
+    FP32-rounded inputs."""
+    n = N_BIG
+    dev = torch.device("cuda")
+    D = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    C32, Y = torch.empty_like(D), torch.empty_like(D)
+    for k0 in range(0, n, 64):  # FP64 draws a slab at a time, rounded to FP32 like the host
+        k1 = min(n, k0 + 64)
+        idx = torch.arange(k0 * n * n, k1 * n * n, dtype=torch.int64, device=dev)
+        D[k0:k1] = ((inputs.T_BASE + inputs.uniform_torch(SEED_T_BIG, idx)) - inputs.T_BASE).view(k1 - k0, n, n)
+        C32[k0:k1] = (((inputs.uniform_torch(inputs.SEED_CI, idx) * 0.5) + 1.0) * (1.0 / inputs.C0)).view(
+            k1 - k0, n, n)
+        Y[k0:k1] = (inputs.uniform_torch(SEED_YBAR_BIG, idx) - 0.5).view(k1 - k0, n, n)
+    dt = api.stable_dt(C32, 1.0)
+    inv = inputs.inverse_spacing(n, n, n)
+    Tbar, Cib = torch.empty_like(D), torch.zeros_like(D)
+    api.adjoint(Tbar, Cib, Y, D, C32, 1.0, dt, inv)
+    del D, C32, Y
+    got_t, got_c = sample(Tbar, PTS_BIG), sample(Cib, PTS_BIG)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    blocks = [(loc, ybar, T - inputs.T_BASE, Ci) for loc, ybar, T, Ci in adjoint_blocks(PTS_BIG, n)]
+    ref_t, ref_c = adjoint_refs(blocks, 1.0, dt, inv, cast=f32)
+    assert np.max(np.abs(got_t - ref_t)) <= 2e-6 * np.max(np.abs(ref_t))
+    assert np.max(np.abs(got_c - ref_c)) <= 2e-6 * np.max(np.abs(ref_c))
+    assert np.count_nonzero(ref_c) >= 3
+    assert api.device_error() == 0
+    del Tbar, Cib
+    torch.cuda.empty_cache()

@@ -77,3 +77,27 @@ def test_gradient_with_state_pairs_is_bitwise_the_single_step_one(every):
     assert torch.equal(c0, c1)
     assert torch.count_nonzero(c0) > 0
     assert api.device_error() == 0
+
+
+def test_state_pairs_at_full_size():
+    """512^3 FP32 (the workload's size; 0.5 GiB a state): five states kept, two fused pairs
+    that keep both states and one single step, bit for bit the one-step loop's."""
+    n, nt = 512, 5
+    from paper_2211_15634_gb300 import inputs
+    T0 = torch.from_numpy(inputs.t0_gaussian(n, n, n)).cuda()
+    D0 = api.to_deviation(T0, 1.7)
+    C = api.to_f32(torch.from_numpy(inputs.ci_random(n, n, n)).cuda())
+    del T0
+    inv = inputs.inverse_spacing(n, n, n)
+    dt = api.stable_dt(C, 1.0)
+    block = api.StateBlock(D0, nt, boundary=False)
+    final = api.run_states(D0, block, 1, C, 1.0, dt, inv, nt, temporal2=True)
+    a, b = D0.clone(), D0.clone()
+    cur = a
+    for t in range(1, nt + 1):
+        dst = b if cur is a else a
+        api.step(dst, cur, C, 1.0, dt, inv)
+        cur = dst
+        assert torch.equal(block.grids[t - 1], cur), t
+    assert torch.equal(final, cur)
+    assert api.device_error() == 0
