@@ -131,3 +131,45 @@ def test_stable_dt2d_matches_oracle(shape, lengths, dtype):
     dx, dy = lengths[0] / (nx - 1), lengths[1] / (ny - 1)
     ref = oracle.stable_dt2d(dx, dy, lam, oracle.maximum(Ci))
     assert api.stable_dt2d(to_dev(Ci, dtype), lam, lengths) == ref
+
+
+N2_BIG = 46368  # 46368^2 = 2,149,991,424 nodes > 2^31
+
+
+def test_fp64_2d_past_2e31_elements():
+    """The 2-D form at 46368^2 FP64 (element offsets past 2^31, 17 GB a field), pre-scaled
+    coefficient, nt = 2: sampled nodes - interior, edges, corners' neighbours - against the
+    2-D oracle on each sample's dependency cone, whose inputs come from the same
+    counter-based draws on the host."""
+    n, nt = N2_BIG, 2
+    dev = torch.device("cuda")
+    T = torch.empty((n, n), dtype=torch.float64, device=dev)
+    C = torch.empty_like(T)
+    for j0 in range(0, n, 4096):  # the draws a slab of rows at a time (bounded temporaries)
+        j1 = min(n, j0 + 4096)
+        idx = torch.arange(j0 * n, j1 * n, dtype=torch.int64, device=dev)
+        T[j0:j1] = (inputs.T_BASE + inputs.uniform_torch(99, idx)).view(j1 - j0, n)
+        C[j0:j1] = (((inputs.uniform_torch(inputs.SEED_CI, idx) * 0.5) + 1.0) * (1.0 / inputs.C0)).view(j1 - j0, n)
+    assert T.numel() > 2 ** 31
+    dt = api.stable_dt2d(C, 1.0)
+    inv = (float(n - 1), float(n - 1))
+    api.scale_ci(C, 1.0, dt, inv, out=C)  # in place: Cs
+    res = api.run2d(T, torch.empty_like(T), C, 1.0, dt, inv, nt, ci_scaled=True)
+    pts = [(n // 2, n // 2), (1, 1), (n - 2, n - 3), (0, 4000), (n - 1, 45000), (30000, n - 2), (46000, 2)]
+    jj = torch.tensor([p[1] for p in pts], device=dev)
+    ii = torch.tensor([p[0] for p in pts], device=dev)
+    got = res[jj, ii].cpu().numpy()
+    ref = []
+    for (i, j) in pts:
+        i0, i1 = max(0, i - nt), min(n, i + nt + 1)
+        j0, j1 = max(0, j - nt), min(n, j + nt + 1)
+        J, I = np.meshgrid(np.arange(j0, j1), np.arange(i0, i1), indexing="ij")
+        idx = (I + n * J).astype(np.uint64)
+        T0c = inputs.T_BASE + inputs.uniform(99, idx)
+        Cic = ((inputs.uniform(inputs.SEED_CI, idx) * 0.5) + 1.0) * (1.0 / inputs.C0)
+        out = oracle.run2d(T0c, Cic, 1.0, dt, *inv, nt) if min(T0c.shape) >= 3 else T0c
+        ref.append(out[j - j0, i - i0])
+    assert np.max(np.abs(got - np.array(ref))) <= FP64_TOL * 2.7
+    assert api.device_error() == 0
+    del T, C, res
+    torch.cuda.empty_cache()
