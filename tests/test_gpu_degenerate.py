@@ -202,3 +202,80 @@ def test_fp64_overflowing_laplacian_gives_inf_like_the_oracle(form):
         inner = ref[1:-1, 1:-1, 1:-1]
         assert np.all(np.isinf(inner)) if nt == 1 else np.all(np.isnan(inner))
         check_nonfinite(run64(form, T0, Ci, 1.0, dt, inv, nt), ref, 2.0 ** 1023, 1e-12)
+
+
+ADJ_FORMS = {  # name: (pre-scaled coefficient?, dtype)
+    "scaled": (True, torch.float64),
+    "as_given": (False, torch.float64),
+    "f32": (False, torch.float32),
+}
+
+
+def adjoint_case(form, nx=68, ny=21, nz=13):
+    scaled, dtype = ADJ_FORMS[form]
+    d = 1.0 / (max(nx, ny, nz) - 1)
+    inv = (1.0 / d,) * 3
+    T = 1.7 + inputs.random_field((nz, ny, nx), 51, 0.0, 1.0)
+    if dtype == torch.float32:
+        T = T - 1.7
+    Ci = inputs.ci_random(nx, ny, nz)
+    dt = d * d / Ci.max() / 6.1
+    ybar = inputs.random_field((nz, ny, nx), 52, -1.0, 1.0)
+    return scaled, dtype, inv, T, Ci, dt, ybar
+
+
+def gpu_adjoint(scaled, dtype, inv, T, Ci, dt, ybar, cib0):
+    Td, Cd, Yd = to_dev(T, dtype), to_dev(Ci, dtype), to_dev(ybar, dtype)
+    C = api.scale_ci(Cd, 1.0, dt, inv) if scaled else Cd
+    tbar, cib = torch.empty_like(Td), to_dev(cib0, dtype)
+    api.adjoint(tbar, cib, Yd, Td, C, 1.0, dt, inv, ci_scaled=scaled)
+    assert api.device_error() == 0
+    return to_host(tbar), to_host(cib)
+
+
+@pytest.mark.parametrize("form", list(ADJ_FORMS))
+def test_transposed_step_degenerate_inputs(form):
+    """Zero cotangent: Tbar = 0 and the coefficient gradient unchanged.  Zero coefficient
+    (Ci = 0): w = 0, so Tbar = ybar exactly.  dt = 0 (coefficient as given): Tbar = ybar
+    and the coefficient gradient unchanged, bit for bit."""
+    scaled, dtype, inv, T, Ci, dt, ybar = adjoint_case(form)
+    cib0 = inputs.random_field(T.shape, 53, -1.0, 1.0)
+    if dtype == torch.float32:
+        cib0 = cib0.astype(np.float32).astype(np.float64)
+        ybar = ybar.astype(np.float32).astype(np.float64)
+    tb, cb = gpu_adjoint(scaled, dtype, inv, T, Ci, dt, np.zeros_like(ybar), cib0)
+    assert not np.any(tb) and np.array_equal(cb, cib0)
+    tb, _ = gpu_adjoint(scaled, dtype, inv, T, np.zeros_like(Ci), dt, ybar, cib0)
+    assert np.array_equal(tb, ybar)
+    if not scaled:  # the pre-scaled form needs dt > 0 to form Cs = dt*lam*_dx^2*Ci
+        tb, cb = gpu_adjoint(scaled, dtype, inv, T, Ci, 0.0, ybar, cib0)
+        assert np.array_equal(tb, ybar) and np.array_equal(cb, cib0)
+
+
+@pytest.mark.parametrize("form", list(ADJ_FORMS))
+def test_transposed_step_nonfinite_cotangent(form):
+    """NaN and Inf in ybar: every node the oracle's transposed step makes non-finite is
+    non-finite on the GPU too, and every node the GPU leaves finite agrees with the oracle.
+    (The FP64 forms hold w in fixed point at a scale shared by a CTA's march; a non-finite
+    w marks that CTA's Tbar NaN, a superset of the oracle's non-finite nodes.)"""
+    scaled, dtype, inv, T, Ci, dt, ybar = adjoint_case(form)
+    ybar[5, 9, 20] = np.nan
+    ybar[8, 4, 50] = np.inf
+    if dtype == torch.float32:
+        ybar = ybar.astype(np.float32).astype(np.float64)
+        T = T.astype(np.float32).astype(np.float64)
+        Ci = Ci.astype(np.float32).astype(np.float64)
+    cib0 = np.zeros_like(T)
+    tb, cb = gpu_adjoint(scaled, dtype, inv, T, Ci, dt, ybar, cib0)
+    cib_ref = np.zeros_like(T)
+    tb_ref = oracle.adjoint_step(ybar, T, Ci, cib_ref, 1.0, dt, *inv)
+    if scaled:  # the GPU accumulated dL/dCs; dL/dCi = dt*lam*_dx^2 * dL/dCs
+        cb = cb * (dt * inv[0] * inv[0])
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    for got, ref in ((tb, tb_ref), (cb, cib_ref)):
+        assert np.all(~np.isfinite(got[~np.isfinite(ref)]))
+        fin = np.isfinite(got)
+        assert np.all(np.isfinite(ref[fin]))
+        scale = np.max(np.abs(ref[np.isfinite(ref)]))
+        assert np.max(np.abs(got[fin] - ref[fin])) <= tol * scale
+        assert fin.sum() > 0.5 * got.size  # the NaN stays local to the CTAs that met it
