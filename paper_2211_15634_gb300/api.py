@@ -199,6 +199,9 @@ def run_states(T0, block: "StateBlock", every: int, Ci, lam: float, dt: float, i
     code = _code(T0)
     _same(T0, Ci)
     nx, ny, nz = _grid(T0)
+    # the library takes the block as a base pointer and a stride in T0's elements
+    if block.flat.dtype != T0.dtype or block.flat.device != T0.device or block.grids.shape != tuple(T0.shape):
+        raise ValueError("the state block must hold grids of T0's shape, dtype and device")
     nslots = nt // every
     need = nslots + (2 if every > 1 and nt > 0 else 0)
     if len(block.grids) < need:
@@ -626,8 +629,9 @@ class Batch:
             if len(pitches) != 1:
                 raise ValueError(f"problem {q}: T, T2 and Ci must share one row pitch")
             for k in ("T", "T2", "Ci"):
-                if not p[k].is_cuda or _code(p[k]) != self.code:
-                    raise TypeError(f"problem {q}: {k} must be a CUDA tensor of the batch's dtype")
+                if not p[k].is_cuda or _code(p[k]) != self.code or p[k].device != self.device:
+                    raise TypeError(f"problem {q}: {k} must be a CUDA tensor of the batch's dtype "
+                                    "on the batch's device")
             tx, ty, tz = p.get("tile", (0, 0, 0))
             arr[q] = _lib.PsProblem(p["T"].data_ptr(), p["T2"].data_ptr(), p["Ci"].data_ptr(),
                                     p["lam"], p["dt"], *p["inv_spacing"], nx, ny, nz, tx, ty, tz,

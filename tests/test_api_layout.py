@@ -43,3 +43,14 @@ def test_solve_pipeline_rejects_mismatched_host_tensors():
         api.SolvePipeline.check_host((4, 5, 6), torch.float64, Ci_host=ok.float())
     with pytest.raises(ValueError):
         api.SolvePipeline.check_host((4, 5, 6), torch.float64, out_host=torch.zeros((4, 5, 6, 1), dtype=torch.float64))
+
+
+def test_run_states_refuses_a_block_of_another_dtype_or_shape():
+    """The state block goes to the library as a base pointer and a stride in T0's
+    elements: a block of another dtype or grid shape is refused before any call."""
+    T0 = torch.zeros((5, 6, 8), dtype=torch.float64)
+    Ci = torch.ones_like(T0)
+    for blk in (api.StateBlock(T0.float(), 4, boundary=False),
+                api.StateBlock(torch.zeros((5, 6, 12), dtype=torch.float64), 4, boundary=False)):
+        with pytest.raises(ValueError, match="state block"):
+            api.run_states(T0, blk, 1, Ci, 1.0, 1e-3, (7.0, 5.0, 4.0), 4)
