@@ -69,10 +69,10 @@ def coefficient(Ci, lam, dt, inv):
 def state_pairs_default(T0) -> bool:
     """Whether the forward pass's state-keeping loops run fused step pairs that write both
     states (``api.run_states(temporal2=True)``: FP32 only; bit for bit the same states).
-    Measured at 256^3, nt = 200: 200 states in 6.05 against 6.69 ms, the gradient with every
-    state kept 18.83 against 19.47 ms.  The reverse sweep's recomputes stay single steps by
+    Measured at 256^3, nt = 200: 200 states in 5.74 against 6.71 ms, the gradient with every
+    state kept 18.52 against 19.52 ms.  The reverse sweep's recomputes stay single steps by
     default: there they run beside the transposed steps, and in pairs the sqrt(nt)
-    gradient measured slower (23.72 against 23.18 ms)."""
+    gradient measured slower (22.00 against 21.80 ms)."""
     return T0.dtype == torch.float32
 
 
